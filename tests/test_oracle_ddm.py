@@ -1,0 +1,106 @@
+"""Pins of the oracle's Krylov solver and DDM (Section 3, Eqs. 4-8) against the
+monolithic direct solve, dense linear algebra, and the structure of Eq. 7."""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import ddm, fem
+from oracle.krylov import gmres
+
+
+def test_gmres_matches_dense_solve():
+    rng = np.random.default_rng(0)
+    n = 40
+    # spectrum in a disc of radius ~4.5 around 10: restarted GMRES converges
+    A = np.eye(n) * 10 + 0.5 * (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)))
+    b = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    x, it, hist = gmres(lambda v: A @ v, b, tol=1e-13, restart=15, maxiter=400)
+    assert np.linalg.norm(x - np.linalg.solve(A, b)) <= 1e-11 * np.linalg.norm(x)
+    assert hist[-1] <= 1e-13 * 1.01
+    # exact right preconditioner -> one step
+    Ainv = np.linalg.inv(A)
+    x1, it1, _ = gmres(lambda v: A @ v, b, precond=lambda v: Ainv @ v, tol=1e-12)
+    assert it1 == 1 and np.linalg.norm(A @ x1 - b) <= 1e-11 * np.linalg.norm(b)
+    # without restart GMRES terminates in <= n steps
+    _, itn, _ = gmres(lambda v: A @ v, b, tol=1e-12, restart=n, maxiter=n)
+    assert itn <= n
+
+
+CASES = [
+    ("2d_p1_2x2", lambda: W.square_problem(8, 2, 1, 9.0, relabel=True, rotate_cells=True)),
+    ("2d_p1_3x3", lambda: W.square_problem(9, 3, 1, 7.0, mu_inv=W.mu_inv_lognormal(81, 0.3, "d3"))),
+    ("2d_p2_2x2", lambda: W.square_problem(8, 2, 2, 11.0, mu_inv=W.mu_inv_lognormal(64, 0.3, "d2"),
+                                           relabel=True, rotate_cells=True)),
+    ("3d_p1_2x2x2", lambda: W.cube_problem(4, 2, 5.0, relabel=True, rotate_cells=True)),
+]
+
+
+@pytest.mark.parametrize("name,make", CASES, ids=[c[0] for c in CASES])
+def test_ddm_fixed_point_equals_monolithic(name, make):
+    P = make()
+    S = fem.assemble(P)
+    u0 = fem.solve_monolithic(S)
+    u, info = ddm.solve(P, inner="direct", outer_tol=1e-13)
+    assert np.linalg.norm(u - u0) <= 1e-10 * np.linalg.norm(u0)
+    assert info["outer_iters"] >= 1
+    # continuity across every interface at the fixed point
+    D = info["ddm"]
+    for p in D.pairs:
+        ui = info["us"][p.i][np.searchsorted(D.subs[p.i].dofs, p.dofs)]
+        uj = info["us"][p.j][np.searchsorted(D.subs[p.j].dofs, p.dofs)]
+        assert np.linalg.norm(p.M @ (ui - uj)) <= 1e-10 * abs(p.M).max() * np.linalg.norm(u0)
+
+
+def test_single_subdomain_is_monolithic():
+    P = W.square_problem(8, 1, 2, 9.0)
+    S = fem.assemble(P)
+    u, info = ddm.solve(P, inner="direct")
+    assert info["ddm"].n_iface == 0
+    assert np.linalg.norm(u - fem.solve_monolithic(S)) <= 1e-12 * np.linalg.norm(u)
+
+
+def test_block_preconditioned_inner_gmres_matches_direct():
+    P = W.square_problem(8, 2, 2, 11.0, mu_inv=W.mu_inv_lognormal(64, 0.3, "bp"))
+    D = ddm.setup(P)
+    ud, infod = ddm.solve(D, inner="direct", outer_tol=1e-12)
+    ug, infog = ddm.solve(D, inner="block_gmres", inner_tol=1e-13, outer_tol=1e-12)
+    assert np.linalg.norm(ud - ug) <= 1e-10 * np.linalg.norm(ud)
+    assert abs(infod["outer_iters"] - infog["outer_iters"]) <= 1
+    assert len(infog["inner_iters"]) > 0
+
+
+def test_block_preconditioner_spectrum():
+    """With the exact P of Eq. 7, P^{-1}(P + iB) = I + i P^{-1}B: every
+    eigenvalue has real part 1 and at most rank(B) of them differ from 1."""
+    P = W.square_problem(4, 2, 1, 6.0)
+    D = ddm.setup(P)
+    for s in D.subs:
+        T = s.Tff.toarray()
+        Pm = s.P.toarray()
+        Bm = T.imag
+        lam = np.linalg.eigvals(np.linalg.solve(Pm, T))
+        assert np.allclose(lam.real, 1.0, atol=1e-9)
+        r = np.linalg.matrix_rank(Bm)
+        assert np.sum(np.abs(lam - 1) > 1e-8) <= r
+        assert np.allclose(Pm, Pm.T) and np.abs(T - T.T).max() < 1e-14
+
+
+def test_jacobi_and_gmres_outer_agree():
+    """Eq. 8 by its Jacobi fixed point and by GMRES: same solution, GMRES in
+    far fewer sweeps (two strips, no cross points, so Jacobi contracts)."""
+    mesh = W.structured_mesh_2d(8, 8, 2, 1)
+    pol, d = W.plane_wave_y(2)
+    P = W.Problem("strips", mesh, 1, np.ones(mesh.n_cell), 8.0, 1.0, pol, d)
+    D = ddm.setup(P)
+    ug, ig = ddm.solve(D, outer="gmres", outer_tol=1e-12)
+    uj, ij = ddm.solve(D, outer="jacobi", outer_tol=1e-11, outer_maxiter=2000)
+    assert np.linalg.norm(ug - uj) <= 1e-8 * np.linalg.norm(ug)
+    assert ij["outer_iters"] > ig["outer_iters"]
+
+
+def test_interface_sizes_small_config():
+    D = ddm.setup(W.config("square32_p1"))
+    assert D.n_iface == 128                           # 4 interfaces x 2 directions x 16 edges
+    assert [len(s.dofs) for s in D.subs] == [544] * 4
