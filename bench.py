@@ -1,0 +1,402 @@
+#!/usr/bin/env python
+"""DDM-GMRES throughput on the 256x256 order-2 square (525,312 complex DOFs,
+8x8 subdomains, omega = 40 pi, mu^{-1} piecewise constant on 16x16-cell tiles).
+
+One step = thm_assemble (operators, Dirichlet lifting, block-preconditioner
+factorisation) + thm_ddm_solve to a global FP64 true residual of 1e-8, with
+mu^{-1} already resident in HBM.  The mesh numbering / subdomain structure is
+built once per geometry before the timed region (its time is reported apart).
+
+value = DOF*iterations per second (sum over subdomains and sweeps of n_i times
+inner GMRES steps, divided by the step time), summed over ranks; the
+time-to-1e-8 of the same steps is reported as time_to_1e8_s.  Under torchrun
+(N > 1) every rank solves its own copy (replicas: the path does not shard
+across GPUs, see the design notes), so scaling is weak.
+
+--impl reference times the FP64 CPU oracle of the same workload on the host
+cores (a bounded sample per step: the subdomain solves of a few subdomains in
+the first DDM sweep, with the paper's block-preconditioned GMRES).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "square256_p2"
+WORKLOAD_DESC = ("square256_p2: unit square, 256x256 quads, order-2 Nedelec (12 DOFs/quad, "
+                 "525,312 complex DOFs), 8x8 subdomains of 32x32 cells, omega=40*pi, kappa=1, "
+                 "mu^-1 piecewise constant on 16x16-cell tiles U[0.5,2] (seed 20210525), "
+                 "E_inc=(0,exp(-i omega x)) Dirichlet on x=0, impedance elsewhere")
+METRIC = "DDM-GMRES DOF*iters/s to a 1e-8 FP64 true residual (time-to-1e-8 beside it)"
+UNIT = "DOF*iter/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--mode", default="mixed", choices=["mixed", "fp64"])
+    p.add_argument("--fp64-steps", type=int, default=1, help="steps of the plain FP64 form timed beside")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--ref-subdomains", type=int, default=4, help="subdomains per reference sample")
+    return p.parse_args()
+
+
+# --------------------------------------------------------------------------
+# clocks sampled during the timed region
+# --------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+# dist helpers
+# --------------------------------------------------------------------------
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def init_dist(ws, backend):
+    if ws > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend=backend)
+        return dist
+    return None
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def allreduce_max(dist, x):
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def allreduce_sum(dist, x):
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t)
+    return float(t.item())
+
+
+# --------------------------------------------------------------------------
+# CPU oracle sample (cpu_baseline and --impl reference)
+# --------------------------------------------------------------------------
+ORACLE_SNIPPET = r"""
+import json, os, sys, time
+sys.path.insert(0, {root!r})
+import numpy as np
+import workloads as W
+from oracle import ddm
+P = W.config({workload!r})
+t0 = time.perf_counter()
+D = ddm.setup(P)
+solve = ddm.subdomain_solver(D, "block_gmres", inner_tol=1e-10, restart=120)
+src = ddm.local_sources(D)
+setup_s = time.perf_counter() - t0
+# the first DDM sweep (zero interface data) restricted to a fixed subdomain sample
+picks = list(range(0, len(D.subs), max(1, len(D.subs) // {nsub})))[:{nsub}]
+out = []
+for step in range({steps}):
+    D.stats["inner_iters"] = []
+    t = time.perf_counter()
+    dof_iters = 0
+    for i in picks:
+        s = D.subs[i]
+        rhs = src[i]
+        if not np.any(rhs):
+            rhs = np.ones(len(s.free), np.complex128)
+        x = solve(i, rhs)
+        it = D.stats["inner_iters"][-1][1]
+        dof_iters += len(s.free) * it
+    out.append((time.perf_counter() - t, dof_iters))
+print(json.dumps({{"setup_s": setup_s, "steps": out, "picks": picks}}))
+"""
+
+
+def run_oracle_sample(steps, nsub):
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = "1"
+    code = ORACLE_SNIPPET.format(root=ROOT, workload=WORKLOAD, nsub=nsub, steps=steps)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def reference_arm(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    K, Wm = args.steps, args.warmup
+    res = run_oracle_sample(K + Wm, args.ref_subdomains)
+    timed = res["steps"][Wm:]
+    t = sum(s for s, _ in timed)
+    di = sum(d for _, d in timed)
+    value = di / t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": K, "warmup": Wm, "ms_per_step": 1e3 * t / K, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC, "mode": "fp64 oracle (numpy/scipy, 1 host thread)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"per step: block-preconditioned GMRES (tol 1e-10) solves of subdomains "
+                                   f"{res['picks']} in the first DDM sweep; oracle set-up "
+                                   f"{res['setup_s']:.1f}s untimed"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------
+# our arm
+# --------------------------------------------------------------------------
+def bytes_per_launch(sysg, mode, cls):
+    import paper_2105_11993_gb300 as thm
+    return thm.algorithmic_bytes(sysg, mode, cls)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    ws, rank, local = dist_env()
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(local)
+    dist = init_dist(ws, "nccl")
+    import paper_2105_11993_gb300 as thm
+    import workloads as W
+    from paper_2105_11993_gb300 import build
+    if rank == 0:
+        build.build()
+    barrier(dist)
+    thm.load()
+    P = W.config(WORKLOAD)
+    mu_h = np.ascontiguousarray(P.mu_inv)
+    mu_d = torch.tensor(mu_h, device="cuda")
+    st = torch.cuda.current_stream()
+
+    t = time.perf_counter()
+    mesh = thm.Mesh.from_workload(P.mesh, P.order)
+    mesh_s = time.perf_counter() - t
+    mode = args.mode
+
+    def step(m):
+        sysg = thm.System(mesh, mu_d, P.omega, P.kappa, P.pol, P.direction, stream=st)
+        u, stats = sysg.solve(mode=m, rtol=1e-8)
+        return sysg, u, stats
+
+    for _ in range(args.warmup):
+        step(mode)
+    torch.cuda.synchronize()
+
+    # timed region
+    prof_mask = (1 << thm.K_PINV) | (1 << thm.K_SPMV)
+    thm.profile_enable(prof_mask)
+    clk = ClockSampler(local)
+    clk.start()
+    barrier(dist)
+    torch.cuda.synchronize()
+    launches0 = thm.kernel_launches()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    stats_all = []
+    for _ in range(args.steps):
+        sysg, u, stats = step(mode)
+        stats_all.append(stats)
+    e1.record(st)
+    torch.cuda.synchronize()
+    barrier(dist)
+    launches = thm.kernel_launches() - launches0
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1)
+    ms_max = allreduce_max(dist, ms)
+    prof = {thm.K_NAMES[c]: thm.profile_read(c) for c in (thm.K_PINV, thm.K_SPMV)}
+    thm.profile_enable(0)
+
+    dof_iters = sum(s["dof_iters"] for s in stats_all)
+    total_dof_iters = allreduce_sum(dist, dof_iters)
+    value = total_dof_iters / (ms_max / 1e3)
+    tt = [s["seconds"] for s in stats_all]
+
+    # roofline of the dominant timed kernel (block-preconditioner apply)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    n_launch, pinv_ms = prof["pinv"]
+    per_launch_s = pinv_ms / 1e3 / max(1, n_launch)
+    alg_bytes = thm.algorithmic_bytes(sysg, mode, thm.K_PINV)
+    achieved = alg_bytes / per_launch_s / 1e9 if n_launch else None
+    spmv_n, spmv_ms = prof["spmv"]
+    spmv_bytes = thm.algorithmic_bytes(sysg, mode, thm.K_SPMV)
+    roofline = {"kernel": "k_bt_apply (block-preconditioner apply, Eq. 7)", "bound": "hbm",
+                "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": (achieved / hbm_peak) if achieved else None, "traffic": None,
+                "peak_source": peak_src, "launches": n_launch, "avg_launch_us": 1e6 * per_launch_s,
+                "alg_bytes_per_launch": alg_bytes,
+                "share_of_step": (pinv_ms / ms) if ms > 0 else None,
+                "spmv": {"launches": spmv_n, "avg_launch_us": 1e6 * spmv_ms / 1e3 / max(1, spmv_n),
+                         "achieved": spmv_bytes / (spmv_ms / 1e3 / max(1, spmv_n)) / 1e9 if spmv_n else None,
+                         "share_of_step": (spmv_ms / ms) if ms > 0 else None}}
+
+    # plain FP64 form, timed beside (time-to-1e-8)
+    fp64 = None
+    if mode == "mixed" and args.fp64_steps > 0:
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(st)
+        fstats = []
+        for _ in range(args.fp64_steps):
+            _, _, s64 = step("fp64")
+            fstats.append(s64)
+        f1.record(st)
+        torch.cuda.synchronize()
+        fms = f0.elapsed_time(f1) / args.fp64_steps
+        fp64 = {"ms_per_step": fms, "time_to_1e8_s": statistics.median(s["seconds"] for s in fstats),
+                "dof_iters_per_s": sum(s["dof_iters"] for s in fstats) / (fms * args.fp64_steps / 1e3),
+                "outer_iters": fstats[-1]["outer_iters"], "inner_iters": fstats[-1]["inner_iters"],
+                "rel_residual": fstats[-1]["rel_residual"],
+                "mixed_speedup_time_to_1e8": statistics.median(s["seconds"] for s in fstats) / statistics.median(tt)}
+
+    # end to end through the host API: mesh from host arrays, mu^{-1} from
+    # pinned host memory, solution copied back to host memory
+    mu_pin = torch.tensor(mu_h).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_di = 0
+    for _ in range(max(1, min(args.steps, 2))):
+        mesh2 = thm.Mesh.from_workload(P.mesh, P.order)
+        s2 = thm.System(mesh2, mu_pin.numpy(), P.omega, P.kappa, P.pol, P.direction, stream=st)
+        uh, st2 = s2.solve_host(mode=mode, rtol=1e-8)
+        e2e_di += st2["dof_iters"]
+        del s2, mesh2
+    torch.cuda.synchronize()
+    e2e_t = time.perf_counter() - t0
+    e2e_t = allreduce_max(dist, e2e_t)
+    e2e_val = allreduce_sum(dist, e2e_di) / e2e_t
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        try:
+            res = run_oracle_sample(1, args.ref_subdomains)
+            s, d = res["steps"][0]
+            cpu = {"value": d / s, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": f"block-preconditioned GMRES (tol 1e-10) solves of subdomains {res['picks']} "
+                             f"of the first DDM sweep of the same workload, {s:.1f}s; oracle set-up "
+                             f"{res['setup_s']:.1f}s untimed"}
+        except Exception as ex:  # noqa: BLE001
+            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {ex}"}
+
+    if rank == 0:
+        last = stats_all[-1]
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws if ws > 1 else args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 operator/preconditioner/inner Krylov + f64 refinement" if mode == "mixed" else "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD_DESC, "mode": mode, "parallelism": f"replicas x{max(ws, 1)}",
+                       "l2": "no flush: the per-step working set (operators, factors, Krylov bases) "
+                             "exceeds the 129 MB L2", "step": "thm_assemble + thm_ddm_solve (rtol 1e-8)",
+                       "mesh_setup_s": mesh_s},
+            "time_to_1e8_s": statistics.median(tt),
+            "solve": {"outer_iters": last["outer_iters"], "sweeps": last["sweeps"],
+                      "inner_iters": last["inner_iters"], "max_inner_iters": last["max_inner_iters"],
+                      "refine_steps": last["refine_steps"], "rel_residual": last["rel_residual"],
+                      "dof_iters": last["dof_iters"]},
+            "fp64": fp64,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(mu_h.nbytes),
+                    "d2h_bytes_per_step": int(16 * sysg.n_dof),
+                    "includes": "thm_mesh_create from host arrays + thm_assemble from host mu^-1 + "
+                                "thm_ddm_solve_host"},
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

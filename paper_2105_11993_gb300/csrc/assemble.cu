@@ -1,0 +1,703 @@
+// Assembly of the subdomain operators T_i = P_i + i B_i (Section 2, the
+// integrals (A), (M), (B) and Eq. 3; Section 3.1, the transmission term of
+// Eq. 5), the Dirichlet data and lifting, and the factorisation of the block
+// preconditioner P_i = A_i - omega^2 M_i of Eq. 7.
+#include <cmath>
+
+#include "common.cuh"
+
+namespace thm {
+
+// ---------------------------------------------------------------------------
+// Reference matrices.  Every component of a reference basis function (and of
+// its curl) is c * f(xi) * g(eta) with f, g from five quadratics; integrals of
+// products of two such terms are exact sums of monomial integrals 1/(i+j+1).
+// Output layout: ref[0] = int curl_i curl_j, ref[1] = int phi_i,x phi_j,x,
+// ref[2] = int phi_i,y phi_j,y on the unit square (12 x 12 each, row-major).
+// Per cell of sides a (xi) and b (eta):  A = ref0/(ab),  M = (b/a) ref1 + (a/b) ref2.
+// ---------------------------------------------------------------------------
+__constant__ double c_poly[5][3] = {
+    {1, 0, 0},     // 1
+    {0, 1, 0},     // t
+    {1, -1, 0},    // 1 - t
+    {0, 1, -1},    // q(t)  = t (1 - t)
+    {1, -2, 0},    // q'(t) = 1 - 2t
+};
+
+struct Term {
+    double c;
+    int f, g;
+};
+
+// Terms (x component, y component, curl) of the 12 order-2 functions in the
+// local order [W0 G0 W1 G1 W2 G2 W3 G3 B0 B1 B2 B3]; order 1 uses W0..W3.
+__device__ void basis_terms(int order, int i, Term& x, Term& y, Term& cu) {
+    const Term Z{0, 0, 0};
+    // Whitney functions of local edges 0..3
+    const Term Wx[4] = {{1, 0, 2}, {1, 0, 1}, Z, Z};
+    const Term Wy[4] = {Z, Z, {1, 2, 0}, {1, 1, 0}};
+    const Term Wc[4] = {{1, 0, 0}, {-1, 0, 0}, {-1, 0, 0}, {1, 0, 0}};
+    // gradient functions grad(q(s) * ramp)
+    const Term Gx[4] = {{1, 4, 2}, {1, 4, 1}, {-1, 0, 3}, {1, 0, 3}};
+    const Term Gy[4] = {{-1, 3, 0}, {1, 3, 0}, {1, 2, 4}, {1, 1, 4}};
+    // cell bubbles
+    const Term Bx[4] = {{1, 2, 3}, {1, 1, 3}, Z, Z};
+    const Term By[4] = {Z, Z, {1, 3, 2}, {1, 3, 1}};
+    const Term Bc[4] = {{-1, 2, 4}, {-1, 1, 4}, {1, 4, 2}, {1, 4, 1}};
+    if (order == 1) {
+        x = Wx[i]; y = Wy[i]; cu = Wc[i];
+        return;
+    }
+    if (i < 8) {
+        int k = i >> 1;
+        if ((i & 1) == 0) { x = Wx[k]; y = Wy[k]; cu = Wc[k]; }
+        else { x = Gx[k]; y = Gy[k]; cu = Z; }
+    } else {
+        int k = i - 8;
+        x = Bx[k]; y = By[k]; cu = Bc[k];
+    }
+}
+
+__device__ double int1(int f, int g) {
+    double s = 0;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            if (c_poly[f][i] != 0 && c_poly[g][j] != 0) s += c_poly[f][i] * c_poly[g][j] / (double)(i + j + 1);
+    return s;
+}
+
+__device__ double int2(const Term& a, const Term& b) {
+    if (a.c == 0 || b.c == 0) return 0.0;
+    return a.c * b.c * int1(a.f, b.f) * int1(a.g, b.g);
+}
+
+__global__ void k_ref_matrices(int order, int nb, double* ref) {
+    for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
+        int i = t / nb, j = t % nb;
+        if (j < i) continue;
+        Term xi, yi, ci, xj, yj, cj;
+        basis_terms(order, i, xi, yi, ci);
+        basis_terms(order, j, xj, yj, cj);
+        double a = int2(ci, cj), mx = int2(xi, xj), my = int2(yi, yj);
+        ref[0 * 144 + i * nb + j] = a;  ref[0 * 144 + j * nb + i] = a;
+        ref[1 * 144 + i * nb + j] = mx; ref[1 * 144 + j * nb + i] = mx;
+        ref[2 * 144 + i * nb + j] = my; ref[2 * 144 + j * nb + i] = my;
+    }
+}
+
+__device__ __forceinline__ void cell_sides(const double* X, const int32_t* cv, double& a, double& b) {
+    double ax = X[cv[1] * 2] - X[cv[0] * 2], ay = X[cv[1] * 2 + 1] - X[cv[0] * 2 + 1];
+    double bx = X[cv[2] * 2] - X[cv[0] * 2], by = X[cv[2] * 2 + 1] - X[cv[0] * 2 + 1];
+    a = sqrt(ax * ax + ay * ay);
+    b = sqrt(bx * bx + by * by);
+}
+
+// Local entry (kr, kc) of cell c: mu^{-1} A - omega^2 M (unsigned, local basis).
+__device__ __forceinline__ double cell_entry(const double* ref, int nb, double mu, double w2,
+                                             double a, double b, int kr, int kc) {
+    double A = ref[kr * nb + kc], Mx = ref[144 + kr * nb + kc], My = ref[288 + kr * nb + kc];
+    return mu * A / (a * b) - w2 * ((b / a) * Mx + (a / b) * My);
+}
+
+// Gather-by-row assembly of P_i in the SELL layout.  Entry (r, col) sums the
+// cells holding both DOFs in ascending cell order; entry (col, r) visits the
+// same cells in the same order with exactly symmetric reference entries, so
+// P_i is bit-symmetric.
+__global__ void k_assemble(int64_t n_loc, int nb, int maxc, const double* __restrict__ ref,
+                           const double* __restrict__ X, const int32_t* __restrict__ cells,
+                           const int8_t* __restrict__ signs, const int32_t* __restrict__ cell_loc,
+                           const double* __restrict__ mu, double w2,
+                           const int64_t* __restrict__ slice_ptr, const int32_t* __restrict__ col,
+                           const uint8_t* __restrict__ pad, const int32_t* __restrict__ row_cell,
+                           const int32_t* __restrict__ row_k, double* __restrict__ val64,
+                           float* __restrict__ val32) {
+    int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= n_loc) return;
+    int64_t sl = r / SELL_C;
+    int lane = (int)(r % SELL_C);
+    int64_t base = slice_ptr[sl];
+    int w = (int)((slice_ptr[sl + 1] - base) / SELL_C);
+    for (int t = 0; t < w; ++t) {
+        int64_t idx = base + (int64_t)t * SELL_C + lane;
+        double v = 0.0;
+        if (!pad[idx]) {
+            int32_t cc = col[idx];
+            for (int u = 0; u < maxc; ++u) {
+                int32_t c = row_cell[r * maxc + u];
+                if (c < 0) break;
+                int kr = row_k[r * maxc + u];
+                for (int kc = 0; kc < nb; ++kc) {
+                    if (cell_loc[(int64_t)c * nb + kc] != cc) continue;
+                    double a, b;
+                    cell_sides(X, cells + (int64_t)c * 4, a, b);
+                    double s = (double)(signs[(int64_t)c * nb + kr] * signs[(int64_t)c * nb + kc]);
+                    v += s * cell_entry(ref, nb, mu[c], w2, a, b, kr, kc);
+                }
+            }
+        }
+        val64[idx] = v;
+        val32[idx] = (float)v;
+    }
+}
+
+// Tangential mass of a DOF on its own face edge: Whitney trace 1/l,
+// gradient trace (1-2s)/l gives 1/(3l); the two are L2-orthogonal.
+__device__ __forceinline__ double edge_trace_mass(const double* X, const int64_t* elo,
+                                                  const int64_t* ehi, int e, int fn) {
+    double dx = X[ehi[e] * 2] - X[elo[e] * 2], dy = X[ehi[e] * 2 + 1] - X[elo[e] * 2 + 1];
+    double l = sqrt(dx * dx + dy * dy);
+    return fn == 0 ? 1.0 / l : 1.0 / (3.0 * l);
+}
+
+__global__ void k_face_terms(int64_t n_loc, const double* __restrict__ X, const int64_t* __restrict__ elo,
+                             const int64_t* __restrict__ ehi, const int8_t* __restrict__ kind,
+                             const int8_t* __restrict__ fn, const int32_t* __restrict__ edge, double kw,
+                             double* bg64, double* bs64, float* bg32, float* bs32) {
+    int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= n_loc) return;
+    double g = 0, s = 0;
+    if (kind[r] != 0) {
+        double mval = kw * edge_trace_mass(X, elo, ehi, edge[r], fn[r]);
+        if (kind[r] == 1) g = mval;
+        else s = mval;
+    }
+    bg64[r] = g; bs64[r] = s; bg32[r] = (float)g; bs32[r] = (float)s;
+}
+
+__global__ void k_iface_mass(int64_t n_if, const double* __restrict__ X, const int64_t* __restrict__ elo,
+                             const int64_t* __restrict__ ehi, const int32_t* __restrict__ edge,
+                             const int8_t* __restrict__ fn, double* __restrict__ mass) {
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= n_if) return;
+    mass[k] = edge_trace_mass(X, elo, ehi, edge[k], fn[k]);
+}
+
+// Dirichlet values: tangential moments of E^inc(x) = pol exp(-i omega dir.x)
+// along the global direction lo -> hi, by 8-point Gauss-Legendre on [0,1]:
+//   Whitney DOF  m0 = l int_0^1 E_t(s) ds,
+//   gradient DOF m1 = 3 l int_0^1 E_t(s) (1 - 2s) ds.
+__constant__ double c_gl8_x[8] = {-0.9602898564975363, -0.7966664774136267, -0.5255324099163290,
+                                  -0.1834346424956498, 0.1834346424956498,  0.5255324099163290,
+                                  0.7966664774136267,  0.9602898564975363};
+__constant__ double c_gl8_w[8] = {0.1012285362903763, 0.2223810344533745, 0.3137066458778873,
+                                  0.3626837833783620, 0.3626837833783620, 0.3137066458778873,
+                                  0.2223810344533745, 0.1012285362903763};
+
+__global__ void k_dirichlet(int64_t n_de, int dim, int order, const int64_t* __restrict__ edges,
+                            const double* __restrict__ X, const int64_t* __restrict__ elo,
+                            const int64_t* __restrict__ ehi, double omega, double pr0, double pi0,
+                            double pr1, double pi1, double pr2, double pi2, double d0, double d1,
+                            double d2, double2* __restrict__ uD) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= n_de) return;
+    int64_t e = edges[t];
+    double xl[3] = {0, 0, 0}, tv[3] = {0, 0, 0};
+    for (int k = 0; k < dim; ++k) {
+        xl[k] = X[elo[e] * dim + k];
+        tv[k] = X[ehi[e] * dim + k] - xl[k];
+    }
+    double l = sqrt(tv[0] * tv[0] + tv[1] * tv[1] + tv[2] * tv[2]);
+    // pol . t_hat
+    double ptr = (pr0 * tv[0] + pr1 * tv[1] + pr2 * tv[2]) / l;
+    double pti = (pi0 * tv[0] + pi1 * tv[1] + pi2 * tv[2]) / l;
+    double m0r = 0, m0i = 0, m1r = 0, m1i = 0;
+    for (int q = 0; q < 8; ++q) {
+        double s = 0.5 * (c_gl8_x[q] + 1.0), wq = 0.5 * c_gl8_w[q];
+        double ph = -omega * (d0 * (xl[0] + s * tv[0]) + d1 * (xl[1] + s * tv[1]) + d2 * (xl[2] + s * tv[2]));
+        double sn, cs;
+        sincos(ph, &sn, &cs);
+        double er = ptr * cs - pti * sn, ei = ptr * sn + pti * cs;
+        m0r += wq * er; m0i += wq * ei;
+        m1r += wq * er * (1.0 - 2.0 * s); m1i += wq * ei * (1.0 - 2.0 * s);
+    }
+    if (order == 1) {
+        uD[e] = make_double2(l * m0r, l * m0i);
+    } else {
+        uD[2 * e] = make_double2(l * m0r, l * m0i);
+        uD[2 * e + 1] = make_double2(3.0 * l * m1r, 3.0 * l * m1i);
+    }
+}
+
+// Lifting: f_i = -(P_i)_{F,D} u_D from the cells of each row (2-D: the face
+// terms never couple a free DOF to a Dirichlet one).
+__global__ void k_lifting(int64_t n_loc, int nb, int maxc, const double* __restrict__ ref,
+                          const double* __restrict__ X, const int32_t* __restrict__ cells,
+                          const int8_t* __restrict__ signs, const int32_t* __restrict__ cell_loc,
+                          const int32_t* __restrict__ cell_dofs, const double* __restrict__ mu, double w2,
+                          const int32_t* __restrict__ row_cell, const int32_t* __restrict__ row_k,
+                          const double2* __restrict__ uD, double2* __restrict__ f) {
+    int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= n_loc) return;
+    double fr = 0, fi = 0;
+    for (int u = 0; u < maxc; ++u) {
+        int32_t c = row_cell[r * maxc + u];
+        if (c < 0) break;
+        int kr = row_k[r * maxc + u];
+        double a, b;
+        cell_sides(X, cells + (int64_t)c * 4, a, b);
+        for (int kc = 0; kc < nb; ++kc) {
+            if (cell_loc[(int64_t)c * nb + kc] >= 0) continue;
+            double s = (double)(signs[(int64_t)c * nb + kr] * signs[(int64_t)c * nb + kc]);
+            double v = s * cell_entry(ref, nb, mu[c], w2, a, b, kr, kc);
+            double2 d = uD[cell_dofs[(int64_t)c * nb + kc]];
+            fr -= v * d.x;
+            fi -= v * d.y;
+        }
+    }
+    f[r] = make_double2(fr, fi);
+}
+
+// ---------------------------------------------------------------------------
+// Static condensation of the order-2 cell bubbles (they couple only to the
+// edge DOFs of their own cell): per cell D = P_II (4x4), G = P_EI D^{-1}
+// (8x4), and the condensed edge matrix S = P_EE - sum_cells G P_IE.
+// ---------------------------------------------------------------------------
+__global__ void k_condense(int64_t n_cell, const double* __restrict__ ref, const double* __restrict__ X,
+                           const int32_t* __restrict__ cells, const int8_t* __restrict__ signs,
+                           const double* __restrict__ mu, double w2, double* __restrict__ cinv,
+                           double* __restrict__ cg, double* __restrict__ ccor, float* __restrict__ cinv32,
+                           float* __restrict__ cg32, int* __restrict__ bad) {
+    int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= n_cell) return;
+    double a, b;
+    cell_sides(X, cells + c * 4, a, b);
+    double D[4][8];                              // [D | I] -> [I | D^{-1}]
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) {
+            D[i][j] = cell_entry(ref, 12, mu[c], w2, a, b, 8 + i, 8 + j);
+            D[i][4 + j] = i == j ? 1.0 : 0.0;
+        }
+    for (int k = 0; k < 4; ++k) {
+        int p = k;
+        for (int i = k + 1; i < 4; ++i)
+            if (fabs(D[i][k]) > fabs(D[p][k])) p = i;
+        if (!(fabs(D[p][k]) > 0)) { atomicExch(bad, 1); return; }
+        if (p != k)
+            for (int j = 0; j < 8; ++j) { double t = D[k][j]; D[k][j] = D[p][j]; D[p][j] = t; }
+        double inv = 1.0 / D[k][k];
+        for (int j = 0; j < 8; ++j) D[k][j] *= inv;
+        for (int i = 0; i < 4; ++i)
+            if (i != k) {
+                double f = D[i][k];
+                for (int j = 0; j < 8; ++j) D[i][j] -= f * D[k][j];
+            }
+    }
+    double Di[4][4];
+    for (int i = 0; i < 4; ++i)
+        for (int j = i; j < 4; ++j) {              // symmetrise the inverse of a symmetric block
+            double v = 0.5 * (D[i][4 + j] + D[j][4 + i]);
+            Di[i][j] = v; Di[j][i] = v;
+        }
+    double PEI[8][4];
+    for (int e = 0; e < 8; ++e)
+        for (int k = 0; k < 4; ++k)
+            PEI[e][k] = (double)signs[c * 12 + e] * cell_entry(ref, 12, mu[c], w2, a, b, e, 8 + k);
+    double G[8][4];
+    for (int e = 0; e < 8; ++e)
+        for (int k = 0; k < 4; ++k) {
+            double v = 0;
+            for (int j = 0; j < 4; ++j) v += PEI[e][j] * Di[j][k];
+            G[e][k] = v;
+        }
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) {
+            cinv[c * 16 + i * 4 + j] = Di[i][j];
+            cinv32[c * 16 + i * 4 + j] = (float)Di[i][j];
+        }
+    for (int e = 0; e < 8; ++e)
+        for (int k = 0; k < 4; ++k) {
+            cg[c * 32 + e * 4 + k] = G[e][k];
+            cg32[c * 32 + e * 4 + k] = (float)G[e][k];
+        }
+    for (int e = 0; e < 8; ++e)
+        for (int f = e; f < 8; ++f) {              // symmetric correction G P_IE
+            double v = 0;
+            for (int k = 0; k < 4; ++k) v += G[e][k] * PEI[f][k];
+            ccor[c * 64 + e * 8 + f] = v;
+            ccor[c * 64 + f * 8 + e] = v;
+        }
+}
+
+// S values on the SELL pattern: edge row r, edge column: P - sum of cell corrections;
+// bubble rows/columns and padding: 0.  Without bubbles S = P.
+__global__ void k_condensed_values(int64_t n_loc, int nb, int maxc, int condensed,
+                                   const int64_t* __restrict__ slice_ptr, const int32_t* __restrict__ col,
+                                   const uint8_t* __restrict__ pad, const int32_t* __restrict__ row_cell,
+                                   const int32_t* __restrict__ row_k, const int32_t* __restrict__ cell_loc,
+                                   const uint8_t* __restrict__ is_bub, const double* __restrict__ val,
+                                   const double* __restrict__ ccor, double* __restrict__ sval,
+                                   float* __restrict__ sval32) {
+    int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= n_loc) return;
+    int64_t sl = r / SELL_C;
+    int lane = (int)(r % SELL_C);
+    int64_t base = slice_ptr[sl];
+    int w = (int)((slice_ptr[sl + 1] - base) / SELL_C);
+    for (int t = 0; t < w; ++t) {
+        int64_t idx = base + (int64_t)t * SELL_C + lane;
+        double v = 0.0;
+        int32_t cc = col[idx];
+        if (!pad[idx] && !(condensed && (is_bub[r] || is_bub[cc]))) {
+            v = val[idx];
+            if (condensed)
+                for (int u = 0; u < maxc; ++u) {
+                    int32_t c = row_cell[r * maxc + u];
+                    if (c < 0) break;
+                    int kr = row_k[r * maxc + u];
+                    for (int kc = 0; kc < 8; ++kc)
+                        if (cell_loc[(int64_t)c * nb + kc] == cc) v -= ccor[(int64_t)c * 64 + kr * 8 + kc];
+                }
+        }
+        sval[idx] = v;
+        sval32[idx] = (float)v;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Level-block-tridiagonal factorisation of S (= P_i, or its edge Schur
+// complement for order 2), one CTA per subdomain.  With levels l = 0..L-1
+// (BFS layers of the DOF graph, merged up to max_block), S is block
+// tridiagonal with diagonal blocks D_l and off-diagonal blocks
+// E_l = S_{l,l-1}, F_l = S_{l,l+1} = E_{l+1}^T:
+//   S_0 = D_0,  S_l = D_l - E_l W_{l-1} E_l^T,  W_l = S_l^{-1}.
+// Apply (x = S^{-1} r):  z_l = W_l (r_l - E_l z_{l-1});  x_{L-1} = z_{L-1},
+// x_l = z_l - W_l F_l x_{l+1}.  Only the dense W_l are stored; E_l, F_l are
+// read from the sparse S.  S_l^{-1} by Gauss-Jordan with partial pivoting.
+// ---------------------------------------------------------------------------
+template <class F>
+__device__ void cta_gemm(F* C, const F* A, const F* B, int m, int k, int n, bool b_transposed, bool subtract) {
+    // C (m x n) (-)= A (m x k) * (B (k x n) or B^T with B (n x k)); row-major, no aliasing
+    for (int t = threadIdx.x; t < m * n; t += blockDim.x) {
+        int i = t / n, j = t % n;
+        F acc = 0;
+        if (b_transposed)
+            for (int q = 0; q < k; ++q) acc += A[(int64_t)i * k + q] * B[(int64_t)j * k + q];
+        else
+            for (int q = 0; q < k; ++q) acc += A[(int64_t)i * k + q] * B[(int64_t)q * n + j];
+        if (subtract) C[t] -= acc;
+        else C[t] = acc;
+    }
+}
+
+template <class F>
+__device__ bool cta_gauss_jordan(F* W, int m, int* perm, F* fcol, F* rv, int* ri) {
+    __shared__ int s_piv;
+    __shared__ int s_bad;
+    if (threadIdx.x == 0) s_bad = 0;
+    __syncthreads();
+    for (int k = 0; k < m; ++k) {
+        // pivot: largest |W[i][k]|, i >= k (lowest index on ties)
+        F best = -1;
+        int bi = -1;
+        for (int i = k + threadIdx.x; i < m; i += blockDim.x) {
+            F v = W[(int64_t)i * m + k];
+            v = v < 0 ? -v : v;
+            if (v > best) { best = v; bi = i; }
+        }
+        rv[threadIdx.x] = best;
+        ri[threadIdx.x] = bi;
+        __syncthreads();
+        for (int sh = blockDim.x / 2; sh > 0; sh >>= 1) {
+            if (threadIdx.x < sh) {
+                F o = rv[threadIdx.x + sh];
+                int oi = ri[threadIdx.x + sh];
+                if (o > rv[threadIdx.x] || (o == rv[threadIdx.x] && oi >= 0 && (ri[threadIdx.x] < 0 || oi < ri[threadIdx.x]))) {
+                    rv[threadIdx.x] = o;
+                    ri[threadIdx.x] = oi;
+                }
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            s_piv = ri[0];
+            if (!(rv[0] > 0) || !isfinite((double)rv[0])) s_bad = 1;
+            perm[k] = ri[0] < 0 ? k : ri[0];
+        }
+        __syncthreads();
+        if (s_bad) return false;
+        int p = s_piv;
+        if (p != k)
+            for (int j = threadIdx.x; j < m; j += blockDim.x) {
+                F a = W[(int64_t)k * m + j];
+                W[(int64_t)k * m + j] = W[(int64_t)p * m + j];
+                W[(int64_t)p * m + j] = a;
+            }
+        __syncthreads();
+        for (int i = threadIdx.x; i < m; i += blockDim.x) fcol[i] = (i == k) ? F(0) : W[(int64_t)i * m + k];
+        __syncthreads();
+        F piv = W[(int64_t)k * m + k];
+        __syncthreads();
+        for (int j = threadIdx.x; j < m; j += blockDim.x) {
+            F v = (j == k) ? F(1) : W[(int64_t)k * m + j];
+            W[(int64_t)k * m + j] = v / piv;
+        }
+        __syncthreads();
+        for (int64_t t = threadIdx.x; t < (int64_t)m * m; t += blockDim.x) {
+            int i = (int)(t / m), j = (int)(t % m);
+            if (i == k) continue;
+            F a = (j == k) ? F(0) : W[t];
+            W[t] = a - fcol[i] * W[(int64_t)k * m + j];
+        }
+        __syncthreads();
+    }
+    // undo the row interchanges as column interchanges, last first
+    for (int k = m - 1; k >= 0; --k) {
+        int p = perm[k];
+        if (p != k)
+            for (int i = threadIdx.x; i < m; i += blockDim.x) {
+                F a = W[(int64_t)i * m + k];
+                W[(int64_t)i * m + k] = W[(int64_t)i * m + p];
+                W[(int64_t)i * m + p] = a;
+            }
+        __syncthreads();
+    }
+    return true;
+}
+
+template <class F>
+__device__ void extract_block(const Level& L, int64_t c0, int mc, F* dst, const int64_t* slice_ptr,
+                              const int32_t* col, const uint8_t* pad, const double* val) {
+    // dst (L.size x mc) = S rows of level L, columns in [c0, c0 + mc)
+    for (int64_t t = threadIdx.x; t < (int64_t)L.size * mc; t += blockDim.x) dst[t] = F(0);
+    __syncthreads();
+    for (int i = threadIdx.x; i < L.size; i += blockDim.x) {
+        int64_t r = L.start + i;
+        int64_t sl = r / SELL_C;
+        int lane = (int)(r % SELL_C);
+        int64_t base = slice_ptr[sl];
+        int w = (int)((slice_ptr[sl + 1] - base) / SELL_C);
+        for (int t = 0; t < w; ++t) {
+            int64_t idx = base + (int64_t)t * SELL_C + lane;
+            if (pad[idx]) continue;
+            int64_t cc = col[idx];
+            if (cc >= c0 && cc < c0 + mc) dst[(int64_t)i * mc + (cc - c0)] = (F)val[idx];
+        }
+    }
+    __syncthreads();
+}
+
+__global__ void k_bt_factor(const Sub* __restrict__ subs, const Level* __restrict__ levels,
+                            const int64_t* __restrict__ slice_ptr, const int32_t* __restrict__ col,
+                            const uint8_t* __restrict__ pad, const double* __restrict__ sval, double* fac,
+                            double* tmp_all, int64_t tmp_stride, int* perm_all, int max_m, int* status) {
+    extern __shared__ unsigned char smem_raw[];
+    double* fcol = reinterpret_cast<double*>(smem_raw);
+    double* rv = fcol + max_m;
+    int* ri = reinterpret_cast<int*>(rv + blockDim.x);
+    const int s = blockIdx.x;
+    const Sub S = subs[s];
+    double* tE = tmp_all + (int64_t)s * tmp_stride;
+    double* tT = tE + (int64_t)max_m * max_m;
+    int* perm = perm_all + (int64_t)s * max_m;
+    for (int l = 0; l < S.nlev; ++l) {
+        const Level L = levels[S.lev0 + l];
+        double* W = fac + L.offW;
+        extract_block(L, L.start, L.size, W, slice_ptr, col, pad, sval);
+        if (l > 0) {
+            const Level Lp = levels[S.lev0 + l - 1];
+            extract_block(L, Lp.start, Lp.size, tE, slice_ptr, col, pad, sval);          // E_l
+            cta_gemm(tT, tE, fac + Lp.offW, L.size, Lp.size, Lp.size, false, false);   // E_l W_{l-1}
+            __syncthreads();
+            cta_gemm(W, tT, tE, L.size, Lp.size, L.size, true, true);                   // S_l
+            __syncthreads();
+        }
+        if (!cta_gauss_jordan(W, L.size, perm, fcol, rv, ri)) {
+            if (threadIdx.x == 0) atomicExch(status, 1);
+            return;
+        }
+    }
+}
+
+__global__ void k_gather_slots(int64_t n, const int64_t* __restrict__ slot, const double* __restrict__ v,
+                               double* __restrict__ o64, float* __restrict__ o32) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) {
+        double x = slot[i] >= 0 ? v[slot[i]] : 0.0;
+        o64[i] = x;
+        o32[i] = (float)x;
+    }
+}
+
+// Order-2 gather tables of the condensation steps (see thm_sys::tab_*).
+__global__ void k_cond_tables(int64_t n_loc, int maxc, const uint8_t* __restrict__ is_bub,
+                              const int32_t* __restrict__ row_cell, const int32_t* __restrict__ row_k,
+                              const int32_t* __restrict__ cell_loc, const double* __restrict__ cinv,
+                              const double* __restrict__ cg, int32_t* __restrict__ ai, double* __restrict__ av,
+                              float* __restrict__ av32, int32_t* __restrict__ ci, double* __restrict__ cv,
+                              float* __restrict__ cv32, int32_t* __restrict__ ei, double* __restrict__ ev,
+                              float* __restrict__ ev32) {
+    int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= n_loc) return;
+    for (int u = 0; u < 8; ++u) { ai[u * n_loc + r] = (int32_t)r; av[u * n_loc + r] = 0; av32[u * n_loc + r] = 0; }
+    for (int u = 0; u < 4; ++u) { ci[u * n_loc + r] = (int32_t)r; cv[u * n_loc + r] = 0; cv32[u * n_loc + r] = 0; }
+    for (int u = 0; u < 8; ++u) { ei[u * n_loc + r] = (int32_t)r; ev[u * n_loc + r] = 0; ev32[u * n_loc + r] = 0; }
+    if (!is_bub[r]) {
+        int q = 0;
+        for (int u = 0; u < maxc; ++u) {
+            int32_t c = row_cell[r * maxc + u];
+            if (c < 0) break;
+            int a = row_k[r * maxc + u];
+            for (int k = 0; k < 4; ++k, ++q) {
+                double g = cg[(int64_t)c * 32 + a * 4 + k];
+                ai[q * n_loc + r] = cell_loc[(int64_t)c * 12 + 8 + k];
+                av[q * n_loc + r] = g;
+                av32[q * n_loc + r] = (float)g;
+            }
+        }
+    } else {
+        int32_t c = row_cell[r * maxc];
+        int k = row_k[r * maxc] - 8;
+        for (int j = 0; j < 4; ++j) {
+            double d = cinv[(int64_t)c * 16 + k * 4 + j];
+            ci[j * n_loc + r] = cell_loc[(int64_t)c * 12 + 8 + j];
+            cv[j * n_loc + r] = d;
+            cv32[j * n_loc + r] = (float)d;
+        }
+        for (int a = 0; a < 8; ++a) {
+            int32_t e = cell_loc[(int64_t)c * 12 + a];
+            if (e < 0) continue;
+            double g = -cg[(int64_t)c * 32 + a * 4 + k];
+            ei[a * n_loc + r] = e;
+            ev[a * n_loc + r] = g;
+            ev32[a * n_loc + r] = (float)g;
+        }
+    }
+}
+
+__global__ void k_to_float(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (float)a[i];
+}
+
+// ---------------------------------------------------------------------------
+void assemble(thm_sys* s) {
+    const thm_mesh* m = s->m;
+    cudaStream_t st = s->st;
+    const int nb = m->dpc;
+    const double w2 = s->omega * s->omega;
+    const double kw = s->kappa * s->omega;
+    s->ref.alloc(3 * 144);
+    s->ref.zero(st);
+    THM_LAUNCH(THM_K_SETUP, st, k_ref_matrices<<<1, 256, 0, st>>>(m->order, nb, s->ref.p));
+    THM_CUDA(cudaGetLastError());
+    s->val64.alloc(m->n_slots);
+    s->val32.alloc(m->n_slots);
+    const int th = 256;
+    auto grid = [&](int64_t n) { return (unsigned)((n + th - 1) / th); };
+    THM_LAUNCH(THM_K_SETUP, st, k_assemble<<<grid(m->n_loc), th, 0, st>>>(m->n_loc, nb, m->maxc, s->ref.p, m->d_coords.p, m->d_cells.p,
+                                              m->d_cell_signs.p, m->d_cell_loc.p, s->mu_inv.p, w2,
+                                              m->d_slice_ptr.p, m->d_sell_col.p, m->d_sell_pad.p,
+                                              m->d_row_cell.p, m->d_row_k.p, s->val64.p, s->val32.p));
+    THM_CUDA(cudaGetLastError());
+    s->bg64.alloc(m->n_loc); s->bs64.alloc(m->n_loc);
+    s->bg32.alloc(m->n_loc); s->bs32.alloc(m->n_loc);
+    THM_LAUNCH(THM_K_SETUP, st, k_face_terms<<<grid(m->n_loc), th, 0, st>>>(m->n_loc, m->d_coords.p, m->d_edge_lo.p, m->d_edge_hi.p,
+                                                m->d_row_face_kind.p, m->d_row_face_fn.p,
+                                                m->d_row_face_edge.p, kw, s->bg64.p, s->bs64.p,
+                                                s->bg32.p, s->bs32.p));
+    THM_CUDA(cudaGetLastError());
+    s->if_mass.alloc(m->n_if > 0 ? m->n_if : 1);
+    if (m->n_if > 0) {
+        THM_LAUNCH(THM_K_SETUP, st, k_iface_mass<<<grid(m->n_if), th, 0, st>>>(m->n_if, m->d_coords.p, m->d_edge_lo.p, m->d_edge_hi.p,
+                                                   m->d_if_edge.p, m->d_if_fn.p, s->if_mass.p));
+        THM_CUDA(cudaGetLastError());
+    }
+    s->uD.alloc(m->n_dof);
+    s->uD.zero(st);
+    if (!m->dir_edges.empty()) {
+        THM_LAUNCH(THM_K_SETUP, st, k_dirichlet<<<grid((int64_t)m->dir_edges.size()), th, 0, st>>>(
+            (int64_t)m->dir_edges.size(), m->dim, m->order, m->d_dir_edges.p, m->d_coords.p, m->d_edge_lo.p,
+            m->d_edge_hi.p, s->omega, s->pol[0], s->pol[1], s->pol[2], s->pol[3], s->pol[4], s->pol[5],
+            s->dir[0], s->dir[1], s->dir[2], s->uD.p));
+        THM_CUDA(cudaGetLastError());
+    }
+    // condensed values (order 2) or a copy of P (order 1)
+    const int condensed = m->order == 2;
+    DArr<double> ccor;
+    s->cinv64.alloc(condensed ? m->n_cell * 16 : 1); s->cg64.alloc(condensed ? m->n_cell * 32 : 1);
+    s->cinv32.alloc(condensed ? m->n_cell * 16 : 1); s->cg32.alloc(condensed ? m->n_cell * 32 : 1);
+    ccor.alloc(condensed ? m->n_cell * 64 : 1);
+    if (condensed) {
+        DArr<int> bad;
+        bad.alloc(1);
+        bad.zero(st);
+        THM_LAUNCH(THM_K_SETUP, st, k_condense<<<grid(m->n_cell), th, 0, st>>>(m->n_cell, s->ref.p, m->d_coords.p, m->d_cells.p,
+                                                     m->d_cell_signs.p, s->mu_inv.p, w2, s->cinv64.p, s->cg64.p,
+                                                     ccor.p, s->cinv32.p, s->cg32.p, bad.p));
+        THM_CUDA(cudaGetLastError());
+        std::vector<int> hb;
+        bad.download(hb, st);
+        if (hb[0]) fail(THM_ESINGULAR, "a cell-bubble block of P_i is singular");
+    }
+    s->sval64.alloc(m->n_slots);
+    s->sval32.alloc(m->n_slots);
+    THM_LAUNCH(THM_K_SETUP, st, k_condensed_values<<<grid(m->n_loc), th, 0, st>>>(m->n_loc, nb, m->maxc, condensed, m->d_slice_ptr.p,
+                                                      m->d_sell_col.p, m->d_sell_pad.p, m->d_row_cell.p,
+                                                      m->d_row_k.p, m->d_cell_loc.p, m->d_loc_is_bub.p,
+                                                      s->val64.p, ccor.p, s->sval64.p, s->sval32.p));
+    THM_CUDA(cudaGetLastError());
+    s->cpl64.alloc(m->cpl_col.size());
+    s->cpl32.alloc(m->cpl_col.size());
+    THM_LAUNCH(THM_K_SETUP, st, k_gather_slots<<<grid((int64_t)m->cpl_col.size()), th, 0, st>>>((int64_t)m->cpl_col.size(), m->d_cpl_slot.p,
+                                                                   s->sval64.p, s->cpl64.p, s->cpl32.p));
+    THM_CUDA(cudaGetLastError());
+    if (condensed) {
+        const size_t n8 = 8 * (size_t)m->n_loc, n4 = 4 * (size_t)m->n_loc;
+        s->tab_ai.alloc(n8); s->tab_av64.alloc(n8); s->tab_av32.alloc(n8);
+        s->tab_ci.alloc(n4); s->tab_cv64.alloc(n4); s->tab_cv32.alloc(n4);
+        s->tab_ei.alloc(n8); s->tab_ev64.alloc(n8); s->tab_ev32.alloc(n8);
+        THM_LAUNCH(THM_K_SETUP, st, k_cond_tables<<<grid(m->n_loc), th, 0, st>>>(m->n_loc, m->maxc, m->d_loc_is_bub.p, m->d_row_cell.p,
+                                                     m->d_row_k.p, m->d_cell_loc.p, s->cinv64.p, s->cg64.p,
+                                                     s->tab_ai.p, s->tab_av64.p, s->tab_av32.p, s->tab_ci.p,
+                                                     s->tab_cv64.p, s->tab_cv32.p, s->tab_ei.p, s->tab_ev64.p,
+                                                     s->tab_ev32.p));
+        THM_CUDA(cudaGetLastError());
+    }
+    s->f_loc.alloc(m->n_loc);
+    THM_LAUNCH(THM_K_SETUP, st, k_lifting<<<grid(m->n_loc), th, 0, st>>>(m->n_loc, nb, m->maxc, s->ref.p, m->d_coords.p, m->d_cells.p,
+                                             m->d_cell_signs.p, m->d_cell_loc.p, m->d_cell_dofs.p,
+                                             s->mu_inv.p, w2, m->d_row_cell.p, m->d_row_k.p, s->uD.p,
+                                             s->f_loc.p));
+    THM_CUDA(cudaGetLastError());
+    THM_CUDA(cudaStreamSynchronize(st));
+}
+
+static void factor64(thm_sys* s) {
+    const thm_mesh* m = s->m;
+    cudaStream_t st = s->st;
+    s->fac64.alloc(m->fac_elems);
+    DArr<double> tmp;
+    const int64_t stride = 2 * (int64_t)m->max_m * m->max_m;
+    tmp.alloc((size_t)stride * m->n_sub);
+    DArr<int> perm, status;
+    perm.alloc((size_t)m->max_m * m->n_sub);
+    status.alloc(1);
+    status.zero(st);
+    const int threads = 512;
+    size_t smem = (size_t)m->max_m * sizeof(double) + threads * (sizeof(double) + sizeof(int));
+    if (smem > 48 * 1024)
+        THM_CUDA(cudaFuncSetAttribute(k_bt_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    THM_LAUNCH(THM_K_SETUP, st, k_bt_factor<<<m->n_sub, threads, smem, st>>>(m->d_subs.p, m->d_levels.p, m->d_slice_ptr.p, m->d_sell_col.p,
+                                                m->d_sell_pad.p, s->sval64.p, s->fac64.p, tmp.p, stride, perm.p,
+                                                m->max_m, status.p));
+    THM_CUDA(cudaGetLastError());
+    std::vector<int> hs;
+    status.download(hs, st);
+    if (hs[0] != 0)
+        fail(THM_ESINGULAR, "a diagonal block of P_i = A_i - omega^2 M_i is singular "
+                            "(omega^2 is a natural-boundary eigenvalue of a subdomain block)");
+}
+
+// The factorisation runs in FP64 for both modes (pivots and Schur updates in
+// FP64); the mixed mode stores the inverse blocks rounded to FP32.
+void ensure_factor(thm_sys* s, bool fp32) {
+    if (!s->fac64_ok) { factor64(s); s->fac64_ok = true; }
+    if (fp32 && !s->fac32_ok) {
+        s->fac32.alloc(s->fac64.n);
+        THM_LAUNCH(THM_K_SETUP, 0, k_to_float<<<(unsigned)((s->fac64.n + 255) / 256), 256, 0, s->st>>>((int64_t)s->fac64.n, s->fac64.p, s->fac32.p));
+        THM_CUDA(cudaGetLastError());
+        s->fac32_ok = true;
+    }
+}
+
+}  // namespace thm

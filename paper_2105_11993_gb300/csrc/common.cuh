@@ -1,0 +1,237 @@
+// Internal structures of the THM DDM-GMRES library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "thm.h"
+
+namespace thm {
+
+struct Error {
+    int code;
+    std::string msg;
+};
+
+[[noreturn]] void fail(int code, const std::string& msg);
+
+#define THM_CUDA(call)                                                                 \
+    do {                                                                               \
+        cudaError_t e_ = (call);                                                       \
+        if (e_ != cudaSuccess)                                                         \
+            ::thm::fail(e_ == cudaErrorMemoryAllocation ? THM_ENOMEM : THM_ECUDA,      \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));           \
+    } while (0)
+
+#define THM_REQUIRE(cond, msg)                                                         \
+    do {                                                                               \
+        if (!(cond)) ::thm::fail(THM_EINVAL, msg);                                     \
+    } while (0)
+
+// Owning device array.
+template <class T>
+struct DArr {
+    T* p = nullptr;
+    size_t n = 0;
+    DArr() = default;
+    DArr(const DArr&) = delete;
+    DArr& operator=(const DArr&) = delete;
+    ~DArr() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    void alloc(size_t count) {
+        release();
+        n = count;
+        if (count) THM_CUDA(cudaMalloc(&p, count * sizeof(T)));
+    }
+    void zero(cudaStream_t st) {
+        if (n) THM_CUDA(cudaMemsetAsync(p, 0, n * sizeof(T), st));
+    }
+    void upload(const std::vector<T>& h, cudaStream_t st = 0) {
+        alloc(h.size());
+        if (n) THM_CUDA(cudaMemcpyAsync(p, h.data(), n * sizeof(T), cudaMemcpyHostToDevice, st));
+    }
+    void download(std::vector<T>& h, cudaStream_t st = 0) const {
+        h.resize(n);
+        if (n) {
+            THM_CUDA(cudaMemcpyAsync(h.data(), p, n * sizeof(T), cudaMemcpyDeviceToHost, st));
+            THM_CUDA(cudaStreamSynchronize(st));
+        }
+    }
+};
+
+void prof_begin(int cls, cudaStream_t st);
+void prof_end(int cls, cudaStream_t st);
+void prof_set(unsigned mask);
+void prof_read(int cls, int64_t* launches, double* ms);
+
+// Every kernel launch of the library goes through THM_LAUNCH (launch count,
+// optional CUDA-event timing of its class).
+#define THM_LAUNCH(cls, st, ...)            \
+    do {                                    \
+        ::thm::prof_begin((cls), (st));     \
+        __VA_ARGS__;                        \
+        ::thm::prof_end((cls), (st));       \
+    } while (0)
+
+constexpr int SELL_C = 32;       // rows per SELL slice (one warp)
+constexpr int CHUNK = 2048;      // elements per reduction chunk of a segment
+
+// One block of the level-block-tridiagonal factorisation of P_i.
+struct Level {
+    int32_t start;    // first local row (absolute index into local vectors)
+    int32_t size;     // m_l
+    int32_t prev;     // m_{l-1} (0 for the first level of a subdomain)
+    int32_t next;     // m_{l+1} (0 for the last)
+    int64_t offW;     // m_l x m_l  inverse of the Schur block S_l (16-byte aligned)
+    // coupling blocks of S to level l-1 (E) and l+1 (F): m_l+1 row pointers
+    // (0-based, at cpl_ptr[eptr..]) and nz (column local to the neighbour
+    // level, value) entries at cpl_col/cpl_val[eoff..]; offsets 16-byte aligned
+    int64_t eptr, eoff, fptr, foff;
+    int32_t enz, fnz;
+};
+
+struct Sub {
+    int64_t off;      // first local row
+    int64_t n;        // free DOFs
+    int64_t ne;       // free edge DOFs (rows off .. off+ne-1); cell bubbles follow
+    int32_t lev0;     // first level
+    int32_t nlev;
+};
+
+// A contiguous piece of one segment, used for deterministic segmented reductions.
+struct Chunk {
+    int32_t seg;
+    int32_t pad;
+    int64_t begin;
+    int64_t end;
+};
+
+}  // namespace thm
+
+struct thm_mesh {
+    int dim = 0, order = 0, dpc = 0, epc = 0, max_block = 0;
+    int64_t n_vert = 0, n_cell = 0, n_bface = 0, n_edge = 0, n_dof = 0;
+    int n_sub = 0;
+    std::vector<double> coords;
+    std::vector<int64_t> cells;
+    std::vector<int32_t> cell_sub;
+    std::vector<int64_t> bfaces;
+    std::vector<uint8_t> btag;
+    std::vector<int64_t> edge_lo, edge_hi;          // sorted (lo, hi)
+    std::vector<int64_t> cell_dofs;                 // [n_cell][dpc]
+    std::vector<int8_t> cell_signs;                 // [n_cell][dpc]
+    std::vector<uint8_t> is_dir;                    // [n_dof]
+    std::vector<int64_t> dir_edges;                 // edges carrying Dirichlet DOFs
+
+    // local (per-subdomain, free DOFs) structure
+    int64_t n_loc = 0;
+    std::vector<thm::Sub> subs;
+    std::vector<int64_t> loc_gdof;                  // [n_loc]
+    std::vector<int32_t> loc_sub;                   // [n_loc]
+    std::vector<int32_t> cell_loc;                  // [n_cell][dpc] local row or -1
+    // SELL-32 pattern of P_i (all subdomains), columns are local indices
+    int64_t n_slices = 0, n_slots = 0;
+    std::vector<int64_t> slice_ptr;                 // [n_slices+1]
+    std::vector<int32_t> sell_col;                  // [n_slots]; padding = own row
+    std::vector<uint8_t> sell_pad;                  // [n_slots] 1 = padding
+    // assembly plan: cells holding each local row (ascending), <= maxc
+    int maxc = 0;
+    std::vector<int32_t> row_cell, row_k;           // [n_loc][maxc]
+    // face terms (2-D: one edge per row at most)
+    std::vector<int8_t> row_face_kind;              // 0 none, 1 Gamma^inf, 2 Sigma
+    std::vector<int8_t> row_face_fn;                // 0 Whitney trace, 1 gradient trace
+    std::vector<int32_t> row_face_edge;
+    // levels of the block-tridiagonal factorisation
+    std::vector<thm::Level> levels;
+    int max_m = 0;
+    int64_t fac_elems = 0;
+    // level couplings of S as compact CSR lists (columns local to the
+    // neighbouring level; slot = position of the value in the SELL arrays)
+    std::vector<int32_t> cpl_ptr, cpl_col;
+    std::vector<int64_t> cpl_slot;                  // -1 for alignment padding
+    int max_cnz = 0;                                // largest coupling block
+    int64_t max_ne = 0;                             // largest number of edge DOFs of a subdomain
+    // reduction chunks over subdomains
+    std::vector<thm::Chunk> chunks;
+    // interface entries (directed pairs i <- j, one per free DOF on Sigma_ij)
+    int64_t n_if = 0;
+    std::vector<int32_t> if_recv, if_send, if_rowi, if_rowj, if_partner, if_edge;
+    std::vector<int8_t> if_fn;
+    std::vector<int64_t> if_gdof;
+    std::vector<int64_t> rowg_ptr;                  // [n_loc+1] local row -> entries received
+    std::vector<int32_t> rowg_idx;
+    // global <-> local
+    std::vector<int32_t> owner_loc;                 // [n_dof] lowest-subdomain copy, -1 Dirichlet
+    std::vector<int64_t> copy_ptr;                  // [n_dof+1]
+    std::vector<int32_t> copy_idx;
+    std::vector<uint8_t> loc_is_owner;              // [n_loc]
+    std::vector<uint8_t> loc_is_bub;                // [n_loc] order-2 cell bubble
+
+    // device mirrors
+    thm::DArr<double> d_coords;
+    thm::DArr<int32_t> d_cells, d_cell_dofs, d_cell_loc, d_sell_col, d_row_cell, d_row_k;
+    thm::DArr<int64_t> d_edge_lo, d_edge_hi, d_slice_ptr, d_dir_edges, d_loc_gdof, d_rowg_ptr,
+        d_copy_ptr;
+    thm::DArr<int8_t> d_cell_signs, d_row_face_kind, d_row_face_fn, d_if_fn;
+    thm::DArr<uint8_t> d_sell_pad, d_loc_is_owner, d_loc_is_bub;
+    thm::DArr<int32_t> d_row_face_edge, d_if_rowi, d_if_rowj, d_if_partner, d_if_edge, d_rowg_idx,
+        d_owner_loc, d_copy_idx, d_loc_sub;
+    thm::DArr<thm::Level> d_levels;
+    thm::DArr<int32_t> d_cpl_ptr, d_cpl_col;
+    thm::DArr<int64_t> d_cpl_slot;
+    thm::DArr<thm::Sub> d_subs;
+    thm::DArr<thm::Chunk> d_chunks;
+};
+
+namespace thm { struct Work; }
+
+// Assembled system of one (mesh, mu^{-1}, omega, kappa, E^inc).
+struct thm_sys {
+    const thm_mesh* m = nullptr;
+    cudaStream_t st = 0;
+    double omega = 0, kappa = 0;
+    double pol[6] = {0};   // complex [dim]
+    double dir[3] = {0};
+    thm::DArr<double> mu_inv;          // [n_cell]
+    thm::DArr<double> ref;             // reference matrices (see assemble.cu)
+    thm::DArr<double> val64;           // SELL values of P_i, FP64
+    thm::DArr<float> val32;            // same, FP32
+    thm::DArr<double> bg64, bs64;      // kappa*omega * diagonal face masses: Gamma^inf, Sigma
+    thm::DArr<float> bg32, bs32;
+    thm::DArr<double> if_mass;         // [n_if] tangential mass of each interface entry
+    thm::DArr<double2> uD;             // [n_dof] Dirichlet values
+    thm::DArr<double2> f_loc;          // [n_loc] lifting right-hand side
+    // block-tridiagonal factors of P_i (lazily built per precision)
+    bool fac64_ok = false, fac32_ok = false;
+    thm::DArr<double> fac64;
+    thm::DArr<float> fac32;
+    // static condensation of order-2 cell bubbles: S = P_EE - P_EI D^{-1} P_IE
+    thm::DArr<double> sval64;          // SELL values of S on edge rows/columns (P elsewhere 0)
+    thm::DArr<float> sval32;
+    thm::DArr<double> cinv64, cg64;    // per cell: D_II^{-1} (4x4), G = P_EI D_II^{-1} (8x4)
+    thm::DArr<float> cinv32, cg32;
+    thm::DArr<double> cpl64;           // values of the level coupling lists
+    thm::DArr<float> cpl32;
+    // order-2 gather tables (structure of arrays, [8][n_loc]): for an edge row
+    // the <= 8 (bubble, G entry) pairs of r_E - G r_I; for a bubble row the 4
+    // (bubble, D^{-1} entry) and 8 (edge, -G entry) pairs of D^{-1} r_I - G^T x_E
+    thm::DArr<int32_t> tab_ai, tab_ci, tab_ei;
+    thm::DArr<double> tab_av64, tab_cv64, tab_ev64;
+    thm::DArr<float> tab_av32, tab_cv32, tab_ev32;
+    // solver workspace (allocated on first solve, see solve.cu)
+    thm::Work* w = nullptr;
+    ~thm_sys();
+};
+
+namespace thm {
+void build_mesh(thm_mesh* m);
+void assemble(thm_sys* s);
+void ensure_factor(thm_sys* s, bool fp32);
+}  // namespace thm

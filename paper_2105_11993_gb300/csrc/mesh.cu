@@ -1,0 +1,605 @@
+// Mesh numbering, orientation signs and the subdomain structure (Section 2:
+// the space N_h^p; Section 3.1: the partition into Omega_i and Sigma_ij).
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+#include <queue>
+
+#include "common.cuh"
+
+namespace thm {
+
+// Local edges of a tensor-order quad / hex: (a -> b) along +xi, +eta, +zeta.
+__constant__ int c_edges2[4][2] = {{0, 1}, {2, 3}, {0, 2}, {1, 3}};
+__constant__ int c_edges3[12][2] = {{0, 1}, {2, 3}, {4, 5}, {6, 7}, {0, 2}, {1, 3},
+                                    {4, 6}, {5, 7}, {0, 4}, {1, 5}, {2, 6}, {3, 7}};
+static const int h_edges2[4][2] = {{0, 1}, {2, 3}, {0, 2}, {1, 3}};
+static const int h_edges3[12][2] = {{0, 1}, {2, 3}, {4, 5}, {6, 7}, {0, 2}, {1, 3},
+                                    {4, 6}, {5, 7}, {0, 4}, {1, 5}, {2, 6}, {3, 7}};
+
+// Edge id of (a, b) by binary search in the lexicographically sorted table.
+__device__ __forceinline__ int64_t find_edge(const int64_t* lo, const int64_t* hi, int64_t n,
+                                             int64_t a, int64_t b) {
+    int64_t x = a < b ? a : b, y = a < b ? b : a;
+    int64_t l = 0, r = n - 1;
+    while (l <= r) {
+        int64_t mid = (l + r) >> 1;
+        int64_t ml = lo[mid], mh = hi[mid];
+        if (ml == x && mh == y) return mid;
+        if (ml < x || (ml == x && mh < y)) l = mid + 1;
+        else r = mid - 1;
+    }
+    return -1;
+}
+
+// DOF ids and orientation signs of every cell.  Whitney DOF of a local edge
+// (a -> b) has sign +1 iff id(a) < id(b); order-2 gradient and bubble DOFs
+// carry no sign.
+__global__ void k_cell_dofs(int dim, int order, int64_t n_cell, const int32_t* __restrict__ cells,
+                            const int64_t* __restrict__ elo, const int64_t* __restrict__ ehi,
+                            int64_t n_edge, int32_t* __restrict__ dofs, int8_t* __restrict__ signs,
+                            int* __restrict__ bad) {
+    int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= n_cell) return;
+    const int nv = dim == 2 ? 4 : 8;
+    const int ne = dim == 2 ? 4 : 12;
+    const int dpc = (order == 1) ? ne : 12;
+    const int32_t* cv = cells + c * nv;
+    for (int k = 0; k < ne; ++k) {
+        int a = dim == 2 ? c_edges2[k][0] : c_edges3[k][0];
+        int b = dim == 2 ? c_edges2[k][1] : c_edges3[k][1];
+        int64_t va = cv[a], vb = cv[b];
+        int64_t e = find_edge(elo, ehi, n_edge, va, vb);
+        if (e < 0) { atomicExch(bad, 1); e = 0; }
+        int8_t s = va < vb ? 1 : -1;
+        if (order == 1) {
+            dofs[c * dpc + k] = (int32_t)e;
+            signs[c * dpc + k] = s;
+        } else {
+            dofs[c * dpc + 2 * k] = (int32_t)(2 * e);
+            signs[c * dpc + 2 * k] = s;
+            dofs[c * dpc + 2 * k + 1] = (int32_t)(2 * e + 1);
+            signs[c * dpc + 2 * k + 1] = 1;
+        }
+    }
+    if (order == 2) {
+        for (int k = 0; k < 4; ++k) {
+            dofs[c * dpc + 8 + k] = (int32_t)(2 * n_edge + 4 * c + k);
+            signs[c * dpc + 8 + k] = 1;
+        }
+    }
+}
+
+static int64_t host_find_edge(const thm_mesh* m, int64_t a, int64_t b) {
+    int64_t x = std::min(a, b), y = std::max(a, b);
+    auto it = std::lower_bound(m->edge_lo.begin(), m->edge_lo.end(), x);
+    int64_t i0 = it - m->edge_lo.begin();
+    auto it2 = std::upper_bound(m->edge_lo.begin(), m->edge_lo.end(), x);
+    int64_t i1 = it2 - m->edge_lo.begin();
+    auto jt = std::lower_bound(m->edge_hi.begin() + i0, m->edge_hi.begin() + i1, y);
+    int64_t j = jt - m->edge_hi.begin();
+    if (j < i1 && m->edge_hi[j] == y) return j;
+    return -1;
+}
+
+static void check_axis_aligned(const thm_mesh* m) {
+    const int d = m->dim, nv = d == 2 ? 4 : 8;
+    for (int64_t c = 0; c < m->n_cell; ++c) {
+        const int64_t* cv = &m->cells[c * nv];
+        auto X = [&](int v, int k) { return m->coords[cv[v] * d + k]; };
+        double ax[3][3];
+        int axes = d;
+        int corner[3] = {1, 2, 4};
+        for (int a = 0; a < axes; ++a)
+            for (int k = 0; k < d; ++k) ax[a][k] = X(corner[a], k) - X(0, k);
+        double len[3];
+        for (int a = 0; a < axes; ++a) {
+            len[a] = 0;
+            int nz = 0;
+            for (int k = 0; k < d; ++k) {
+                len[a] += ax[a][k] * ax[a][k];
+                nz += ax[a][k] != 0.0;
+            }
+            len[a] = std::sqrt(len[a]);
+            THM_REQUIRE(nz == 1 && len[a] > 0, "cell " + std::to_string(c) + " is not axis-aligned");
+        }
+        // every corner = v0 + sum of the selected axis vectors
+        for (int v = 0; v < nv; ++v)
+            for (int k = 0; k < d; ++k) {
+                double x = X(0, k);
+                for (int a = 0; a < axes; ++a)
+                    if ((v >> a) & 1) x += ax[a][k];
+                THM_REQUIRE(std::fabs(x - X(v, k)) <= 1e-12 * (len[0] + std::fabs(x)),
+                            "cell " + std::to_string(c) + " is not a tensor-order box");
+            }
+    }
+}
+
+void build_mesh(thm_mesh* m) {
+    const int d = m->dim, nv = d == 2 ? 4 : 8;
+    const int ne = d == 2 ? 4 : 12;
+    m->epc = ne;
+    m->dpc = (m->order == 1) ? ne : 12;
+    check_axis_aligned(m);
+
+    // ---- global edges: distinct (lo, hi) pairs in lexicographic order
+    std::vector<std::pair<int64_t, int64_t>> keys;
+    keys.reserve(m->n_cell * ne);
+    for (int64_t c = 0; c < m->n_cell; ++c)
+        for (int k = 0; k < ne; ++k) {
+            int a = d == 2 ? h_edges2[k][0] : h_edges3[k][0];
+            int b = d == 2 ? h_edges2[k][1] : h_edges3[k][1];
+            int64_t va = m->cells[c * nv + a], vb = m->cells[c * nv + b];
+            keys.emplace_back(std::min(va, vb), std::max(va, vb));
+        }
+    std::sort(keys.begin(), keys.end());
+    keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
+    m->n_edge = (int64_t)keys.size();
+    m->edge_lo.resize(m->n_edge);
+    m->edge_hi.resize(m->n_edge);
+    for (int64_t e = 0; e < m->n_edge; ++e) {
+        m->edge_lo[e] = keys[e].first;
+        m->edge_hi[e] = keys[e].second;
+    }
+    keys.clear();
+    keys.shrink_to_fit();
+    m->n_dof = m->order == 1 ? m->n_edge : 2 * m->n_edge + 4 * m->n_cell;
+    THM_REQUIRE(m->n_dof < (int64_t)INT32_MAX, "more than 2^31 DOFs");
+
+    // ---- per-cell DOFs and signs on the device
+    std::vector<int32_t> cells32(m->cells.begin(), m->cells.end());
+    m->d_cells.upload(cells32);
+    m->d_coords.upload(m->coords);
+    m->d_edge_lo.upload(m->edge_lo);
+    m->d_edge_hi.upload(m->edge_hi);
+    m->d_cell_dofs.alloc(m->n_cell * m->dpc);
+    m->d_cell_signs.alloc(m->n_cell * m->dpc);
+    DArr<int> bad;
+    bad.alloc(1);
+    bad.zero(0);
+    int th = 256;
+    THM_LAUNCH(THM_K_SETUP, 0, k_cell_dofs<<<(unsigned)((m->n_cell + th - 1) / th), th>>>(
+        d, m->order, m->n_cell, m->d_cells.p, m->d_edge_lo.p, m->d_edge_hi.p, m->n_edge,
+        m->d_cell_dofs.p, m->d_cell_signs.p, bad.p));
+    THM_CUDA(cudaGetLastError());
+    std::vector<int> hbad;
+    bad.download(hbad);
+    THM_REQUIRE(hbad[0] == 0, "internal: edge lookup failed");
+    std::vector<int32_t> cd32;
+    m->d_cell_dofs.download(cd32);
+    m->cell_dofs.assign(cd32.begin(), cd32.end());
+    m->d_cell_signs.download(m->cell_signs);
+    const int dpc = m->dpc;
+
+    // ---- edge -> cells (first two) and edge of each (cell, local edge)
+    std::vector<int32_t> ecell(m->n_edge * 2, -1);
+    auto edge_of = [&](int64_t c, int k) -> int64_t {
+        int64_t dof = m->cell_dofs[c * dpc + (m->order == 1 ? k : 2 * k)];
+        return m->order == 1 ? dof : dof / 2;
+    };
+    if (d == 2) {
+        for (int64_t c = 0; c < m->n_cell; ++c)
+            for (int k = 0; k < ne; ++k) {
+                int64_t e = edge_of(c, k);
+                if (ecell[2 * e] < 0) ecell[2 * e] = (int32_t)c;
+                else ecell[2 * e + 1] = (int32_t)c;
+            }
+    }
+
+    // ---- boundary faces: Dirichlet DOFs and impedance edges
+    m->is_dir.assign(m->n_dof, 0);
+    std::vector<int8_t> edge_kind(m->n_edge, 0);   // 1 = Gamma^inf face edge (2-D)
+    const int fv = d == 2 ? 2 : 4;
+    for (int64_t f = 0; f < m->n_bface; ++f) {
+        const int64_t* v = &m->bfaces[f * fv];
+        for (int k = 0; k < fv; ++k)
+            THM_REQUIRE(v[k] >= 0 && v[k] < m->n_vert, "bface vertex out of range");
+        std::vector<int64_t> es;
+        if (d == 2) {
+            es.push_back(host_find_edge(m, v[0], v[1]));
+        } else {
+            for (int k = 0; k < 4; ++k) es.push_back(host_find_edge(m, v[h_edges2[k][0]], v[h_edges2[k][1]]));
+        }
+        for (int64_t e : es) THM_REQUIRE(e >= 0, "bface " + std::to_string(f) + " is not a cell face");
+        if (d == 2) THM_REQUIRE(ecell[2 * es[0] + 1] < 0, "bface " + std::to_string(f) + " is interior");
+        if (m->btag[f] == THM_TAG_DIRICHLET) {
+            for (int64_t e : es) {
+                if (m->order == 1) m->is_dir[e] = 1;
+                else { m->is_dir[2 * e] = 1; m->is_dir[2 * e + 1] = 1; }
+                m->dir_edges.push_back(e);
+            }
+        } else if (m->btag[f] == THM_TAG_IMPEDANCE) {
+            if (d == 2) edge_kind[es[0]] = 1;
+        } else {
+            THM_REQUIRE(m->btag[f] == THM_TAG_NATURAL, "unknown boundary tag");
+        }
+    }
+    std::sort(m->dir_edges.begin(), m->dir_edges.end());
+    m->dir_edges.erase(std::unique(m->dir_edges.begin(), m->dir_edges.end()), m->dir_edges.end());
+
+    // ---- subdomains
+    const int ns = m->n_sub;
+    std::vector<std::vector<int64_t>> sub_cells(ns);
+    for (int64_t c = 0; c < m->n_cell; ++c) sub_cells[m->cell_sub[c]].push_back(c);
+    for (int s = 0; s < ns; ++s) THM_REQUIRE(!sub_cells[s].empty(), "empty subdomain " + std::to_string(s));
+
+    // DOF "position" along the sweep axis (last coordinate): edge midpoint or cell centre
+    auto dof_pos = [&](int64_t c, int k) -> double {
+        int64_t dof = m->cell_dofs[c * dpc + k];
+        if (m->order == 2 && k >= 8) {
+            double y = 0;
+            for (int v = 0; v < nv; ++v) y += m->coords[m->cells[c * nv + v] * d + d - 1];
+            return y / nv;
+        }
+        int64_t e = m->order == 1 ? dof : dof / 2;
+        return 0.5 * (m->coords[m->edge_lo[e] * d + d - 1] + m->coords[m->edge_hi[e] * d + d - 1]);
+    };
+
+    m->cell_loc.assign(m->n_cell * dpc, -1);
+    m->subs.resize(ns);
+    m->loc_gdof.clear();
+    m->loc_sub.clear();
+    m->levels.clear();
+    std::vector<std::vector<int32_t>> row_cols_all;   // per local row: sorted local columns
+    m->maxc = d == 2 ? 2 : 4;
+    std::vector<int32_t> row_cell_v, row_k_v;
+    int64_t off = 0;
+    for (int s = 0; s < ns; ++s) {
+        const auto& cs = sub_cells[s];
+        // free DOFs of the subdomain
+        std::vector<int64_t> gd;
+        for (int64_t c : cs)
+            for (int k = 0; k < dpc; ++k) {
+                int64_t g = m->cell_dofs[c * dpc + k];
+                if (!m->is_dir[g]) gd.push_back(g);
+            }
+        std::sort(gd.begin(), gd.end());
+        gd.erase(std::unique(gd.begin(), gd.end()), gd.end());
+        const int64_t n = (int64_t)gd.size();
+        THM_REQUIRE(n > 0, "subdomain without free DOFs");
+        auto lid = [&](int64_t g) { return (int64_t)(std::lower_bound(gd.begin(), gd.end(), g) - gd.begin()); };
+        // adjacency through cells, cells of each DOF, position
+        std::vector<std::vector<int32_t>> adj(n);
+        std::vector<std::vector<std::pair<int32_t, int32_t>>> dcells(n);
+        std::vector<double> pos(n, 0.0);
+        for (int64_t c : cs) {
+            int32_t loc[12];
+            for (int k = 0; k < dpc; ++k) {
+                int64_t g = m->cell_dofs[c * dpc + k];
+                loc[k] = m->is_dir[g] ? -1 : (int32_t)lid(g);
+                if (loc[k] >= 0) {
+                    dcells[loc[k]].emplace_back((int32_t)c, k);
+                    pos[loc[k]] = dof_pos(c, k);
+                }
+            }
+            for (int a = 0; a < dpc; ++a)
+                if (loc[a] >= 0)
+                    for (int b = 0; b < dpc; ++b)
+                        if (loc[b] >= 0) adj[loc[a]].push_back(loc[b]);
+        }
+        for (auto& v : adj) {
+            std::sort(v.begin(), v.end());
+            v.erase(std::unique(v.begin(), v.end()), v.end());
+        }
+        // Order-2 cell bubbles are condensed cell by cell and ordered last;
+        // the block-tridiagonal levels cover the edge DOFs only.
+        std::vector<uint8_t> bub(n, 0);
+        int64_t nbub = 0;
+        if (m->order == 2)
+            for (int64_t i = 0; i < n; ++i)
+                if (gd[i] >= 2 * m->n_edge) { bub[i] = 1; ++nbub; }
+        // BFS levels from the DOFs at the smallest sweep coordinate
+        double pmin = 1e300, pmax = -1e300;
+        for (int64_t i = 0; i < n; ++i)
+            if (!bub[i]) { pmin = std::min(pmin, pos[i]); pmax = std::max(pmax, pos[i]); }
+        double tol = 1e-9 * (pmax - pmin + 1.0);
+        std::vector<int32_t> lev(n, -1);
+        std::vector<int32_t> frontier;
+        for (int64_t i = 0; i < n; ++i)
+            if (!bub[i] && pos[i] <= pmin + tol) { lev[i] = 0; frontier.push_back((int32_t)i); }
+        int nl = 1;
+        auto bfs = [&](std::vector<int32_t>& fr) {
+            while (!fr.empty()) {
+                std::vector<int32_t> nxt;
+                for (int32_t i : fr)
+                    for (int32_t j : adj[i])
+                        if (!bub[j] && lev[j] < 0) { lev[j] = nl; nxt.push_back(j); }
+                if (!nxt.empty()) ++nl;
+                fr.swap(nxt);
+            }
+        };
+        bfs(frontier);
+        for (int64_t i = 0; i < n; ++i)
+            if (!bub[i] && lev[i] < 0) {       // disconnected piece: start a new BFS there
+                std::vector<int32_t> fr{(int32_t)i};
+                lev[i] = nl++;
+                bfs(fr);
+            }
+        // merge consecutive BFS levels into blocks of <= max_block DOFs
+        std::vector<int64_t> cnt(nl, 0);
+        for (int64_t i = 0; i < n; ++i)
+            if (!bub[i]) cnt[lev[i]]++;
+        std::vector<int32_t> blk_of(nl);
+        std::vector<int64_t> bsize;
+        for (int l = 0; l < nl; ++l) {
+            if (cnt[l] == 0) { blk_of[l] = bsize.empty() ? 0 : (int32_t)bsize.size() - 1; continue; }
+            if (!bsize.empty() && bsize.back() + cnt[l] <= m->max_block) {
+                bsize.back() += cnt[l];
+            } else {
+                bsize.push_back(cnt[l]);
+            }
+            blk_of[l] = (int32_t)bsize.size() - 1;
+        }
+        // local order: (block, global id) for edge DOFs, then bubbles by global id
+        std::vector<int64_t> order(n);
+        std::iota(order.begin(), order.end(), 0);
+        auto key = [&](int64_t a) -> int64_t { return bub[a] ? (int64_t)INT32_MAX : blk_of[lev[a]]; };
+        std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return key(a) < key(b); });
+        std::vector<int32_t> newid(n);
+        for (int64_t i = 0; i < n; ++i) newid[order[i]] = (int32_t)i;
+        m->subs[s].off = off;
+        m->subs[s].n = n;
+        m->subs[s].ne = n - nbub;
+        m->subs[s].lev0 = (int32_t)m->levels.size();
+        m->subs[s].nlev = (int32_t)bsize.size();
+        int32_t st = (int32_t)off;
+        for (size_t b = 0; b < bsize.size(); ++b) {
+            Level L{};
+            L.start = st;
+            L.size = (int32_t)bsize[b];
+            st += L.size;
+            m->levels.push_back(L);
+        }
+        for (int64_t i = 0; i < n; ++i) {
+            int64_t o = order[i];
+            m->loc_gdof.push_back(gd[o]);
+            m->loc_sub.push_back(s);
+            std::vector<int32_t> cols;
+            for (int32_t j : adj[o]) cols.push_back((int32_t)(off + newid[j]));
+            std::sort(cols.begin(), cols.end());
+            row_cols_all.push_back(std::move(cols));
+            auto dc = dcells[o];
+            std::sort(dc.begin(), dc.end());
+            THM_REQUIRE((int)dc.size() <= m->maxc, "internal: too many cells per DOF");
+            for (int t = 0; t < m->maxc; ++t) {
+                row_cell_v.push_back(t < (int)dc.size() ? dc[t].first : -1);
+                row_k_v.push_back(t < (int)dc.size() ? dc[t].second : -1);
+            }
+        }
+        for (int64_t c : cs)
+            for (int k = 0; k < dpc; ++k) {
+                int64_t g = m->cell_dofs[c * dpc + k];
+                m->cell_loc[c * dpc + k] = m->is_dir[g] ? -1 : (int32_t)(off + newid[lid(g)]);
+            }
+        off += n;
+    }
+    m->n_loc = off;
+    m->row_cell.swap(row_cell_v);
+    m->row_k.swap(row_k_v);
+
+    // ---- level offsets into the factor storage
+    m->max_m = 0;
+    int64_t fo = 0;
+    for (int s = 0; s < ns; ++s) {
+        auto& S = m->subs[s];
+        for (int l = 0; l < S.nlev; ++l) {
+            Level& L = m->levels[S.lev0 + l];
+            L.prev = l > 0 ? m->levels[S.lev0 + l - 1].size : 0;
+            L.next = l + 1 < S.nlev ? m->levels[S.lev0 + l + 1].size : 0;
+            m->max_m = std::max(m->max_m, L.size);
+            L.offW = fo;
+            fo += ((int64_t)L.size * L.size + 3) / 4 * 4;     // keep every block 16-byte aligned
+        }
+    }
+    m->fac_elems = fo + 4;
+
+    // ---- SELL-32 pattern
+    m->n_slices = (m->n_loc + SELL_C - 1) / SELL_C;
+    m->slice_ptr.assign(m->n_slices + 1, 0);
+    for (int64_t sl = 0; sl < m->n_slices; ++sl) {
+        size_t w = 0;
+        for (int64_t r = sl * SELL_C; r < std::min<int64_t>(m->n_loc, (sl + 1) * SELL_C); ++r)
+            w = std::max(w, row_cols_all[r].size());
+        m->slice_ptr[sl + 1] = m->slice_ptr[sl] + (int64_t)w * SELL_C;
+    }
+    m->n_slots = m->slice_ptr[m->n_slices];
+    m->sell_col.assign(m->n_slots, 0);
+    m->sell_pad.assign(m->n_slots, 1);
+    for (int64_t sl = 0; sl < m->n_slices; ++sl) {
+        int64_t w = (m->slice_ptr[sl + 1] - m->slice_ptr[sl]) / SELL_C;
+        for (int lane = 0; lane < SELL_C; ++lane) {
+            int64_t r = sl * SELL_C + lane;
+            for (int64_t t = 0; t < w; ++t) {
+                int64_t idx = m->slice_ptr[sl] + t * SELL_C + lane;
+                if (r < m->n_loc && t < (int64_t)row_cols_all[r].size()) {
+                    m->sell_col[idx] = row_cols_all[r][t];
+                    m->sell_pad[idx] = 0;
+                } else {
+                    m->sell_col[idx] = (int32_t)std::min<int64_t>(r, m->n_loc - 1);
+                }
+            }
+        }
+    }
+    // ---- level coupling lists: for every level row, its S entries in the
+    //      previous level (E_l) and in the next level (F_l), one 16-byte
+    //      aligned block per (level, side)
+    m->cpl_ptr.clear(); m->cpl_col.clear(); m->cpl_slot.clear();
+    m->max_cnz = 0;
+    m->max_ne = 0;
+    auto pad4i = [](std::vector<int32_t>& v) { while (v.size() % 4) v.push_back(0); };
+    for (int s = 0; s < ns; ++s) {
+        const auto& S = m->subs[s];
+        m->max_ne = std::max<int64_t>(m->max_ne, S.ne);
+        for (int l = 0; l < S.nlev; ++l) {
+            Level& L = m->levels[S.lev0 + l];
+            for (int side = 0; side < 2; ++side) {
+                int64_t c0 = side == 0 ? (int64_t)L.start - L.prev : (int64_t)L.start + L.size;
+                int64_t c1 = side == 0 ? (int64_t)L.start : c0 + L.next;
+                pad4i(m->cpl_ptr);
+                while (m->cpl_col.size() % 4) { m->cpl_col.push_back(0); m->cpl_slot.push_back(-1); }
+                int64_t p0 = (int64_t)m->cpl_ptr.size(), q0 = (int64_t)m->cpl_col.size();
+                for (int i = 0; i <= L.size; ++i) {
+                    m->cpl_ptr.push_back((int32_t)(m->cpl_col.size() - q0));
+                    if (i == L.size) break;
+                    int64_t r = L.start + i;
+                    int64_t sl = r / SELL_C;
+                    int lane = (int)(r % SELL_C);
+                    int64_t w = (m->slice_ptr[sl + 1] - m->slice_ptr[sl]) / SELL_C;
+                    for (int64_t t = 0; t < w; ++t) {
+                        int64_t idx = m->slice_ptr[sl] + t * SELL_C + lane;
+                        if (m->sell_pad[idx]) continue;
+                        int64_t c = m->sell_col[idx];
+                        if (c >= c0 && c < c1) {
+                            m->cpl_col.push_back((int32_t)(c - c0));
+                            m->cpl_slot.push_back(idx);
+                        }
+                    }
+                }
+                int32_t nz = (int32_t)(m->cpl_col.size() - q0);
+                m->max_cnz = std::max(m->max_cnz, nz);
+                if (side == 0) { L.eptr = p0; L.eoff = q0; L.enz = nz; }
+                else { L.fptr = p0; L.foff = q0; L.fnz = nz; }
+            }
+        }
+    }
+    pad4i(m->cpl_ptr);
+    for (int k = 0; k < 8; ++k) { m->cpl_ptr.push_back(0); m->cpl_col.push_back(0); m->cpl_slot.push_back(-1); }
+    THM_REQUIRE(m->cpl_col.size() < (size_t)INT32_MAX, "coupling lists too large");
+    row_cols_all.clear();
+
+    // ---- reduction chunks
+    m->chunks.clear();
+    for (int s = 0; s < ns; ++s) {
+        const auto& S = m->subs[s];
+        for (int64_t b = 0; b < S.n; b += CHUNK) {
+            Chunk ch{};
+            ch.seg = s;
+            ch.begin = S.off + b;
+            ch.end = S.off + std::min<int64_t>(S.n, b + CHUNK);
+            m->chunks.push_back(ch);
+        }
+    }
+
+    // ---- global <-> local maps
+    m->owner_loc.assign(m->n_dof, -1);
+    std::vector<int64_t> ccount(m->n_dof + 1, 0);
+    for (int64_t r = 0; r < m->n_loc; ++r) ccount[m->loc_gdof[r] + 1]++;
+    m->copy_ptr.assign(m->n_dof + 1, 0);
+    for (int64_t g = 0; g < m->n_dof; ++g) m->copy_ptr[g + 1] = m->copy_ptr[g] + ccount[g + 1];
+    m->copy_idx.assign(m->n_loc, 0);
+    std::vector<int64_t> fill(m->copy_ptr.begin(), m->copy_ptr.end() - 1);
+    for (int64_t r = 0; r < m->n_loc; ++r) m->copy_idx[fill[m->loc_gdof[r]]++] = (int32_t)r;  // ascending subdomain
+    m->loc_is_owner.assign(m->n_loc, 0);
+    for (int64_t g = 0; g < m->n_dof; ++g)
+        if (m->copy_ptr[g + 1] > m->copy_ptr[g]) {
+            m->owner_loc[g] = m->copy_idx[m->copy_ptr[g]];
+            m->loc_is_owner[m->owner_loc[g]] = 1;
+        } else {
+            THM_REQUIRE(m->is_dir[g], "internal: free DOF without a subdomain copy");
+        }
+
+    // ---- faces (2-D): impedance and interface edges, interface entries
+    m->row_face_kind.assign(m->n_loc, 0);
+    m->row_face_fn.assign(m->n_loc, 0);
+    m->row_face_edge.assign(m->n_loc, -1);
+    THM_REQUIRE(d == 2, "3-D meshes are not supported by this build of the library");
+    struct IfE { int32_t i, j; int64_t g; int32_t edge; int8_t fn; };
+    std::vector<IfE> ifs;
+    for (int64_t r = 0; r < m->n_loc; ++r) {
+        int64_t g = m->loc_gdof[r];
+        if (m->order == 2 && g >= 2 * m->n_edge) continue;       // bubble
+        int64_t e = m->order == 1 ? g : g / 2;
+        int8_t fn = (m->order == 2 && (g & 1)) ? 1 : 0;
+        int32_t c0 = ecell[2 * e], c1 = ecell[2 * e + 1];
+        int s = m->loc_sub[r];
+        if (c1 < 0) {
+            if (edge_kind[e] == 1) {
+                m->row_face_kind[r] = 1; m->row_face_fn[r] = fn; m->row_face_edge[r] = (int32_t)e;
+            }
+        } else if (m->cell_sub[c0] != m->cell_sub[c1]) {
+            int other = m->cell_sub[c0] == s ? m->cell_sub[c1] : m->cell_sub[c0];
+            m->row_face_kind[r] = 2; m->row_face_fn[r] = fn; m->row_face_edge[r] = (int32_t)e;
+            ifs.push_back({s, other, g, (int32_t)e, fn});
+        }
+    }
+    std::sort(ifs.begin(), ifs.end(), [](const IfE& a, const IfE& b) {
+        if (a.i != b.i) return a.i < b.i;
+        if (a.j != b.j) return a.j < b.j;
+        return a.g < b.g;
+    });
+    m->n_if = (int64_t)ifs.size();
+    m->if_recv.resize(m->n_if); m->if_send.resize(m->n_if); m->if_gdof.resize(m->n_if);
+    m->if_rowi.resize(m->n_if); m->if_rowj.resize(m->n_if); m->if_partner.resize(m->n_if);
+    m->if_edge.resize(m->n_if); m->if_fn.resize(m->n_if);
+    auto loc_in = [&](int64_t g, int s) -> int32_t {
+        for (int64_t p = m->copy_ptr[g]; p < m->copy_ptr[g + 1]; ++p)
+            if (m->loc_sub[m->copy_idx[p]] == s) return m->copy_idx[p];
+        return -1;
+    };
+    for (int64_t k = 0; k < m->n_if; ++k) {
+        m->if_recv[k] = ifs[k].i; m->if_send[k] = ifs[k].j; m->if_gdof[k] = ifs[k].g;
+        m->if_edge[k] = ifs[k].edge; m->if_fn[k] = ifs[k].fn;
+        m->if_rowi[k] = loc_in(ifs[k].g, ifs[k].i);
+        m->if_rowj[k] = loc_in(ifs[k].g, ifs[k].j);
+        THM_REQUIRE(m->if_rowi[k] >= 0 && m->if_rowj[k] >= 0, "internal: interface DOF without copies");
+    }
+    for (int64_t k = 0; k < m->n_if; ++k) {
+        // partner entry (j <- i, same DOF): binary search in the sorted list
+        IfE key{ifs[k].j, ifs[k].i, ifs[k].g, 0, 0};
+        auto it = std::lower_bound(ifs.begin(), ifs.end(), key, [](const IfE& a, const IfE& b) {
+            if (a.i != b.i) return a.i < b.i;
+            if (a.j != b.j) return a.j < b.j;
+            return a.g < b.g;
+        });
+        THM_REQUIRE(it != ifs.end() && it->i == key.i && it->j == key.j && it->g == key.g,
+                    "internal: interface entry without partner");
+        m->if_partner[k] = (int32_t)(it - ifs.begin());
+    }
+    m->rowg_ptr.assign(m->n_loc + 1, 0);
+    for (int64_t k = 0; k < m->n_if; ++k) m->rowg_ptr[m->if_rowi[k] + 1]++;
+    for (int64_t r = 0; r < m->n_loc; ++r) m->rowg_ptr[r + 1] += m->rowg_ptr[r];
+    m->rowg_idx.assign(m->n_if, 0);
+    {
+        std::vector<int64_t> f2(m->rowg_ptr.begin(), m->rowg_ptr.end() - 1);
+        for (int64_t k = 0; k < m->n_if; ++k) m->rowg_idx[f2[m->if_rowi[k]]++] = (int32_t)k;
+    }
+
+    // ---- device mirrors
+    std::vector<int32_t> cl32(m->cell_loc.begin(), m->cell_loc.end());
+    m->d_cell_loc.upload(cl32);
+    m->d_sell_col.upload(m->sell_col);
+    m->d_sell_pad.upload(m->sell_pad);
+    m->d_slice_ptr.upload(m->slice_ptr);
+    m->d_row_cell.upload(m->row_cell);
+    m->d_row_k.upload(m->row_k);
+    m->d_row_face_kind.upload(m->row_face_kind);
+    m->d_row_face_fn.upload(m->row_face_fn);
+    m->d_row_face_edge.upload(m->row_face_edge);
+    m->d_levels.upload(m->levels);
+    m->d_cpl_ptr.upload(m->cpl_ptr);
+    m->d_cpl_col.upload(m->cpl_col);
+    m->d_cpl_slot.upload(m->cpl_slot);
+    m->d_subs.upload(m->subs);
+    m->d_chunks.upload(m->chunks);
+    m->d_dir_edges.upload(m->dir_edges);
+    m->d_loc_gdof.upload(m->loc_gdof);
+    m->d_loc_sub.upload(m->loc_sub);
+    m->d_if_rowi.upload(m->if_rowi);
+    m->d_if_rowj.upload(m->if_rowj);
+    m->d_if_partner.upload(m->if_partner);
+    m->d_if_edge.upload(m->if_edge);
+    m->d_if_fn.upload(m->if_fn);
+    m->d_rowg_ptr.upload(m->rowg_ptr);
+    m->d_rowg_idx.upload(m->rowg_idx);
+    m->d_owner_loc.upload(m->owner_loc);
+    m->d_copy_ptr.upload(m->copy_ptr);
+    m->d_copy_idx.upload(m->copy_idx);
+    m->d_loc_is_owner.upload(m->loc_is_owner);
+    m->loc_is_bub.assign(m->n_loc, 0);
+    if (m->order == 2)
+        for (int64_t r = 0; r < m->n_loc; ++r) m->loc_is_bub[r] = m->loc_gdof[r] >= 2 * m->n_edge;
+    m->d_loc_is_bub.upload(m->loc_is_bub);
+    THM_CUDA(cudaDeviceSynchronize());
+}
+
+}  // namespace thm

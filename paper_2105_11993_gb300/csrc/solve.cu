@@ -1,0 +1,742 @@
+// The DDM-GMRES solve: batched block-preconditioned GMRES in every subdomain
+// (Section 3.2, Eq. 7), the impedance-trace exchange (Eqs. 5-6), GMRES on the
+// interface system (Eq. 8), gluing, the FP64 true residual and iterative
+// refinement.
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <functional>
+
+#include "kernels.cuh"
+#include "solver.cuh"
+
+namespace thm {
+
+__global__ void k_seg_reduce(int nseg, const int32_t* __restrict__ seg_ch, const double2* __restrict__ partial,
+                             int ldp, int nk, double2* __restrict__ out, int ldo, int accumulate) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nseg * nk) return;
+    int s = t / nk, k = t % nk;
+    double2 acc = make_double2(0, 0);
+    for (int c = seg_ch[s]; c < seg_ch[s + 1]; ++c) acc = cadd(acc, partial[(int64_t)c * ldp + k]);
+    if (accumulate) acc = cadd(acc, out[(int64_t)s * ldo + k]);
+    out[(int64_t)s * ldo + k] = acc;
+}
+
+__global__ void k_seg_reduce_real(int nseg, const int32_t* __restrict__ seg_ch, const double* __restrict__ part,
+                                  double* __restrict__ out) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nseg) return;
+    double acc = 0;
+    for (int c = seg_ch[s]; c < seg_ch[s + 1]; ++c) acc += part[c];
+    out[s] = acc;
+}
+
+// Start of a cycle: beta = ||r||, activity, g = (beta, 0, ...).  On the first
+// cycle the per-segment target is tol * ||b_s|| (x = 0 there, so r = b).
+// A segment whose true residual did not fall below half of its value at the
+// previous cycle start has reached the accuracy its arithmetic allows
+// (FP32 iterates: about cond(T_i) * 6e-8) and stops as well.
+__global__ void k_cycle_start(int nseg, int m, const double* __restrict__ nrm2, double tol, int first,
+                              double* __restrict__ target, double* __restrict__ beta, int* __restrict__ active,
+                              int* __restrict__ kused, double2* __restrict__ gv, int* __restrict__ nact,
+                              double* __restrict__ prev) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nseg) return;
+    double b = sqrt(nrm2[s]);
+    if (first) { target[s] = tol * b; prev[s] = INFINITY; }
+    int a = b > target[s] && b > 0 && b < 0.5 * prev[s];
+    prev[s] = b;
+    active[s] = a;
+    beta[s] = a ? b : 0.0;
+    kused[s] = 0;
+    for (int k = 0; k <= m; ++k) gv[(int64_t)s * (m + 1) + k] = make_double2(k == 0 && a ? b : 0.0, 0.0);
+    if (a) atomicAdd(nact, 1);
+}
+
+// Column j of the Hessenberg matrix (h1 + h2 from the two Gram-Schmidt passes,
+// ||w|| below the diagonal), previous Givens rotations, a new rotation, the
+// updated residual estimate |g_{j+1}| and the per-segment convergence flag.
+__global__ void k_givens(int nseg, int j, int m, const double2* __restrict__ h1, const double2* __restrict__ h2,
+                         int ldh, const double* __restrict__ nrm2, double2* __restrict__ Rm,
+                         double* __restrict__ cs, double2* __restrict__ sn, double2* __restrict__ gv,
+                         const double* __restrict__ target, int* __restrict__ active, int* __restrict__ kused,
+                         double* __restrict__ beta, int* __restrict__ nact, int* __restrict__ flag) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nseg) return;
+    if (!active[s]) { beta[s] = 0.0; return; }
+    double2* col = Rm + ((int64_t)s * m + j) * m;      // column j, rows 0..j
+    for (int i = 0; i <= j; ++i) col[i] = cadd(h1[(int64_t)s * ldh + i], h2[(int64_t)s * ldh + i]);
+    double hn = sqrt(nrm2[s]);
+    if (!isfinite(hn)) { atomicExch(flag, 1); active[s] = 0; beta[s] = 0.0; return; }
+    double* c = cs + (int64_t)s * m;
+    double2* sg = sn + (int64_t)s * m;
+    for (int i = 0; i < j; ++i) {
+        double2 a = col[i], b = col[i + 1];
+        // [a; b] <- [[c, s], [-conj(s), c]] [a; b]
+        double2 t = make_double2(c[i] * a.x + sg[i].x * b.x - sg[i].y * b.y, c[i] * a.y + sg[i].x * b.y + sg[i].y * b.x);
+        double2 u = make_double2(-(sg[i].x * a.x + sg[i].y * a.y) + c[i] * b.x, -(sg[i].x * a.y - sg[i].y * a.x) + c[i] * b.y);
+        col[i] = t;
+        col[i + 1] = u;
+    }
+    double2 a = col[j];
+    double am = hypot(a.x, a.y);
+    double d = hypot(am, hn);
+    double cj;
+    double2 sj;
+    if (d == 0.0) { cj = 1.0; sj = make_double2(0, 0); }
+    else if (am == 0.0) { cj = 0.0; sj = make_double2(1.0, 0.0); }
+    else {
+        cj = am / d;
+        // s = (a/|a|) * conj(hn) / d, hn real
+        sj = make_double2(a.x / am * hn / d, a.y / am * hn / d);
+    }
+    c[j] = cj;
+    sg[j] = sj;
+    col[j] = make_double2(cj * a.x + (sj.x * hn), cj * a.y + (sj.y * hn));
+    double2* g = gv + (int64_t)s * (m + 1);
+    double2 gj = g[j];
+    // g_{j+1} = -conj(s) g_j ; g_j = c g_j
+    g[j + 1] = make_double2(-(sj.x * gj.x + sj.y * gj.y), -(sj.x * gj.y - sj.y * gj.x));
+    g[j] = make_double2(cj * gj.x, cj * gj.y);
+    kused[s] = j + 1;
+    beta[s] = hn;
+    double res = hypot(g[j + 1].x, g[j + 1].y);
+    if (res <= target[s] || hn == 0.0) active[s] = 0;
+    else atomicAdd(nact, 1);
+}
+
+// y = R^{-1} g (upper triangular, k = kused[s])
+__global__ void k_backsolve(int nseg, int m, const double2* __restrict__ Rm, const double2* __restrict__ gv,
+                            const int* __restrict__ kused, double2* __restrict__ y) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nseg) return;
+    int k = kused[s];
+    const double2* R = Rm + (int64_t)s * m * m;          // R[col * m + row]
+    const double2* g = gv + (int64_t)s * (m + 1);
+    double2* yy = y + (int64_t)s * m;
+    for (int i = k - 1; i >= 0; --i) {
+        double2 acc = g[i];
+        for (int q = i + 1; q < k; ++q) {
+            double2 r = R[(int64_t)q * m + i], v = yy[q];
+            acc.x -= r.x * v.x - r.y * v.y;
+            acc.y -= r.x * v.y + r.y * v.x;
+        }
+        double2 d = R[(int64_t)i * m + i];
+        double den = d.x * d.x + d.y * d.y;
+        yy[i] = den > 0 ? make_double2((acc.x * d.x + acc.y * d.y) / den, (acc.y * d.x - acc.x * d.y) / den)
+                        : make_double2(0, 0);
+    }
+}
+
+// Right-hand side of every subdomain: sources + sum of received interface data.
+__global__ void k_rhs(int64_t n, const double2* __restrict__ src, const int64_t* __restrict__ rowg_ptr,
+                      const int32_t* __restrict__ rowg_idx, const double2* __restrict__ g, double2* __restrict__ b) {
+    int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    double2 v = src ? src[r] : make_double2(0, 0);
+    if (g)
+        for (int64_t p = rowg_ptr[r]; p < rowg_ptr[r + 1]; ++p) v = cadd(v, g[rowg_idx[p]]);
+    b[r] = v;
+}
+
+// Impedance-trace exchange (Eq. 6):  G_{i<-j} = -G_{j<-i} + 2 i kappa omega M_Sigma u_j
+__global__ void k_exchange(int64_t n_if, const int32_t* __restrict__ partner, const int32_t* __restrict__ rowj,
+                           const double* __restrict__ mass, double kw, const double2* __restrict__ g_in,
+                           const double2* __restrict__ u, double2* __restrict__ g_out) {
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= n_if) return;
+    double2 gp = g_in ? g_in[partner[k]] : make_double2(0, 0);
+    double2 uj = u[rowj[k]];
+    double f = 2.0 * kw * mass[k];
+    g_out[k] = make_double2(-gp.x - f * uj.y, -gp.y + f * uj.x);
+}
+
+// u[d] += u_loc[owner(d)] on free DOFs
+__global__ void k_glue_add(int64_t n_dof, const int32_t* __restrict__ owner, const double2* __restrict__ uloc,
+                           double2* __restrict__ u) {
+    int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (d >= n_dof) return;
+    int32_t o = owner[d];
+    if (o >= 0) u[d] = cadd(u[d], uloc[o]);
+}
+
+__global__ void k_scatter_loc(int64_t n_loc, const int64_t* __restrict__ gdof, const double2* __restrict__ u,
+                              double2* __restrict__ uloc) {
+    int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r < n_loc) uloc[r] = u[gdof[r]];
+}
+
+// r_glob[d] = sum over the local copies of d of rl (free d), 0 on Dirichlet DOFs
+__global__ void k_gather_sum(int64_t n_dof, const int64_t* __restrict__ cptr, const int32_t* __restrict__ cidx,
+                             const double2* __restrict__ rl, double2* __restrict__ rg) {
+    int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (d >= n_dof) return;
+    double2 a = make_double2(0, 0);
+    for (int64_t p = cptr[d]; p < cptr[d + 1]; ++p) a = cadd(a, rl[cidx[p]]);
+    rg[d] = a;
+}
+
+// owner split of a global vector into local sources
+__global__ void k_owner_split(int64_t n_loc, const int64_t* __restrict__ gdof, const uint8_t* __restrict__ owner,
+                              const double2* __restrict__ rg, double2* __restrict__ src) {
+    int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r < n_loc) src[r] = owner[r] ? rg[gdof[r]] : make_double2(0, 0);
+}
+
+__global__ void k_norm2_blocks(int64_t n, const double2* __restrict__ x, double* __restrict__ part) {
+    __shared__ double sw[32];
+    double s = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double2 v = x[i];
+        s += v.x * v.x + v.y * v.y;
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += sw[q];
+        part[blockIdx.x] = t;
+    }
+}
+
+// Mixed-precision refinement of the subdomain solves: a subdomain stays
+// active while its FP64 residual is above tol * ||b_s|| and still falling.
+__global__ void k_ir_mask(int nseg, double tol, int first, const double* __restrict__ bn2,
+                          const double* __restrict__ rn2, double* __restrict__ prev, int* __restrict__ active,
+                          int* __restrict__ nact) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nseg) return;
+    double rn = sqrt(rn2[s]), bn = sqrt(bn2[s]);
+    if (first) prev[s] = INFINITY;
+    int a = rn > tol * bn && rn < 0.5 * prev[s];
+    prev[s] = rn;
+    active[s] = a;
+    if (a) atomicAdd(nact, 1);
+}
+
+__global__ void k_ir_to_f32(const Chunk* __restrict__ chunks, const int* __restrict__ active,
+                            const double2* __restrict__ r, float2* __restrict__ r32) {
+    const Chunk c = chunks[blockIdx.x];
+    const int a = active[c.seg];
+    for (int64_t e = c.begin + threadIdx.x; e < c.end; e += blockDim.x) {
+        double2 v = r[e];
+        r32[e] = a ? make_float2((float)v.x, (float)v.y) : make_float2(0.f, 0.f);
+    }
+}
+
+__global__ void k_ir_update(int64_t n, const float2* __restrict__ d, double2* __restrict__ x) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) {
+        float2 v = d[i];
+        double2 u = x[i];
+        x[i] = make_double2(u.x + (double)v.x, u.y + (double)v.y);
+    }
+}
+
+static inline unsigned nblk(int64_t n, int th = 256) { return (unsigned)((n + th - 1) / th); }
+
+// ---------------------------------------------------------------------------
+// Batched restarted GMRES over segments (subdomains, or the one interface
+// segment), right-preconditioned, classical Gram-Schmidt with one full
+// re-orthogonalisation (CGS2), Givens rotations in FP64.
+// ---------------------------------------------------------------------------
+struct KStats {
+    int64_t iters = 0;       // sum over segments of Arnoldi steps
+    int64_t dof_iters = 0;   // sum over segments of n_s * steps
+    int max_iters = 0;       // largest per-segment count of this solve
+    int status = THM_OK;
+};
+
+template <class V>
+struct Krylov {
+    int64_t n = 0;
+    int nseg = 0, m = 0, nch = 0;
+    const Chunk* d_chunks = nullptr;
+    DArr<Chunk> own_chunks;
+    DArr<int32_t> seg_ch;
+    std::vector<int64_t> seg_n;
+    DArr<V> basis, w, z, r, t;
+    DArr<V> zbasis;            // flexible variant: Z_j = M v_j (x = Z y)
+    bool flexible = false;
+    DArr<double2> partial, h1, h2, Rm, sn, gv, y;
+    DArr<double> nrm_part, nrm, cs, beta, target, prev;
+    DArr<int> active, kused, nact, flag;
+    int* h_pinned = nullptr;
+    std::vector<int> h_kused;
+
+    ~Krylov() { if (h_pinned) cudaFreeHost(h_pinned); }
+
+    void init(int64_t n_, int nseg_, int m_, const std::vector<Chunk>& chunks, const Chunk* dch,
+              const std::vector<int64_t>& segn, bool flexible_ = false) {
+        n = n_; nseg = nseg_; m = m_; nch = (int)chunks.size();
+        flexible = flexible_;
+        if (flexible) zbasis.alloc((size_t)m * n);
+        seg_n = segn;
+        if (dch) d_chunks = dch;
+        else { own_chunks.upload(chunks); d_chunks = own_chunks.p; }
+        std::vector<int32_t> sc(nseg + 1, 0);
+        for (const Chunk& c : chunks) sc[c.seg + 1]++;
+        for (int s = 0; s < nseg; ++s) sc[s + 1] += sc[s];
+        seg_ch.upload(sc);
+        basis.alloc((size_t)(m + 1) * n);
+        w.alloc(n); z.alloc(n); r.alloc(n); t.alloc(n);
+        partial.alloc((size_t)nch * (m + 1));
+        h1.alloc((size_t)nseg * (m + 1)); h2.alloc((size_t)nseg * (m + 1));
+        Rm.alloc((size_t)nseg * m * m);
+        sn.alloc((size_t)nseg * m); cs.alloc((size_t)nseg * m);
+        gv.alloc((size_t)nseg * (m + 1)); y.alloc((size_t)nseg * m);
+        nrm_part.alloc(nch); nrm.alloc(nseg); beta.alloc(nseg); target.alloc(nseg); prev.alloc(nseg);
+        active.alloc(nseg); kused.alloc(nseg); nact.alloc(1); flag.alloc(1);
+        if (!h_pinned) THM_CUDA(cudaMallocHost(&h_pinned, 2 * sizeof(int)));
+        size_t dots_smem = (size_t)(m + 1) * (KT / 32) * sizeof(double2);
+        THM_REQUIRE(dots_smem <= 200 * 1024, "restart length too large");
+        THM_CUDA(cudaFuncSetAttribute(k_chunk_dots<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dots_smem));
+        THM_CUDA(cudaFuncSetAttribute(k_chunk_update<V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)((m + 1) * sizeof(double2))));
+        THM_CUDA(cudaDeviceSynchronize());
+    }
+
+    void seg_norm2(const V* x, cudaStream_t st) {
+        THM_LAUNCH(THM_K_KRYLOV, st, k_chunk_norm2<V><<<nch, KT, 0, st>>>(d_chunks, x, nrm_part.p));
+        THM_LAUNCH(THM_K_KRYLOV, st, k_seg_reduce_real<<<nblk(nseg), 256, 0, st>>>(nseg, seg_ch.p, nrm_part.p, nrm.p));
+    }
+
+    int read_nact(cudaStream_t st) {
+        THM_CUDA(cudaMemcpyAsync(h_pinned, nact.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+        THM_CUDA(cudaMemcpyAsync(h_pinned + 1, flag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+        THM_CUDA(cudaStreamSynchronize(st));
+        return h_pinned[0];
+    }
+
+    // Solve A x = b for all segments (x in/out).  A(in, out); M(in, out) or empty.
+    KStats solve(const std::function<void(const V*, V*)>& A, const std::function<void(const V*, V*)>& M,
+                 const V* b, V* x, bool x_zero, double tol, int maxit, cudaStream_t st, bool single_cycle = false) {
+        KStats ks;
+        std::vector<int64_t> per_seg(nseg, 0);
+        int total = 0;
+        bool first = true;
+        flag.zero(st);
+        if (x_zero) {
+            THM_CUDA(cudaMemsetAsync(x, 0, n * sizeof(V), st));
+            THM_CUDA(cudaMemcpyAsync(r.p, b, n * sizeof(V), cudaMemcpyDeviceToDevice, st));
+        } else {
+            A(x, w.p);
+            THM_LAUNCH(THM_K_KRYLOV, st, k_sub<V><<<nblk(n), 256, 0, st>>>(n, b, w.p, r.p));
+        }
+        while (true) {
+            seg_norm2(r.p, st);
+            nact.zero(st);
+            THM_LAUNCH(THM_K_KRYLOV, st, k_cycle_start<<<nblk(nseg), 256, 0, st>>>(nseg, m, nrm.p, tol, first ? 1 : 0, target.p, beta.p,
+                                                      active.p, kused.p, gv.p, nact.p, prev.p));
+            first = false;
+            if (read_nact(st) == 0) break;
+            if (total >= maxit) { ks.status = THM_ENOCONV; break; }
+            THM_LAUNCH(THM_K_KRYLOV, st, k_chunk_scale<V><<<nch, 256, 0, st>>>(d_chunks, r.p, beta.p, basis.p));
+            int j = 0;
+            for (; j < m && total < maxit; ++j) {
+                V* vj = basis.p + (int64_t)j * n;
+                const V* zin = vj;
+                V* zj = flexible ? zbasis.p + (int64_t)j * n : z.p;
+                if (M) { M(vj, zj); zin = zj; }
+                A(zin, w.p);
+                const int nk = j + 1;
+                size_t sm = (size_t)nk * (KT / 32) * sizeof(double2);
+                THM_LAUNCH(THM_K_DOTS, st, k_chunk_dots<V><<<nch, KT, sm, st>>>(d_chunks, basis.p, n, nk, w.p, partial.p, m + 1));
+                THM_LAUNCH(THM_K_KRYLOV, st, k_seg_reduce<<<nblk((int64_t)nseg * nk), 256, 0, st>>>(nseg, seg_ch.p, partial.p, m + 1, nk, h1.p, m + 1, 0));
+                THM_LAUNCH(THM_K_UPDATE, st, k_chunk_update<V><<<nch, KT, nk * sizeof(double2), st>>>(d_chunks, basis.p, n, nk, h1.p, m + 1, w.p, nullptr));
+                THM_LAUNCH(THM_K_DOTS, st, k_chunk_dots<V><<<nch, KT, sm, st>>>(d_chunks, basis.p, n, nk, w.p, partial.p, m + 1));
+                THM_LAUNCH(THM_K_KRYLOV, st, k_seg_reduce<<<nblk((int64_t)nseg * nk), 256, 0, st>>>(nseg, seg_ch.p, partial.p, m + 1, nk, h2.p, m + 1, 0));
+                THM_LAUNCH(THM_K_UPDATE, st, k_chunk_update<V><<<nch, KT, nk * sizeof(double2), st>>>(d_chunks, basis.p, n, nk, h2.p, m + 1, w.p, nrm_part.p));
+                THM_LAUNCH(THM_K_KRYLOV, st, k_seg_reduce_real<<<nblk(nseg), 256, 0, st>>>(nseg, seg_ch.p, nrm_part.p, nrm.p));
+                nact.zero(st);
+                THM_LAUNCH(THM_K_KRYLOV, st, k_givens<<<nblk(nseg), 128, 0, st>>>(nseg, j, m, h1.p, h2.p, m + 1, nrm.p, Rm.p, cs.p, sn.p, gv.p,
+                                                     target.p, active.p, kused.p, beta.p, nact.p, flag.p));
+                THM_LAUNCH(THM_K_KRYLOV, st, k_chunk_scale<V><<<nch, 256, 0, st>>>(d_chunks, w.p, beta.p, basis.p + (int64_t)(j + 1) * n));
+                ++total;
+                int na = read_nact(st);
+                if (h_pinned[1]) { ks.status = THM_EBREAKDOWN; break; }
+                if (na == 0) { ++j; break; }
+            }
+            THM_CUDA(cudaGetLastError());
+            // x += M (V y)
+            THM_LAUNCH(THM_K_KRYLOV, st, k_backsolve<<<nblk(nseg), 64, 0, st>>>(nseg, m, Rm.p, gv.p, kused.p, y.p));
+            if (flexible && M) {
+                // x += Z y: the preconditioned directions actually used by the Arnoldi process
+                THM_LAUNCH(THM_K_KRYLOV, st, k_chunk_combine<V><<<nch, KT, 0, st>>>(d_chunks, zbasis.p, n, kused.p, y.p, m, t.p));
+                THM_LAUNCH(THM_K_KRYLOV, st, k_axpy<V><<<nblk(n), 256, 0, st>>>(n, t.p, x));
+            } else {
+            THM_LAUNCH(THM_K_KRYLOV, st, k_chunk_combine<V><<<nch, KT, 0, st>>>(d_chunks, basis.p, n, kused.p, y.p, m, t.p));
+            if (M) {
+                M(t.p, z.p);
+                THM_LAUNCH(THM_K_KRYLOV, st, k_axpy<V><<<nblk(n), 256, 0, st>>>(n, z.p, x));
+            } else {
+                THM_LAUNCH(THM_K_KRYLOV, st, k_axpy<V><<<nblk(n), 256, 0, st>>>(n, t.p, x));
+            }
+            }
+            kused.download(h_kused, st);
+            for (int s = 0; s < nseg; ++s) {
+                per_seg[s] += h_kused[s];
+                ks.iters += h_kused[s];
+                ks.dof_iters += (int64_t)h_kused[s] * seg_n[s];
+            }
+            if (ks.status == THM_EBREAKDOWN || single_cycle) break;
+            A(x, w.p);
+            THM_LAUNCH(THM_K_KRYLOV, st, k_sub<V><<<nblk(n), 256, 0, st>>>(n, b, w.p, r.p));
+        }
+        for (int s = 0; s < nseg; ++s) ks.max_iters = std::max<int>(ks.max_iters, (int)per_seg[s]);
+        THM_CUDA(cudaGetLastError());
+        return ks;
+    }
+};
+
+// ---------------------------------------------------------------------------
+struct Work {
+    int m_in = 0, m_out = 0;
+    bool has64 = false, has32 = false;
+    Krylov<double2> in64;
+    Krylov<float2> in32;
+    Krylov<double2> outer;
+    DArr<double2> b64, x64, src, g0, gtmp, gb, gsol, uglob, uloc, rloc, rglob, ytmp;
+    DArr<float2> b32, x32;
+    DArr<double2> r64, ytmp2;
+    DArr<double> bn2, rn2, rprev;
+    DArr<int> ir_active, nact_ir;
+    DArr<double> npart;
+};
+
+static void ensure_work(thm_sys* s, bool fp32, int m_in, int m_out) {
+    const thm_mesh* m = s->m;
+    if (!s->w) s->w = new Work();
+    Work* w = s->w;
+    if (w->m_in != m_in) { w->has64 = w->has32 = false; w->m_in = m_in; }
+    std::vector<int64_t> segn(m->n_sub);
+    for (int i = 0; i < m->n_sub; ++i) segn[i] = m->subs[i].n;
+    if (!fp32 && !w->has64) {
+        w->in64.init(m->n_loc, m->n_sub, m_in, m->chunks, m->d_chunks.p, segn);
+        w->has64 = true;
+    }
+    if (fp32 && !w->has32) {
+        w->in32.init(m->n_loc, m->n_sub, m_in, m->chunks, m->d_chunks.p, segn, true);
+        w->b32.alloc(m->n_loc); w->x32.alloc(m->n_loc);
+        w->r64.alloc(m->n_loc); w->ytmp2.alloc(m->n_loc);
+        w->bn2.alloc(m->n_sub); w->rn2.alloc(m->n_sub); w->rprev.alloc(m->n_sub);
+        w->ir_active.alloc(m->n_sub); w->nact_ir.alloc(1);
+        w->has32 = true;
+    }
+    if (w->m_out != m_out && m->n_if > 0) {
+        std::vector<Chunk> oc;
+        for (int64_t b = 0; b < m->n_if; b += CHUNK) {
+            Chunk c{};
+            c.seg = 0; c.begin = b; c.end = std::min<int64_t>(m->n_if, b + CHUNK);
+            oc.push_back(c);
+        }
+        w->outer.init(m->n_if, 1, m_out, oc, nullptr, std::vector<int64_t>{m->n_if});
+        w->m_out = m_out;
+    }
+    if (w->b64.n == 0) {
+        w->b64.alloc(m->n_loc); w->x64.alloc(m->n_loc); w->src.alloc(m->n_loc);
+        w->uloc.alloc(m->n_loc); w->rloc.alloc(m->n_loc); w->ytmp.alloc(m->n_loc);
+        size_t ni = m->n_if > 0 ? m->n_if : 1;
+        w->g0.alloc(ni); w->gtmp.alloc(ni); w->gb.alloc(ni); w->gsol.alloc(ni);
+        w->uglob.alloc(m->n_dof); w->rglob.alloc(m->n_dof);
+        w->npart.alloc(1024);
+    }
+}
+
+
+
+SolveCfg make_cfg(const thm_solve_opts* o) {
+    SolveCfg c{};
+    c.fp32 = o && o->mode == THM_MODE_MIXED;
+    THM_REQUIRE(!o || o->mode == THM_MODE_FP64 || o->mode == THM_MODE_MIXED, "unknown mode");
+    c.rtol = (o && o->rtol > 0) ? o->rtol : 1e-8;
+    c.m_in = (o && o->inner_restart > 0) ? o->inner_restart : 120;
+    c.m_out = (o && o->outer_restart > 0) ? o->outer_restart : 600;
+    c.inner_maxit = (o && o->inner_maxit > 0) ? o->inner_maxit : 2000;
+    c.outer_maxit = (o && o->outer_maxit > 0) ? o->outer_maxit : 2000;
+    c.max_refine = (o && o->max_refine > 0) ? o->max_refine : 6;
+    c.inner_tol = (o && o->inner_tol > 0) ? o->inner_tol : 1e-11;
+    c.outer_tol = (o && o->outer_tol > 0) ? o->outer_tol : 1e-9;
+    return c;
+}
+
+template <class V, class F>
+static void apply_T(const thm_sys* s, const F* val, const F* bg, const F* bs, int use_bs, const V* x, V* y) {
+    const thm_mesh* m = s->m;
+    THM_LAUNCH(THM_K_SPMV, 0, k_spmv<V, F><<<nblk(m->n_loc), 256, 0, s->st>>>(m->n_loc, m->d_slice_ptr.p, m->d_sell_col.p, val, bg, bs,
+                                                    use_bs, x, y));
+}
+
+template <class V, class F>
+static void apply_Pinv(const thm_sys* s, const F* fac, const F* cval, const int32_t* ai, const F* av,
+                       const int32_t* ci, const F* cv, const int32_t* ei, const F* ev, const V* x, V* y) {
+    const thm_mesh* m = s->m;
+    using R = typename VT<V>::R;
+    auto r4 = [](int64_t v) { return (int64_t)((v + 3) / 4 * 4); };
+    int max_lev = 0;
+    for (const auto& S : m->subs) max_lev = std::max(max_lev, S.nlev);
+    const size_t tail = (size_t)(r4(m->max_ne) + r4(m->max_m)) * sizeof(R) + 2 * (size_t)r4(max_lev) * sizeof(int);
+    const size_t csr = (size_t)r4(m->max_m + 1) * 4 + (size_t)r4(m->max_cnz) * (4 + sizeof(F)) + 16;
+    const size_t cap = 220 * 1024;
+    THM_REQUIRE(tail + 3 * csr <= cap, "subdomain too large for the shared-memory block solve");
+    // tile height: the largest multiple of 4 rows (<= 64) whose ring of 3..6 slots fits
+    int rows = 64, nslot = 6;
+    size_t slot = 0;
+    for (;; rows -= 4) {
+        THM_REQUIRE(rows >= 4, "level block too wide for the shared-memory block solve");
+        slot = std::max(csr, (size_t)rows * m->max_m * sizeof(F) + 16);
+        slot = (slot + 15) / 16 * 16;
+        nslot = (int)std::min<size_t>(6, (cap - tail) / slot);
+        if (nslot >= 3) break;
+    }
+    const size_t smem = (size_t)nslot * slot + tail;
+    static size_t attr = 0;
+    if (smem > 48 * 1024 && smem > attr) {
+        THM_CUDA(cudaFuncSetAttribute(k_bt_apply<V, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr = smem;
+    }
+    dim3 grid(m->n_sub, 2);
+    THM_LAUNCH(THM_K_PINV, s->st,
+               k_bt_apply<V, F><<<grid, 512, smem, s->st>>>(m->d_subs.p, m->d_levels.p, fac, m->d_cpl_ptr.p,
+                                                            m->d_cpl_col.p, cval, m->n_loc, m->order == 2 ? 1 : 0,
+                                                            ai, av, ci, cv, ei, ev, rows, nslot, (int)slot,
+                                                            (int)m->max_ne, m->max_m, max_lev, x, y));
+}
+
+template <class V>
+static void apply_Pinv_mode(const thm_sys* s, bool f32, const V* x, V* y) {
+    if (f32)
+        apply_Pinv<V, float>(s, s->fac32.p, s->cpl32.p, s->tab_ai.p, s->tab_av32.p, s->tab_ci.p, s->tab_cv32.p,
+                             s->tab_ei.p, s->tab_ev32.p, x, y);
+    else
+        apply_Pinv<V, double>(s, s->fac64.p, s->cpl64.p, s->tab_ai.p, s->tab_av64.p, s->tab_ci.p, s->tab_cv64.p,
+                              s->tab_ei.p, s->tab_ev64.p, x, y);
+}
+
+
+
+static void add(RunStats& rs, const KStats& k) {
+    rs.inner += k.iters;
+    rs.dof_iters += k.dof_iters;
+    rs.max_inner = std::max(rs.max_inner, k.max_iters);
+    if (k.status != THM_OK && rs.status == THM_OK) rs.status = k.status;
+}
+
+// Solve all subdomain problems T_i x_i = b_i (b, x FP64 local vectors).
+static void subdomain_solves(thm_sys* s, const SolveCfg& c, const double2* b, double2* x, RunStats& rs) {
+    const thm_mesh* m = s->m;
+    Work* w = s->w;
+    cudaStream_t st = s->st;
+    if (!c.fp32) {
+        auto A = [&](const double2* in, double2* out) { apply_T<double2, double>(s, s->val64.p, s->bg64.p, s->bs64.p, 1, in, out); };
+        auto M = [&](const double2* in, double2* out) { apply_Pinv_mode<double2>(s, false, in, out); };
+        add(rs, w->in64.solve(A, M, b, x, true, c.inner_tol, c.inner_maxit, st));
+    } else {
+        // Mixed: GMRES-IR.  Each cycle solves T d = r in FP32 (FP32 operator,
+        // FP32 preconditioner, FP32 Krylov basis; flexible form, so d is built
+        // from the very preconditioned vectors the Arnoldi process used) to a
+        // relative 1e-5; x and the true residual r = b - T x are kept in FP64,
+        // so the subdomain solves reach the same tolerance as in FP64 mode.
+        auto A = [&](const float2* in, float2* out) { apply_T<float2, float>(s, s->val32.p, s->bg32.p, s->bs32.p, 1, in, out); };
+        auto M = [&](const float2* in, float2* out) { apply_Pinv_mode<float2>(s, true, in, out); };
+        Krylov<float2>& K = w->in32;
+        THM_CUDA(cudaMemsetAsync(x, 0, m->n_loc * sizeof(double2), st));
+        THM_CUDA(cudaMemcpyAsync(w->r64.p, b, m->n_loc * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+        // per-subdomain ||b|| -> target
+        THM_LAUNCH(THM_K_KRYLOV, st, k_chunk_norm2<double2><<<K.nch, KT, 0, st>>>(K.d_chunks, b, K.nrm_part.p));
+        THM_LAUNCH(THM_K_KRYLOV, st, k_seg_reduce_real<<<nblk(K.nseg), 256, 0, st>>>(K.nseg, K.seg_ch.p, K.nrm_part.p, w->bn2.p));
+        const int max_cycles = std::max(1, c.inner_maxit / std::max(1, c.m_in));
+        for (int cyc = 0; cyc < max_cycles; ++cyc) {
+            THM_LAUNCH(THM_K_KRYLOV, st, k_chunk_norm2<double2><<<K.nch, KT, 0, st>>>(K.d_chunks, w->r64.p, K.nrm_part.p));
+            THM_LAUNCH(THM_K_KRYLOV, st, k_seg_reduce_real<<<nblk(K.nseg), 256, 0, st>>>(K.nseg, K.seg_ch.p, K.nrm_part.p, w->rn2.p));
+            w->nact_ir.zero(st);
+            THM_LAUNCH(THM_K_DDM, st, k_ir_mask<<<nblk(K.nseg), 256, 0, st>>>(K.nseg, c.inner_tol, cyc == 0 ? 1 : 0, w->bn2.p, w->rn2.p,
+                                                  w->rprev.p, w->ir_active.p, w->nact_ir.p));
+            THM_LAUNCH(THM_K_DDM, st, k_ir_to_f32<<<K.nch, 256, 0, st>>>(K.d_chunks, w->ir_active.p, w->r64.p, w->b32.p));
+            std::vector<int> na;
+            w->nact_ir.download(na, st);
+            if (na[0] == 0) break;
+            KStats ks = K.solve(A, M, w->b32.p, w->x32.p, true, 1e-5, c.m_in, st, true);
+            ks.status = THM_OK;      // the refinement loop owns convergence
+            add(rs, ks);
+            THM_LAUNCH(THM_K_DDM, st, k_ir_update<<<nblk(m->n_loc), 256, 0, st>>>(m->n_loc, w->x32.p, x));
+            apply_T<double2, double>(s, s->val64.p, s->bg64.p, s->bs64.p, 1, x, w->ytmp2.p);
+            THM_LAUNCH(THM_K_KRYLOV, st, k_sub<double2><<<nblk(m->n_loc), 256, 0, st>>>(m->n_loc, b, w->ytmp2.p, w->r64.p));
+        }
+    }
+}
+
+// One sweep: x = T^{-1}(src + R g_in), g_out = exchange(g_in, x).
+static void sweep(thm_sys* s, const SolveCfg& c, const double2* src, const double2* g_in, double2* g_out,
+                  double2* x, RunStats& rs) {
+    const thm_mesh* m = s->m;
+    Work* w = s->w;
+    cudaStream_t st = s->st;
+    THM_LAUNCH(THM_K_DDM, st, k_rhs<<<nblk(m->n_loc), 256, 0, st>>>(m->n_loc, src, m->d_rowg_ptr.p, m->d_rowg_idx.p,
+                                          m->n_if > 0 ? g_in : nullptr, w->b64.p));
+    subdomain_solves(s, c, w->b64.p, x, rs);
+    if (m->n_if > 0 && g_out)
+        THM_LAUNCH(THM_K_DDM, st, k_exchange<<<nblk(m->n_if), 256, 0, st>>>(m->n_if, m->d_if_partner.p, m->d_if_rowj.p, s->if_mass.p,
+                                                  s->kappa * s->omega, g_in, x, g_out));
+    rs.sweeps++;
+    THM_CUDA(cudaGetLastError());
+}
+
+// DDM solve of Eq. 8 for local sources src -> local solution uloc.
+static void ddm_solve(thm_sys* s, const SolveCfg& c, const double2* src, double2* uloc, RunStats& rs) {
+    const thm_mesh* m = s->m;
+    Work* w = s->w;
+    cudaStream_t st = s->st;
+    if (m->n_if == 0) {
+        sweep(s, c, src, nullptr, nullptr, uloc, rs);
+        return;
+    }
+    // b = A_src(0): sweep with sources and zero interface data
+    w->g0.zero(st);
+    sweep(s, c, src, w->g0.p, w->gb.p, uloc, rs);
+    auto A = [&](const double2* v, double2* out) {
+        sweep(s, c, nullptr, v, w->gtmp.p, w->ytmp.p, rs);
+        THM_LAUNCH(THM_K_KRYLOV, st, k_sub<double2><<<nblk(m->n_if), 256, 0, st>>>(m->n_if, v, w->gtmp.p, out));   // (I - A) v
+    };
+    std::function<void(const double2*, double2*)> none;
+    static const bool verbose = getenv("THM_VERBOSE") != nullptr;
+    std::function<void(const double2*, double2*)> Av = A;
+    if (verbose) {
+        Av = [&, t0 = std::chrono::steady_clock::now()](const double2* v, double2* out) {
+            int64_t before = rs.inner;
+            A(v, out);
+            double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+            fprintf(stderr, "[thm] sweep %d: inner %lld (max %d) t=%.3fs\n", rs.sweeps,
+                    (long long)(rs.inner - before), rs.max_inner, el);
+        };
+    }
+    KStats ko = w->outer.solve(Av, none, w->gb.p, w->gsol.p, true, c.outer_tol, c.outer_maxit, st);
+    rs.outer += (int)ko.iters;
+    if (ko.status != THM_OK && rs.status == THM_OK) rs.status = ko.status;
+    sweep(s, c, src, w->gsol.p, nullptr, uloc, rs);
+}
+
+static double global_norm(thm_sys* s, const double2* x, int64_t n) {
+    Work* w = s->w;
+    const int nb = 512;
+    THM_LAUNCH(THM_K_DDM, 0, k_norm2_blocks<<<nb, 256, 0, s->st>>>(n, x, w->npart.p));
+    std::vector<double> h(nb);
+    THM_CUDA(cudaMemcpyAsync(h.data(), w->npart.p, nb * sizeof(double), cudaMemcpyDeviceToHost, s->st));
+    THM_CUDA(cudaStreamSynchronize(s->st));
+    double t = 0;
+    for (double v : h) t += v;
+    return std::sqrt(t);
+}
+
+// FP64 true residual r = f - K u for a local right-hand-side split f_loc of f.
+static double true_residual_rhs(thm_sys* s, const double2* f_loc, const double2* u, double2* rglob) {
+    const thm_mesh* m = s->m;
+    Work* w = s->w;
+    cudaStream_t st = s->st;
+    THM_LAUNCH(THM_K_DDM, st, k_scatter_loc<<<nblk(m->n_loc), 256, 0, st>>>(m->n_loc, m->d_loc_gdof.p, u, w->uloc.p));
+    apply_T<double2, double>(s, s->val64.p, s->bg64.p, s->bs64.p, 0, w->uloc.p, w->ytmp.p);   // K^loc
+    THM_LAUNCH(THM_K_DDM, st, k_sub<double2><<<nblk(m->n_loc), 256, 0, st>>>(m->n_loc, f_loc, w->ytmp.p, w->rloc.p));
+    THM_LAUNCH(THM_K_DDM, st, k_gather_sum<<<nblk(m->n_dof), 256, 0, st>>>(m->n_dof, m->d_copy_ptr.p, m->d_copy_idx.p, w->rloc.p, rglob));
+    return global_norm(s, rglob, m->n_dof);
+}
+
+// Refined DDM solve of K_FF u_F = f (f given by its local split f_loc), u
+// initialised with u0 on all DOFs (the Dirichlet values, or zeros).
+int solve_rhs(thm_sys* s, const SolveCfg& c, const double2* f_loc, const double2* u0, double2* u, RunStats& rs,
+              double& rel) {
+    const thm_mesh* m = s->m;
+    Work* w = s->w;
+    cudaStream_t st = s->st;
+    THM_LAUNCH(THM_K_DDM, st, k_gather_sum<<<nblk(m->n_dof), 256, 0, st>>>(m->n_dof, m->d_copy_ptr.p, m->d_copy_idx.p, f_loc, w->rglob.p));
+    double fn = global_norm(s, w->rglob.p, m->n_dof);
+    if (u0) THM_CUDA(cudaMemcpyAsync(u, u0, m->n_dof * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+    else THM_CUDA(cudaMemsetAsync(u, 0, m->n_dof * sizeof(double2), st));
+    THM_CUDA(cudaMemcpyAsync(w->src.p, f_loc, m->n_loc * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+    rel = fn > 0 ? 1.0 : 0.0;
+    for (int it = 0; it < c.max_refine && fn > 0; ++it) {
+        ddm_solve(s, c, w->src.p, w->x64.p, rs);
+        rs.refine++;
+        THM_LAUNCH(THM_K_DDM, st, k_glue_add<<<nblk(m->n_dof), 256, 0, st>>>(m->n_dof, m->d_owner_loc.p, w->x64.p, u));
+        double rn = true_residual_rhs(s, f_loc, u, w->rglob.p);
+        rel = rn / fn;
+        if (!std::isfinite(rel)) { rs.status = THM_EBREAKDOWN; break; }
+        if (rel <= c.rtol) break;
+        THM_LAUNCH(THM_K_DDM, st, k_owner_split<<<nblk(m->n_loc), 256, 0, st>>>(m->n_loc, m->d_loc_gdof.p, m->d_loc_is_owner.p,
+                                                                               w->rglob.p, w->src.p));
+    }
+    THM_CUDA(cudaStreamSynchronize(st));
+    THM_CUDA(cudaGetLastError());
+    if (rs.status == THM_EBREAKDOWN) return THM_EBREAKDOWN;
+    if (rel > c.rtol) return THM_ENOCONV;
+    return THM_OK;
+}
+
+void fill_stats(const RunStats& rs, double rel, double sec, thm_stats* stats) {
+    if (!stats) return;
+    stats->outer_iters = rs.outer;
+    stats->sweeps = rs.sweeps;
+    stats->refine_steps = rs.refine;
+    stats->inner_iters = rs.inner;
+    stats->dof_iters = rs.dof_iters;
+    stats->max_inner_iters = rs.max_inner;
+    stats->rel_residual = rel;
+    stats->seconds = sec;
+}
+
+void prepare(thm_sys* s, const SolveCfg& c) {
+    ensure_factor(s, c.fp32);
+    ensure_work(s, c.fp32, c.m_in, c.m_out);
+}
+
+int solve(thm_sys* s, const thm_solve_opts* opts, double2* u, thm_stats* stats) {
+    auto t0 = std::chrono::steady_clock::now();
+    SolveCfg c = make_cfg(opts);
+    prepare(s, c);
+    RunStats rs;
+    double rel = 0;
+    int rc = solve_rhs(s, c, s->f_loc.p, s->uD.p, u, rs, rel);
+    double sec = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    fill_stats(rs, rel, sec, stats);
+    return rc;
+}
+
+// ---- diagnostics -----------------------------------------------------------
+void apply_local(thm_sys* s, int op, int mode, const double2* x, double2* y) {
+    bool f32 = mode == THM_MODE_MIXED;
+    THM_REQUIRE(op == THM_OP_T || op == THM_OP_PINV || op == THM_OP_KLOC, "unknown op");
+    if (op == THM_OP_PINV) {
+        ensure_factor(s, f32);
+        apply_Pinv_mode<double2>(s, f32, x, y);
+    } else {
+        int use_bs = op == THM_OP_T;
+        if (f32) apply_T<double2, float>(s, s->val32.p, s->bg32.p, s->bs32.p, use_bs, x, y);
+        else apply_T<double2, double>(s, s->val64.p, s->bg64.p, s->bs64.p, use_bs, x, y);
+    }
+    THM_CUDA(cudaGetLastError());
+    THM_CUDA(cudaStreamSynchronize(s->st));
+}
+
+int sweep_diag(thm_sys* s, const thm_solve_opts* opts, int with_sources, const double2* g_in, double2* g_out,
+               double2* uloc, thm_stats* stats) {
+    SolveCfg c = make_cfg(opts);
+    ensure_factor(s, c.fp32);
+    ensure_work(s, c.fp32, c.m_in, c.m_out);
+    RunStats rs;
+    sweep(s, c, with_sources ? s->f_loc.p : nullptr, g_in, g_out, uloc, rs);
+    THM_CUDA(cudaStreamSynchronize(s->st));
+    if (stats) {
+        memset(stats, 0, sizeof(*stats));
+        stats->sweeps = rs.sweeps;
+        stats->inner_iters = rs.inner;
+        stats->dof_iters = rs.dof_iters;
+        stats->max_inner_iters = rs.max_inner;
+    }
+    return rs.status;
+}
+
+}  // namespace thm
+
+thm_sys::~thm_sys() { delete w; }

@@ -1,0 +1,80 @@
+"""GPU adjoint (thm_adjoint and the autograd wrapper) against the FP64 oracle
+adjoint and central finite differences through the GPU solve."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import adjoint as adj
+from oracle import fem
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2105_11993_gb300 import build
+    build.build()
+
+
+def _setup(order, oblique=False):
+    P = W.square_problem(8, 2, order, 9.0, mu_inv=W.mu_inv_lognormal(64, 0.3, "gadj"), relabel=True,
+                         rotate_cells=True)
+    if oblique:
+        P.direction = np.array([0.6, 0.8])
+    S = fem.assemble(P)
+    X = P.mesh.coords[P.mesh.cells].mean(1)
+    region = np.flatnonzero((X[:, 0] > 0.3) & (X[:, 0] < 0.7) & (X[:, 1] > 0.3) & (X[:, 1] < 0.7))
+    MR = adj.region_mass(P, S, region)
+    return P, S, MR
+
+
+@pytest.mark.parametrize("order,oblique", [(1, False), (2, False), (1, True)])
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+def test_adjoint_matches_oracle_adjoint(order, oblique, mode):
+    import paper_2105_11993_gb300 as thm
+    P, S, MR = _setup(order, oblique)
+    mesh = thm.Mesh.from_workload(P.mesh, P.order)
+    sysg = thm.System(mesh, P.mu_inv, P.omega, P.kappa, P.pol, P.direction)
+    u, _ = sysg.solve(mode=mode, rtol=1e-12 if mode == "fp64" else 1e-11)
+    uh = u.cpu().numpy()
+    a = MR @ np.conj(uh)
+    g_mu, g_w, st = sysg.adjoint(u, torch.tensor(a, device="cuda"), mode=mode, rtol=1e-12 if mode == "fp64" else 1e-11)
+    g_ref, gw_ref, _ = adj.adjoint_gradients(P, S, fem.solve_monolithic(S), MR @ np.conj(fem.solve_monolithic(S)))
+    g_mu = g_mu.cpu().numpy()
+    assert np.linalg.norm(g_mu - g_ref) <= 1e-8 * np.linalg.norm(g_ref)
+    assert abs(g_w - gw_ref) <= 1e-8 * abs(gw_ref)
+
+
+def test_adjoint_vs_central_differences_and_autograd():
+    """North-star check: dL/dmu^{-1} and dL/domega against central differences
+    (h = 1e-4) of the GPU solve itself, to 1e-5 relative."""
+    import paper_2105_11993_gb300 as thm
+    from paper_2105_11993_gb300 import autograd as ag
+    P, S, MR = _setup(2)
+    mesh = thm.Mesh.from_workload(P.mesh, P.order)
+    MRt = torch.tensor(MR.toarray(), dtype=torch.complex128, device="cuda")
+    mu = torch.tensor(P.mu_inv, device="cuda", requires_grad=True)
+    om = torch.tensor(P.omega, dtype=torch.float64, requires_grad=True)
+
+    def L_of(mu_t, omega):
+        u = ag.solve(mesh, mu_t, omega, P.kappa, P.pol, P.direction, rtol=1e-13)
+        return torch.real(torch.vdot(u, MRt @ u))
+
+    L = L_of(mu, om)
+    L.backward()
+    g_mu = mu.grad.cpu().numpy()
+    g_w = float(om.grad)
+    rng = np.random.default_rng(5)
+    h = 1e-4
+    scale = np.abs(g_mu).max()
+    with torch.no_grad():
+        for c in rng.choice(P.mesh.n_cell, 5, replace=False):
+            mp = mu.detach().clone(); mp[c] += h
+            mm = mu.detach().clone(); mm[c] -= h
+            fd = (float(L_of(mp, P.omega)) - float(L_of(mm, P.omega))) / (2 * h)
+            assert abs(g_mu[c] - fd) <= 1e-5 * max(abs(fd), 1e-3 * scale)
+        fdw = (float(L_of(mu.detach(), P.omega + h)) - float(L_of(mu.detach(), P.omega - h))) / (2 * h)
+        assert abs(g_w - fdw) <= 1e-5 * abs(fdw)
