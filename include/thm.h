@@ -138,6 +138,10 @@ typedef struct thm_solve_opts {
     double outer_tol;      /* interface GMRES relative tolerance (<=0: 1e-9) */
     int    outer_maxit;    /* (<=0: 2000) */
     int    max_refine;     /* iterative-refinement steps (<=0: 6) */
+    int    relax;          /* 1: inexact-Krylov relaxation of the subdomain tolerance as the
+                              interface residual falls (clamp(outer_tol/||r_k||, inner_tol,
+                              1e-3)); the refinement on the FP64 residual still decides
+                              convergence.  0: fixed inner_tol */
 } thm_solve_opts;
 
 typedef struct thm_stats {

@@ -36,7 +36,8 @@ class ThmError(RuntimeError):
 class SolveOptions(C.Structure):
     _fields_ = [("mode", C.c_int), ("rtol", C.c_double), ("inner_restart", C.c_int),
                 ("inner_tol", C.c_double), ("inner_maxit", C.c_int), ("outer_restart", C.c_int),
-                ("outer_tol", C.c_double), ("outer_maxit", C.c_int), ("max_refine", C.c_int)]
+                ("outer_tol", C.c_double), ("outer_maxit", C.c_int), ("max_refine", C.c_int),
+                ("relax", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -179,10 +180,10 @@ class Mesh:
 
 
 def _opts(mode="fp64", rtol=1e-8, inner_restart=0, inner_tol=0.0, inner_maxit=0, outer_restart=0,
-          outer_tol=0.0, outer_maxit=0, max_refine=0):
+          outer_tol=0.0, outer_maxit=0, max_refine=0, relax=0):
     m = {"fp64": MODE_FP64, "mixed": MODE_MIXED}[mode] if isinstance(mode, str) else int(mode)
     return SolveOptions(m, rtol, inner_restart, inner_tol, inner_maxit, outer_restart, outer_tol,
-                        outer_maxit, max_refine)
+                        outer_maxit, max_refine, int(relax))
 
 
 class System:

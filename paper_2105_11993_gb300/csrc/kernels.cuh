@@ -92,9 +92,16 @@ struct TileCursor {
     int r0;    // -1: coupling tile; otherwise first row of a W tile
 };
 
+// Row-tile height of a level of m rows: at most R rows, tiles of nearly
+// equal height, every tile start a multiple of 4 rows (16-byte aligned rows).
+__device__ __forceinline__ int tile_rows(int m, int R) {
+    const int nt = (m + R - 1) / R;
+    return (((m + nt - 1) / nt) + 3) / 4 * 4;
+}
+
 __device__ __forceinline__ void tile_next(TileCursor& c, int nlev, const int* msz, int R) {
     if (c.r0 < 0) { c.r0 = 0; return; }
-    c.r0 += R;
+    c.r0 += tile_rows(msz[c.l], R);
     if (c.r0 < msz[c.l]) return;
     c.r0 = -1;
     if (c.dir == 0) {
@@ -135,33 +142,42 @@ __global__ void __launch_bounds__(512) k_bt_apply(const Sub* __restrict__ subs, 
     R_t* su = vec + ((max_ne + 3) / 4) * 4;
     int* msz = reinterpret_cast<int*>(su + ((max_m + 3) / 4) * 4);   // [max_lev] level sizes
     int* mst = msz + max_lev;                                          // level starts (relative)
+    int* enz = mst + max_lev;                                          // coupling entries E, F
+    int* fnz = enz + max_lev;
+    long long* offw = reinterpret_cast<long long*>(fnz + max_lev);   // 16-byte aligned: 4*max_lev ints precede
+    long long* eptr = offw + max_lev;
+    long long* eoff = eptr + max_lev;
+    long long* fptr = eoff + max_lev;
+    long long* foff = fptr + max_lev;
     const Sub S = subs[blockIdx.x];
     const int comp = blockIdx.y;
     const R_t* x = reinterpret_cast<const R_t*>(xin) + comp;     // stride 2
     R_t* y = reinterpret_cast<R_t*>(yout) + comp;
     const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5, lane = threadIdx.x & 31;
     for (int l = threadIdx.x; l < S.nlev; l += blockDim.x) {
-        msz[l] = levels[S.lev0 + l].size;
-        mst[l] = (int)(levels[S.lev0 + l].start - S.off);
+        const Level L = levels[S.lev0 + l];
+        msz[l] = L.size;
+        mst[l] = (int)(L.start - S.off);
+        enz[l] = L.enz; fnz[l] = L.fnz;
+        offw[l] = L.offW; eptr[l] = L.eptr; eoff[l] = L.eoff; fptr[l] = L.fptr; foff[l] = L.foff;
     }
     __syncthreads();
 
     auto issue = [&](const TileCursor& c, int t) {
         if (c.dir < 2) {
             unsigned char* dst = slots + (size_t)(t % nslot) * slot_bytes;
-            const Level& L = levels[S.lev0 + c.l];
             const int m = msz[c.l];
             if (c.r0 < 0) {
                 const bool fwd = c.dir == 0;
-                const int64_t po = fwd ? L.eptr : L.fptr, qo = fwd ? L.eoff : L.foff;
-                const int nz = fwd ? L.enz : L.fnz;
+                const int64_t po = fwd ? eptr[c.l] : fptr[c.l], qo = fwd ? eoff[c.l] : foff[c.l];
+                const int nz = fwd ? enz[c.l] : fnz[c.l];
                 const int pw = ((m + 1 + 3) / 4) * 4, cw = ((nz + 3) / 4) * 4;
                 stage_words(dst, cptr + po, m + 1);
                 stage_words(dst + 4 * (size_t)pw, ccol + qo, nz);
                 stage_words(dst + 4 * (size_t)pw + 4 * (size_t)cw, cval + qo, (int64_t)nz * (int64_t)(sizeof(F) / 4));
             } else {
-                const int nr = min(R, m - c.r0);
-                stage_words(dst, fac + L.offW + (int64_t)c.r0 * m, (int64_t)nr * m * (int64_t)(sizeof(F) / 4));
+                const int nr = min(tile_rows(m, R), m - c.r0);
+                stage_words(dst, fac + offw[c.l] + (int64_t)c.r0 * m, (int64_t)nr * m * (int64_t)(sizeof(F) / 4));
             }
         }
         cp_async_commit();
@@ -201,8 +217,7 @@ __global__ void __launch_bounds__(512) k_bt_apply(const Sub* __restrict__ subs, 
             const int* P = reinterpret_cast<const int*>(buf);
             const int pw = ((m + 1 + 3) / 4) * 4;
             const int* C = P + pw;
-            const Level& L = levels[S.lev0 + cur.l];
-            const int nz = cur.dir == 0 ? L.enz : L.fnz;
+            const int nz = cur.dir == 0 ? enz[cur.l] : fnz[cur.l];
             const F* Vv = reinterpret_cast<const F*>(C + ((nz + 3) / 4) * 4);
             if (cur.dir == 0) {
                 const int op = cur.l > 0 ? mst[cur.l - 1] : 0;
@@ -221,7 +236,7 @@ __global__ void __launch_bounds__(512) k_bt_apply(const Sub* __restrict__ subs, 
             }
         } else {
             const F* W = reinterpret_cast<const F*>(buf);
-            const int nr = min(R, m - cur.r0);
+            const int nr = min(tile_rows(m, R), m - cur.r0);
             for (int i = warp; i < nr; i += nw) {
                 R_t v = warp_dot<F, R_t>(W + (int64_t)i * m, su, m);
                 if (lane == 0) {
@@ -275,33 +290,6 @@ __global__ void __launch_bounds__(KT) k_chunk_dots(const Chunk* __restrict__ chu
     }
     const bool full = c.end - c.begin == CHUNK;
     int k = 0;
-    for (; k + 1 < nk; k += 2) {               // two basis vectors per pass: more loads in flight
-        const V* v0 = basis + (int64_t)k * ld;
-        const V* v1 = v0 + ld;
-        R a0 = 0, b0 = 0, a1 = 0, b1 = 0;
-#pragma unroll
-        for (int q = 0; q < EPT; ++q) {
-            int64_t e = c.begin + threadIdx.x + (int64_t)q * KT;
-            if (full || e < c.end) {
-                V p = v0[e], u = v1[e];
-                a0 += p.x * wr[q].x + p.y * wr[q].y;
-                b0 += p.x * wr[q].y - p.y * wr[q].x;
-                a1 += u.x * wr[q].x + u.y * wr[q].y;
-                b1 += u.x * wr[q].y - u.y * wr[q].x;
-            }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            a0 += __shfl_down_sync(0xffffffffu, a0, o);
-            b0 += __shfl_down_sync(0xffffffffu, b0, o);
-            a1 += __shfl_down_sync(0xffffffffu, a1, o);
-            b1 += __shfl_down_sync(0xffffffffu, b1, o);
-        }
-        if (lane == 0) {
-            sred[k * (KT / 32) + warp] = make_double2((double)a0, (double)b0);
-            sred[(k + 1) * (KT / 32) + warp] = make_double2((double)a1, (double)b1);
-        }
-    }
     for (; k < nk; ++k) {
         const V* vk = basis + (int64_t)k * ld;
         R ar = 0, ai = 0;

@@ -266,8 +266,23 @@ struct Krylov {
     DArr<int> active, kused, nact, flag;
     int* h_pinned = nullptr;
     std::vector<int> h_kused;
+    // asynchronous convergence monitor: per Arnoldi step the active-segment
+    // count and the breakdown flag land in a pinned ring; the host reads them
+    // a few steps behind the GPU instead of blocking every step
+    static constexpr int RING = 4;
+    int* h_ring = nullptr;
+    double2* h_gring = nullptr;      // g_{j+1} of segment 0 (residual estimate)
+    double h_beta0 = 0;              // ||r_0|| of segment 0 at the first cycle
+    double last_rel = 1.0;           // latest residual estimate of segment 0 seen by the host, relative
+    cudaEvent_t ring_ev[RING] = {};
 
-    ~Krylov() { if (h_pinned) cudaFreeHost(h_pinned); }
+    ~Krylov() {
+        if (h_pinned) cudaFreeHost(h_pinned);
+        if (h_ring) cudaFreeHost(h_ring);
+        if (h_gring) cudaFreeHost(h_gring);
+        for (auto& e : ring_ev)
+            if (e) cudaEventDestroy(e);
+    }
 
     void init(int64_t n_, int nseg_, int m_, const std::vector<Chunk>& chunks, const Chunk* dch,
               const std::vector<int64_t>& segn, bool flexible_ = false) {
@@ -291,6 +306,11 @@ struct Krylov {
         nrm_part.alloc(nch); nrm.alloc(nseg); beta.alloc(nseg); target.alloc(nseg); prev.alloc(nseg);
         active.alloc(nseg); kused.alloc(nseg); nact.alloc(1); flag.alloc(1);
         if (!h_pinned) THM_CUDA(cudaMallocHost(&h_pinned, 2 * sizeof(int)));
+        if (!h_ring) {
+            THM_CUDA(cudaMallocHost(&h_ring, 2 * RING * sizeof(int)));
+            THM_CUDA(cudaMallocHost(&h_gring, RING * sizeof(double2)));
+            for (auto& e : ring_ev) THM_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        }
         size_t dots_smem = (size_t)(m + 1) * (KT / 32) * sizeof(double2);
         THM_REQUIRE(dots_smem <= 200 * 1024, "restart length too large");
         THM_CUDA(cudaFuncSetAttribute(k_chunk_dots<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dots_smem));
@@ -331,11 +351,18 @@ struct Krylov {
             nact.zero(st);
             THM_LAUNCH(THM_K_KRYLOV, st, k_cycle_start<<<nblk(nseg), 256, 0, st>>>(nseg, m, nrm.p, tol, first ? 1 : 0, target.p, beta.p,
                                                       active.p, kused.p, gv.p, nact.p, prev.p));
+            if (first && nseg == 1) {
+                double b0 = 0;
+                THM_CUDA(cudaMemcpyAsync(&b0, beta.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+                THM_CUDA(cudaStreamSynchronize(st));
+                h_beta0 = b0;
+                last_rel = 1.0;
+            }
             first = false;
             if (read_nact(st) == 0) break;
             if (total >= maxit) { ks.status = THM_ENOCONV; break; }
             THM_LAUNCH(THM_K_KRYLOV, st, k_chunk_scale<V><<<nch, 256, 0, st>>>(d_chunks, r.p, beta.p, basis.p));
-            int j = 0;
+            int j = 0, checked = 0;
             for (; j < m && total < maxit; ++j) {
                 V* vj = basis.p + (int64_t)j * n;
                 const V* zin = vj;
@@ -356,11 +383,31 @@ struct Krylov {
                                                      target.p, active.p, kused.p, beta.p, nact.p, flag.p));
                 THM_LAUNCH(THM_K_KRYLOV, st, k_chunk_scale<V><<<nch, 256, 0, st>>>(d_chunks, w.p, beta.p, basis.p + (int64_t)(j + 1) * n));
                 ++total;
-                int na = read_nact(st);
-                if (h_pinned[1]) { ks.status = THM_EBREAKDOWN; break; }
-                if (na == 0) { ++j; break; }
+                // monitor: copy (active count, breakdown flag) of step j into the ring
+                const int slot = j % RING;
+                THM_CUDA(cudaMemcpyAsync(h_ring + 2 * slot, nact.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+                THM_CUDA(cudaMemcpyAsync(h_ring + 2 * slot + 1, flag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+                if (nseg == 1)
+                    THM_CUDA(cudaMemcpyAsync(h_gring + slot, gv.p + j + 1, sizeof(double2), cudaMemcpyDeviceToHost, st));
+                THM_CUDA(cudaEventRecord(ring_ev[slot], st));
+                // read every finished step; block only when the ring is full
+                bool stop = false;
+                while (checked <= j) {
+                    const int rs_ = checked % RING;
+                    cudaError_t q = (j - checked >= RING - 1) ? cudaEventSynchronize(ring_ev[rs_]) : cudaEventQuery(ring_ev[rs_]);
+                    if (q == cudaErrorNotReady) break;
+                    THM_CUDA(q);
+                    if (h_ring[2 * rs_ + 1]) { ks.status = THM_EBREAKDOWN; stop = true; break; }
+                    if (nseg == 1 && h_beta0 > 0) last_rel = std::hypot(h_gring[rs_].x, h_gring[rs_].y) / h_beta0;
+                    if (h_ring[2 * rs_] == 0) { stop = true; break; }
+                    ++checked;
+                }
+                if (stop) break;
             }
-            THM_CUDA(cudaGetLastError());
+            // drain the monitor: any later step may still report breakdown
+            THM_CUDA(cudaStreamSynchronize(st));
+            for (; checked < j && ks.status != THM_EBREAKDOWN; ++checked)
+                if (h_ring[2 * (checked % RING) + 1]) ks.status = THM_EBREAKDOWN;            THM_CUDA(cudaGetLastError());
             // x += M (V y)
             THM_LAUNCH(THM_K_KRYLOV, st, k_backsolve<<<nblk(nseg), 64, 0, st>>>(nseg, m, Rm.p, gv.p, kused.p, y.p));
             if (flexible && M) {
@@ -459,6 +506,9 @@ SolveCfg make_cfg(const thm_solve_opts* o) {
     c.outer_maxit = (o && o->outer_maxit > 0) ? o->outer_maxit : 2000;
     c.max_refine = (o && o->max_refine > 0) ? o->max_refine : 6;
     c.inner_tol = (o && o->inner_tol > 0) ? o->inner_tol : 1e-11;
+    c.cycle_tol = 1e-5;
+    c.relax = o ? o->relax : 0;
+    if (const char* e = getenv("THM_CYCLE_TOL")) c.cycle_tol = atof(e);
     c.outer_tol = (o && o->outer_tol > 0) ? o->outer_tol : 1e-9;
     return c;
 }
@@ -478,7 +528,8 @@ static void apply_Pinv(const thm_sys* s, const F* fac, const F* cval, const int3
     auto r4 = [](int64_t v) { return (int64_t)((v + 3) / 4 * 4); };
     int max_lev = 0;
     for (const auto& S : m->subs) max_lev = std::max(max_lev, S.nlev);
-    const size_t tail = (size_t)(r4(m->max_ne) + r4(m->max_m)) * sizeof(R) + 2 * (size_t)r4(max_lev) * sizeof(int);
+    const size_t tail = (size_t)(r4(m->max_ne) + r4(m->max_m)) * sizeof(R) + 4 * (size_t)(max_lev + 1) * sizeof(int) +
+                        5 * (size_t)max_lev * sizeof(long long) + 16;
     const size_t csr = (size_t)r4(m->max_m + 1) * 4 + (size_t)r4(m->max_cnz) * (4 + sizeof(F)) + 16;
     const size_t cap = 220 * 1024;
     THM_REQUIRE(tail + 3 * csr <= cap, "subdomain too large for the shared-memory block solve");
@@ -559,7 +610,7 @@ static void subdomain_solves(thm_sys* s, const SolveCfg& c, const double2* b, do
             std::vector<int> na;
             w->nact_ir.download(na, st);
             if (na[0] == 0) break;
-            KStats ks = K.solve(A, M, w->b32.p, w->x32.p, true, 1e-5, c.m_in, st, true);
+            KStats ks = K.solve(A, M, w->b32.p, w->x32.p, true, c.cycle_tol, c.m_in, st, true);
             ks.status = THM_OK;      // the refinement loop owns convergence
             add(rs, ks);
             THM_LAUNCH(THM_K_DDM, st, k_ir_update<<<nblk(m->n_loc), 256, 0, st>>>(m->n_loc, w->x32.p, x));
@@ -598,7 +649,14 @@ static void ddm_solve(thm_sys* s, const SolveCfg& c, const double2* src, double2
     w->g0.zero(st);
     sweep(s, c, src, w->g0.p, w->gb.p, uloc, rs);
     auto A = [&](const double2* v, double2* out) {
-        sweep(s, c, nullptr, v, w->gtmp.p, w->ytmp.p, rs);
+        SolveCfg cr = c;
+        if (c.relax) {
+            // inexact Krylov: the sweep may be as inaccurate as the outer
+            // residual is small (GMRES tolerates matvec errors ~ tol / ||r_k||)
+            double eta = c.outer_tol / std::max(w->outer.last_rel, 1e-300);
+            cr.inner_tol = std::min(1e-3, std::max(c.inner_tol, eta));
+        }
+        sweep(s, cr, nullptr, v, w->gtmp.p, w->ytmp.p, rs);
         THM_LAUNCH(THM_K_KRYLOV, st, k_sub<double2><<<nblk(m->n_if), 256, 0, st>>>(m->n_if, v, w->gtmp.p, out));   // (I - A) v
     };
     std::function<void(const double2*, double2*)> none;

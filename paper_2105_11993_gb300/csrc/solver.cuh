@@ -8,7 +8,9 @@ namespace thm {
 struct SolveCfg {
     bool fp32;
     double inner_tol, outer_tol, rtol;
+    double cycle_tol;          // mixed: relative tolerance of one FP32 GMRES cycle
     int m_in, m_out, inner_maxit, outer_maxit, max_refine;
+    int relax;
 };
 
 struct RunStats {
