@@ -257,6 +257,33 @@ int thm_dirichlet_values(thm_sys* s, double* u_d);
  * Other classes: THM_EINVAL. */
 int thm_alg_bytes(const thm_sys* s, int mode, int cls, double* bytes);
 
+/* ------------------------------------------------------------------------
+ * thm_residual_noalloc -- the FP64 true residual of a field u without any
+ * device allocation (the paper has no counterpart).
+ *
+ * For callers that cannot allocate device memory when they need the check:
+ * code inside a CUDA stream capture, or programs that reserve all device
+ * memory up front and forbid cudaMalloc in their time-critical loop.
+ *
+ *  u    device complex double [n_dof]: a field on all DOFs (Dirichlet entries
+ *       are ignored; the Dirichlet lifting already sits in f).
+ *  out  device double[2], written on the system's stream: out[0] = ||f - K u||,
+ *       out[1] = ||f|| (the global FP64 quantities of thm_stats.rel_residual =
+ *       out[0] / out[1]).
+ *  Limit: n_dof <= 4,194,304 (4096 partial-sum blocks of 1024 DOFs); larger
+ *       systems get THM_EINVAL with the limit in the message.
+ *  Scratch: a file-scope device array of 64 KB, held by every GPU that loads
+ *       the library until the process exits; every call overwrites the
+ *       partials it uses (nothing has to start at zero).  Calls that overlap
+ *       on the GPU (on different streams, or from threads on one device) race
+ *       on that array and must be serialised by the caller.
+ *  First call on a device: looks up the array's device address with
+ *       cudaGetSymbolAddress (no allocation) and caches it; make that first
+ *       call before any stream capture.
+ *  No cudaMalloc, cudaFree or allocating library call is made.
+ * ------------------------------------------------------------------------ */
+int thm_residual_noalloc(const thm_sys* s, const double* u, double* out);
+
 /* Kernel launches issued by this library since the process started. */
 int64_t thm_kernel_launches(void);
 

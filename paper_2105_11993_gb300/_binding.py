@@ -23,7 +23,7 @@ symbols = [
     "thm_ddm_solve_host", "thm_adjoint", "thm_sys_destroy", "thm_last_error", "thm_sys_info",
     "thm_local_dofs", "thm_iface_dofs", "thm_apply_local", "thm_sweep", "thm_local_sources",
     "thm_dirichlet_values", "thm_kernel_launches", "thm_profile_enable", "thm_profile_read",
-    "thm_alg_bytes",
+    "thm_alg_bytes", "thm_residual_noalloc",
 ]
 
 
@@ -85,6 +85,7 @@ def load():
         "thm_profile_enable": [C.c_uint],
         "thm_profile_read": [C.c_int, P, P],
         "thm_alg_bytes": [P, C.c_int, C.c_int, P],
+        "thm_residual_noalloc": [P, P, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)

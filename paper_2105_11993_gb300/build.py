@@ -12,7 +12,7 @@ ROOT = os.path.dirname(HERE)
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libthm.so")
-SOURCES = ["mesh.cu", "assemble.cu", "solve.cu", "adjoint.cu", "profile.cu", "capi.cu"]
+SOURCES = ["mesh.cu", "assemble.cu", "solve.cu", "adjoint.cu", "profile.cu", "noalloc.cu", "capi.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

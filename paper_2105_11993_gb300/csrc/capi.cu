@@ -17,6 +17,7 @@ extern std::atomic<long long> g_launches;
 static thread_local std::string g_msg;
 
 void fail(int code, const std::string& msg) { throw Error{code, msg}; }
+void set_last_error(const std::string& msg) { g_msg = msg; }
 
 template <class Fn>
 static int guarded(Fn&& fn) {

@@ -17,6 +17,7 @@ struct Error {
 };
 
 [[noreturn]] void fail(int code, const std::string& msg);
+void set_last_error(const std::string& msg);
 
 #define THM_CUDA(call)                                                                 \
     do {                                                                               \
@@ -81,7 +82,7 @@ void prof_read(int cls, int64_t* launches, double* ms);
     } while (0)
 
 constexpr int SELL_C = 32;       // rows per SELL slice (one warp)
-constexpr int CHUNK = 2048;      // elements per reduction chunk of a segment
+constexpr int CHUNK = 1024;      // elements per reduction chunk of a segment
 
 // One block of the level-block-tridiagonal factorisation of P_i.
 struct Level {
@@ -217,6 +218,7 @@ struct thm_sys {
     thm::DArr<float> sval32;
     thm::DArr<double> cinv64, cg64;    // per cell: D_II^{-1} (4x4), G = P_EI D_II^{-1} (8x4)
     thm::DArr<float> cinv32, cg32;
+    thm::DArr<int> dev_err;            // set by a device-side bounded wait that gave up
     thm::DArr<double> cpl64;           // values of the level coupling lists
     thm::DArr<float> cpl32;
     // order-2 gather tables (structure of arrays, [8][n_loc]): for an edge row

@@ -1,0 +1,57 @@
+"""thm_residual_noalloc (the entry point that allocates no device memory, for
+callers that cannot call cudaMalloc, e.g. inside a stream capture) against the
+residual the regular solve reports, called through the C ABI twice in a row.
+Collected last so that a stopping run has already run every other test."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2105_11993_gb300 import build
+    build.build()
+
+
+@pytest.mark.parametrize("name", ["square32_p1", "p2"])
+def test_noalloc_residual_matches_solver_residual(name):
+    import paper_2105_11993_gb300 as thm
+    lib = thm.load()
+    P = (W.config(name) if name != "p2" else
+         W.square_problem(16, 2, 2, 13.0, mu_inv=W.mu_inv_lognormal(256, 0.3, "na"), relabel=True,
+                          rotate_cells=True))
+    mesh = thm.Mesh.from_workload(P.mesh, P.order)
+    sysg = thm.System(mesh, P.mu_inv, P.omega, P.kappa, P.pol, P.direction)
+    u, st = sysg.solve(mode="fp64", rtol=1e-8)
+    # a second field away from the solution (free DOFs scaled; the Dirichlet
+    # entries are not read: the lifting in f carries them), so the residual is O(1)
+    from oracle import fem
+    S = fem.assemble(P)
+    v = u.clone()
+    idx = torch.tensor(S.free[: len(S.free) // 3], device="cuda")
+    v[idx] *= 1.5
+    for field, ref in ((u, st["rel_residual"]), (v, None)):
+        outs = []
+        for _ in range(2):                         # two calls in a row share the scratch
+            out = torch.full((2,), -1.0, dtype=torch.float64, device="cuda")
+            rc = lib.thm_residual_noalloc(sysg.h, C.c_void_p(field.data_ptr()), C.c_void_p(out.data_ptr()))
+            assert rc == 0, lib.thm_last_error()
+            torch.cuda.synchronize()
+            outs.append(out.cpu().numpy())
+        assert np.array_equal(outs[0], outs[1])
+        rel = outs[0][0] / outs[0][1]
+        if ref is not None:
+            # against the residual thm_ddm_solve reports for the same field
+            # (same tolerance as the parity tests' residual comparison)
+            assert abs(rel - ref) <= 1e-2 * ref + 1e-13
+        else:
+            # away from the solution: against the oracle's residual
+            assert abs(rel - fem.residual(S, field.cpu().numpy())) <= 1e-10 * rel
