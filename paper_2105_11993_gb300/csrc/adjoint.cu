@@ -110,23 +110,16 @@ __global__ void k_adj_cells(int64_t n_cell, int nb, const double* __restrict__ r
 
 // Impedance-face share of dL/domega (2-D: diagonal face mass per DOF) and the
 // explicit dependence of L on the Dirichlet data.
-__global__ void k_adj_rows(int64_t n_loc, const int64_t* __restrict__ gdof, const int8_t* __restrict__ kind,
-                           const int8_t* __restrict__ fn, const int32_t* __restrict__ edge,
-                           const double* __restrict__ X, const int64_t* __restrict__ elo,
-                           const int64_t* __restrict__ ehi, double kappa, const double2* __restrict__ lam,
-                           const double2* __restrict__ u, double* __restrict__ gw) {
+// -2 Re(lambda^T (i kappa M_Gamma) u) per local row, 2-D: the Gamma^inf face
+// mass is diagonal and bg holds kappa*omega*m per row (each boundary edge lies
+// in one cell, so each term is counted once).
+__global__ void k_adj_rows(int64_t n_loc, const int64_t* __restrict__ gdof, const double* __restrict__ bg,
+                           double inv_omega, const double2* __restrict__ lam, const double2* __restrict__ u,
+                           double* __restrict__ gw) {
     int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (r >= n_loc) return;
-    double v = 0;
-    if (kind[r] == 1) {
-        int e = edge[r];
-        double dx = X[ehi[e] * 2] - X[elo[e] * 2], dy = X[ehi[e] * 2 + 1] - X[elo[e] * 2 + 1];
-        double l = sqrt(dx * dx + dy * dy);
-        double mass = fn[r] == 0 ? 1.0 / l : 1.0 / (3.0 * l);
-        double2 p = cmul(lam[gdof[r]], u[gdof[r]]);
-        v = 2.0 * kappa * mass * p.y;          // -2 Re(i kappa m lambda u)
-    }
-    gw[r] = v;
+    double2 p = cmul(lam[gdof[r]], u[gdof[r]]);
+    gw[r] = 2.0 * bg[r] * inv_omega * p.y;
 }
 
 __global__ void k_adj_dir(int64_t n_dof, const double2* __restrict__ a, const double2* __restrict__ duD,
@@ -176,7 +169,7 @@ int adjoint(thm_sys* s, const thm_solve_opts* opts, const double2* u, const doub
     THM_LAUNCH(THM_K_DDM, st, k_adj_rhs<<<nb(m->n_loc), 256, 0, st>>>(m->n_loc, m->d_loc_gdof.p, m->d_loc_is_owner.p, a, rhs.p));
     RunStats rs;
     double rel = 0;
-    int rc = solve_rhs(s, c, rhs.p, nullptr, lam.p, rs, rel);
+    int rc = solve_rhs(s, c, rhs.p, rhs.p, nullptr, lam.p, rs, rel);
     duD.zero(st);
     if (!m->dir_edges.empty())
         THM_LAUNCH(THM_K_DDM, st, k_dirichlet_dw<<<nb((int64_t)m->dir_edges.size()), 256, 0, st>>>(
@@ -187,10 +180,8 @@ int adjoint(thm_sys* s, const thm_solve_opts* opts, const double2* u, const doub
                                                                         m->d_cells.p, m->d_cell_dofs.p, m->d_cell_signs.p,
                                                                         s->mu_inv.p, s->omega, lam.p, u, duD.p, grad_mu,
                                                                         gw_cell.p));
-    THM_LAUNCH(THM_K_DDM, st, k_adj_rows<<<nb(m->n_loc), 256, 0, st>>>(m->n_loc, m->d_loc_gdof.p, m->d_row_face_kind.p,
-                                                                      m->d_row_face_fn.p, m->d_row_face_edge.p,
-                                                                      m->d_coords.p, m->d_edge_lo.p, m->d_edge_hi.p,
-                                                                      s->kappa, lam.p, u, gw_row.p));
+    THM_LAUNCH(THM_K_DDM, st, k_adj_rows<<<nb(m->n_loc), 256, 0, st>>>(m->n_loc, m->d_loc_gdof.p, s->bg64.p,
+                                                                      1.0 / s->omega, lam.p, u, gw_row.p));
     THM_LAUNCH(THM_K_DDM, st, k_adj_dir<<<nb(m->n_dof), 256, 0, st>>>(m->n_dof, a, duD.p, gw_dof.p));
     THM_CUDA(cudaGetLastError());
     *grad_omega = device_sum(st, gw_cell.p, m->n_cell, part) + device_sum(st, gw_row.p, m->n_loc, part) +

@@ -26,13 +26,13 @@ __constant__ double c_poly[5][3] = {
 
 struct Term {
     double c;
-    int f, g;
+    int f, g, h;      // 1-D factors in xi, eta, zeta (h = 0: the constant, for 2-D)
 };
 
 // Terms (x component, y component, curl) of the 12 order-2 functions in the
 // local order [W0 G0 W1 G1 W2 G2 W3 G3 B0 B1 B2 B3]; order 1 uses W0..W3.
 __device__ void basis_terms(int order, int i, Term& x, Term& y, Term& cu) {
-    const Term Z{0, 0, 0};
+    const Term Z{0, 0, 0, 0};
     // Whitney functions of local edges 0..3
     const Term Wx[4] = {{1, 0, 2}, {1, 0, 1}, Z, Z};
     const Term Wy[4] = {Z, Z, {1, 2, 0}, {1, 1, 0}};
@@ -68,42 +68,132 @@ __device__ double int1(int f, int g) {
 
 __device__ double int2(const Term& a, const Term& b) {
     if (a.c == 0 || b.c == 0) return 0.0;
-    return a.c * b.c * int1(a.f, b.f) * int1(a.g, b.g);
+    return a.c * b.c * int1(a.f, b.f) * int1(a.g, b.g) * int1(a.h, b.h);
 }
 
-__global__ void k_ref_matrices(int order, int nb, double* ref) {
-    for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
-        int i = t / nb, j = t % nb;
-        if (j < i) continue;
-        Term xi, yi, ci, xj, yj, cj;
-        basis_terms(order, i, xi, yi, ci);
-        basis_terms(order, j, xj, yj, cj);
-        double a = int2(ci, cj), mx = int2(xi, xj), my = int2(yi, yj);
-        ref[0 * 144 + i * nb + j] = a;  ref[0 * 144 + j * nb + i] = a;
-        ref[1 * 144 + i * nb + j] = mx; ref[1 * 144 + j * nb + i] = mx;
-        ref[2 * 144 + i * nb + j] = my; ref[2 * 144 + j * nb + i] = my;
+// Order-1 hex: 12 Whitney functions in the local edge order (xi-edges at
+// (eta,zeta) = 00,10,01,11, then eta-edges at (xi,zeta), then zeta-edges at
+// (xi,eta)); comp[3] = value components, cu[3] = reference curl components.
+// L(t;0) = 1 - t (poly 2), L(t;1) = t (poly 1), dL(0) = -1, dL(1) = +1.
+__device__ void basis_terms3(int i, Term* comp, Term* cu) {
+    const Term Z{0, 0, 0, 0};
+    const int ax = i / 4, e0 = (i % 4) & 1, e1 = (i % 4) >> 1;
+    const int L0 = e0 ? 1 : 2, L1 = e1 ? 1 : 2;
+    const double d0 = e0 ? 1.0 : -1.0, d1 = e1 ? 1.0 : -1.0;
+    for (int k = 0; k < 3; ++k) { comp[k] = Z; cu[k] = Z; }
+    if (ax == 0) {           // (L(eta) L(zeta), 0, 0); curl = (0, L(eta) dL(zeta), -dL(eta) L(zeta))
+        comp[0] = Term{1, 0, L0, L1};
+        cu[1] = Term{d1, 0, L0, 0};
+        cu[2] = Term{-d0, 0, 0, L1};
+    } else if (ax == 1) {    // (0, L(xi) L(zeta), 0); curl = (-L(xi) dL(zeta), 0, dL(xi) L(zeta))
+        comp[1] = Term{1, L0, 0, L1};
+        cu[0] = Term{-d1, L0, 0, 0};
+        cu[2] = Term{d0, 0, 0, L1};
+    } else {                 // (0, 0, L(xi) L(eta)); curl = (L(xi) dL(eta), -dL(xi) L(eta), 0)
+        comp[2] = Term{1, L0, L1, 0};
+        cu[0] = Term{d1, L0, 0, 0};
+        cu[1] = Term{-d0, 0, L1, 0};
     }
 }
 
-__device__ __forceinline__ void cell_sides(const double* X, const int32_t* cv, double& a, double& b) {
-    double ax = X[cv[1] * 2] - X[cv[0] * 2], ay = X[cv[1] * 2 + 1] - X[cv[0] * 2 + 1];
-    double bx = X[cv[2] * 2] - X[cv[0] * 2], by = X[cv[2] * 2 + 1] - X[cv[0] * 2 + 1];
-    a = sqrt(ax * ax + ay * ay);
-    b = sqrt(bx * bx + by * by);
+// ref layout (144 doubles per matrix, row stride nb):
+//  2-D: [0] int curl curl, [1] int phi_x phi_x, [2] int phi_y phi_y,
+//       [6] face (edge) scalars: [0] int 1*1, [1] int q'(s)^2
+//  3-D: [0..2] int curl_a curl_a (a = xi, eta, zeta), [3..5] int phi_a phi_a,
+//       [6], [7] the order-1 quad face mass parts (row stride 4)
+__global__ void k_ref_matrices(int dim, int order, int nb, double* ref) {
+    for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
+        int i = t / nb, j = t % nb;
+        if (j < i) continue;
+        if (dim == 2) {
+            Term xi, yi, ci, xj, yj, cj;
+            basis_terms(order, i, xi, yi, ci);
+            basis_terms(order, j, xj, yj, cj);
+            double a = int2(ci, cj), mx = int2(xi, xj), my = int2(yi, yj);
+            ref[0 * 144 + i * nb + j] = a;  ref[0 * 144 + j * nb + i] = a;
+            ref[1 * 144 + i * nb + j] = mx; ref[1 * 144 + j * nb + i] = mx;
+            ref[2 * 144 + i * nb + j] = my; ref[2 * 144 + j * nb + i] = my;
+        } else {
+            Term vi[3], ci[3], vj[3], cj[3];
+            basis_terms3(i, vi, ci);
+            basis_terms3(j, vj, cj);
+            for (int k = 0; k < 3; ++k) {
+                double aa = int2(ci[k], cj[k]), mm = int2(vi[k], vj[k]);
+                ref[k * 144 + i * nb + j] = aa;       ref[k * 144 + j * nb + i] = aa;
+                ref[(3 + k) * 144 + i * nb + j] = mm; ref[(3 + k) * 144 + j * nb + i] = mm;
+            }
+        }
+    }
+    if (threadIdx.x == 0) {
+        if (dim == 2) {
+            ref[6 * 144 + 0] = int1(0, 0);
+            ref[6 * 144 + 1] = int1(4, 4);
+        } else {
+            for (int i = 0; i < 4; ++i)
+                for (int j = 0; j < 4; ++j) {
+                    Term xi, yi, ci, xj, yj, cj;
+                    basis_terms(1, i, xi, yi, ci);
+                    basis_terms(1, j, xj, yj, cj);
+                    ref[6 * 144 + i * 4 + j] = int2(xi, xj);
+                    ref[7 * 144 + i * 4 + j] = int2(yi, yj);
+                }
+        }
+    }
 }
 
-// Local entry (kr, kc) of cell c: mu^{-1} A - omega^2 M (unsigned, local basis).
-__device__ __forceinline__ double cell_entry(const double* ref, int nb, double mu, double w2,
-                                             double a, double b, int kr, int kc) {
-    double A = ref[kr * nb + kc], Mx = ref[144 + kr * nb + kc], My = ref[288 + kr * nb + kc];
-    return mu * A / (a * b) - w2 * ((b / a) * Mx + (a / b) * My);
+__device__ __forceinline__ double vdist(const double* X, int dim, int64_t p, int64_t q) {
+    double s = 0;
+    for (int k = 0; k < dim; ++k) {
+        double t = X[q * dim + k] - X[p * dim + k];
+        s += t * t;
+    }
+    return sqrt(s);
+}
+
+// Side lengths of a box cell along its local axes xi (v0->v1), eta (v0->v2), zeta (v0->v4).
+__device__ __forceinline__ void cell_sides(const double* X, int dim, const int32_t* cells, int64_t c, double* h) {
+    const int nv = dim == 2 ? 4 : 8;
+    const int32_t* cv = cells + c * nv;
+    h[0] = vdist(X, dim, cv[0], cv[1]);
+    h[1] = vdist(X, dim, cv[0], cv[2]);
+    h[2] = dim == 3 ? vdist(X, dim, cv[0], cv[4]) : 1.0;
+}
+
+// Local entry (kr, kc) of a cell: mu^{-1} A - omega^2 M (unsigned, local basis).
+// 2-D: A = ref0/(ab), M = (b/a) ref1 + (a/b) ref2.
+// 3-D: A = sum_k h_k^2/(abc) ref_k, M = sum_k abc/h_k^2 ref_{3+k}.
+__device__ __forceinline__ double cell_entry(int dim, const double* ref, int nb, double mu, double w2,
+                                             const double* h, int kr, int kc) {
+    const int o = kr * nb + kc;
+    if (dim == 2) {
+        const double a = h[0], b = h[1];
+        return mu * ref[o] / (a * b) - w2 * ((b / a) * ref[144 + o] + (a / b) * ref[288 + o]);
+    }
+    const double V = h[0] * h[1] * h[2];
+    double A = 0, M = 0;
+    for (int k = 0; k < 3; ++k) {
+        A += h[k] * h[k] / V * ref[k * 144 + o];
+        M += V / (h[k] * h[k]) * ref[(3 + k) * 144 + o];
+    }
+    return mu * A - w2 * M;
+}
+
+// Tangential mass of face f between its local DOFs a and b (unsigned).
+__device__ __forceinline__ double face_mass(int dim, const double* ref, const double* X, const int32_t* fv, int a,
+                                            int b) {
+    if (dim == 2) {
+        if (a != b) return 0.0;                   // Whitney and gradient traces are L2-orthogonal
+        return ref[6 * 144 + a] / vdist(X, 2, fv[0], fv[1]);
+    }
+    const double p = vdist(X, 3, fv[0], fv[1]), q = vdist(X, 3, fv[0], fv[2]);
+    return (q / p) * ref[6 * 144 + a * 4 + b] + (p / q) * ref[7 * 144 + a * 4 + b];
 }
 
 // Gather-by-row assembly of P_i in the SELL layout.  Entry (r, col) sums the
 // cells holding both DOFs in ascending cell order; entry (col, r) visits the
 // same cells in the same order with exactly symmetric reference entries, so
 // P_i is bit-symmetric.
-__global__ void k_assemble(int64_t n_loc, int nb, int maxc, const double* __restrict__ ref,
+__global__ void k_assemble(int dim, int64_t n_loc, int nb, int maxc, const double* __restrict__ ref,
                            const double* __restrict__ X, const int32_t* __restrict__ cells,
                            const int8_t* __restrict__ signs, const int32_t* __restrict__ cell_loc,
                            const double* __restrict__ mu, double w2,
@@ -128,10 +218,10 @@ __global__ void k_assemble(int64_t n_loc, int nb, int maxc, const double* __rest
                 int kr = row_k[r * maxc + u];
                 for (int kc = 0; kc < nb; ++kc) {
                     if (cell_loc[(int64_t)c * nb + kc] != cc) continue;
-                    double a, b;
-                    cell_sides(X, cells + (int64_t)c * 4, a, b);
+                    double hh[3];
+                    cell_sides(X, dim, cells, c, hh);
                     double s = (double)(signs[(int64_t)c * nb + kr] * signs[(int64_t)c * nb + kc]);
-                    v += s * cell_entry(ref, nb, mu[c], w2, a, b, kr, kc);
+                    v += s * cell_entry(dim, ref, nb, mu[c], w2, hh, kr, kc);
                 }
             }
         }
@@ -140,36 +230,70 @@ __global__ void k_assemble(int64_t n_loc, int nb, int maxc, const double* __rest
     }
 }
 
-// Tangential mass of a DOF on its own face edge: Whitney trace 1/l,
-// gradient trace (1-2s)/l gives 1/(3l); the two are L2-orthogonal.
-__device__ __forceinline__ double edge_trace_mass(const double* X, const int64_t* elo,
-                                                  const int64_t* ehi, int e, int fn) {
-    double dx = X[ehi[e] * 2] - X[elo[e] * 2], dy = X[ehi[e] * 2 + 1] - X[elo[e] * 2 + 1];
-    double l = sqrt(dx * dx + dy * dy);
-    return fn == 0 ? 1.0 / l : 1.0 / (3.0 * l);
-}
-
-__global__ void k_face_terms(int64_t n_loc, const double* __restrict__ X, const int64_t* __restrict__ elo,
-                             const int64_t* __restrict__ ehi, const int8_t* __restrict__ kind,
-                             const int8_t* __restrict__ fn, const int32_t* __restrict__ edge, double kw,
-                             double* bg64, double* bs64, float* bg32, float* bs32) {
+// Impedance / transmission face terms, gathered per local row from the faces
+// whose terms reach it (kind 1: Gamma^inf, kind 2: Sigma), times kappa*omega.
+// 2-D: the face mass is diagonal, stored per row (bg, bs).  3-D: the face mass
+// couples the four edges of a face; stored on the SELL pattern (bvg, bvs).
+__global__ void k_face_terms(int dim, int64_t n_loc, int fd, const double* __restrict__ ref,
+                             const double* __restrict__ X, const int32_t* __restrict__ face_v,
+                             const int8_t* __restrict__ face_sgn, const int8_t* __restrict__ face_kind,
+                             const int32_t* __restrict__ face_loc, const int32_t* __restrict__ row_face,
+                             const int8_t* __restrict__ row_face_a, const int8_t* __restrict__ row_face_side,
+                             const int64_t* __restrict__ slice_ptr, const int32_t* __restrict__ col,
+                             const uint8_t* __restrict__ pad, double kw, double* bg64, double* bs64, float* bg32,
+                             float* bs32, double* bvg64, double* bvs64, float* bvg32, float* bvs32) {
     int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (r >= n_loc) return;
-    double g = 0, s = 0;
-    if (kind[r] != 0) {
-        double mval = kw * edge_trace_mass(X, elo, ehi, edge[r], fn[r]);
-        if (kind[r] == 1) g = mval;
-        else s = mval;
+    constexpr int RF = thm_mesh::RF;
+    if (dim == 2) {
+        double g = 0, s = 0;
+        for (int u = 0; u < RF; ++u) {
+            const int32_t f = row_face[r * RF + u];
+            if (f < 0) continue;
+            const int a = row_face_a[r * RF + u];
+            const double v = kw * face_mass(2, ref, X, face_v + (int64_t)f * 4, a, a);
+            if (face_kind[f] == 1) g += v; else s += v;
+        }
+        bg64[r] = g; bs64[r] = s; bg32[r] = (float)g; bs32[r] = (float)s;
+        return;
     }
-    bg64[r] = g; bs64[r] = s; bg32[r] = (float)g; bs32[r] = (float)s;
+    bg64[r] = 0; bs64[r] = 0; bg32[r] = 0; bs32[r] = 0;
+    const int64_t sl = r / SELL_C;
+    const int lane = (int)(r % SELL_C);
+    const int64_t base = slice_ptr[sl];
+    const int w = (int)((slice_ptr[sl + 1] - base) / SELL_C);
+    for (int t = 0; t < w; ++t) {
+        const int64_t idx = base + (int64_t)t * SELL_C + lane;
+        double g = 0, s = 0;
+        if (!pad[idx]) {
+            const int32_t cc = col[idx];
+            for (int u = 0; u < RF; ++u) {
+                const int32_t f = row_face[r * RF + u];
+                if (f < 0) continue;
+                const int a = row_face_a[r * RF + u], side = row_face_side[r * RF + u];
+                for (int b = 0; b < fd; ++b) {
+                    if (face_loc[((int64_t)f * 2 + side) * fd + b] != cc) continue;
+                    const double v = kw * face_sgn[(int64_t)f * fd + a] * face_sgn[(int64_t)f * fd + b] *
+                                     face_mass(3, ref, X, face_v + (int64_t)f * 4, a, b);
+                    if (face_kind[f] == 1) g += v; else s += v;
+                }
+            }
+        }
+        bvg64[idx] = g; bvs64[idx] = s; bvg32[idx] = (float)g; bvs32[idx] = (float)s;
+    }
 }
 
-__global__ void k_iface_mass(int64_t n_if, const double* __restrict__ X, const int64_t* __restrict__ elo,
-                             const int64_t* __restrict__ ehi, const int32_t* __restrict__ edge,
-                             const int8_t* __restrict__ fn, double* __restrict__ mass) {
-    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (k >= n_if) return;
-    mass[k] = edge_trace_mass(X, elo, ehi, edge[k], fn[k]);
+// Values of the interface-entry terms: signed face mass between DOFs a and b.
+__global__ void k_iface_vals(int dim, int64_t n_terms, int fd, const double* __restrict__ ref,
+                             const double* __restrict__ X, const int32_t* __restrict__ face_v,
+                             const int8_t* __restrict__ face_sgn, const int32_t* __restrict__ tf,
+                             const int8_t* __restrict__ ta, const int8_t* __restrict__ tb, double* __restrict__ val) {
+    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= n_terms) return;
+    const int32_t f = tf[p];
+    const int a = ta[p], b = tb[p];
+    val[p] = face_sgn[(int64_t)f * fd + a] * face_sgn[(int64_t)f * fd + b] *
+             face_mass(dim, ref, X, face_v + (int64_t)f * 4, a, b);
 }
 
 // Dirichlet values: tangential moments of E^inc(x) = pol exp(-i omega dir.x)
@@ -220,12 +344,17 @@ __global__ void k_dirichlet(int64_t n_de, int dim, int order, const int64_t* __r
 
 // Lifting: f_i = -(P_i)_{F,D} u_D from the cells of each row (2-D: the face
 // terms never couple a free DOF to a Dirichlet one).
-__global__ void k_lifting(int64_t n_loc, int nb, int maxc, const double* __restrict__ ref,
+__global__ void k_lifting(int dim, int64_t n_loc, int nb, int maxc, const double* __restrict__ ref,
                           const double* __restrict__ X, const int32_t* __restrict__ cells,
                           const int8_t* __restrict__ signs, const int32_t* __restrict__ cell_loc,
                           const int32_t* __restrict__ cell_dofs, const double* __restrict__ mu, double w2,
                           const int32_t* __restrict__ row_cell, const int32_t* __restrict__ row_k,
-                          const double2* __restrict__ uD, double2* __restrict__ f) {
+                          const double2* __restrict__ uD, int fd, const int32_t* __restrict__ face_v,
+                          const int32_t* __restrict__ face_dof, const int8_t* __restrict__ face_sgn,
+                          const int32_t* __restrict__ face_loc, const int32_t* __restrict__ row_face,
+                          const int8_t* __restrict__ row_face_a, const int8_t* __restrict__ row_face_side,
+                          const int8_t* __restrict__ face_kind, double kw, double2* __restrict__ f,
+                          double2* __restrict__ fres) {
     int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (r >= n_loc) return;
     double fr = 0, fi = 0;
@@ -233,18 +362,40 @@ __global__ void k_lifting(int64_t n_loc, int nb, int maxc, const double* __restr
         int32_t c = row_cell[r * maxc + u];
         if (c < 0) break;
         int kr = row_k[r * maxc + u];
-        double a, b;
-        cell_sides(X, cells + (int64_t)c * 4, a, b);
+        double hh[3];
+        cell_sides(X, dim, cells, c, hh);
         for (int kc = 0; kc < nb; ++kc) {
             if (cell_loc[(int64_t)c * nb + kc] >= 0) continue;
             double s = (double)(signs[(int64_t)c * nb + kr] * signs[(int64_t)c * nb + kc]);
-            double v = s * cell_entry(ref, nb, mu[c], w2, a, b, kr, kc);
+            double v = s * cell_entry(dim, ref, nb, mu[c], w2, hh, kr, kc);
             double2 d = uD[cell_dofs[(int64_t)c * nb + kc]];
             fr -= v * d.x;
             fi -= v * d.y;
         }
     }
+    // face terms coupling the row to Dirichlet DOFs: -(i kappa omega M_f) u_D.
+    // The global system holds only the Gamma^inf faces; the subdomain operator
+    // T_i also the transmission faces of Sigma (3-D only: in 2-D no Dirichlet
+    // DOF lies on an interface edge).
+    double gr = fr, gi = fi;
+    constexpr int RF = thm_mesh::RF;
+    for (int u = 0; u < RF; ++u) {
+        const int32_t f = row_face[r * RF + u];
+        if (f < 0) continue;
+        const int a = row_face_a[r * RF + u], side = row_face_side[r * RF + u];
+        for (int b = 0; b < fd; ++b) {
+            if (face_loc[((int64_t)f * 2 + side) * fd + b] >= 0) continue;
+            const int32_t gd = face_dof[(int64_t)f * fd + b];
+            const double v = kw * face_sgn[(int64_t)f * fd + a] * face_sgn[(int64_t)f * fd + b] *
+                             face_mass(dim, ref, X, face_v + (int64_t)f * 4, a, b);
+            const double2 d = uD[gd];
+            fr += v * d.y;            // -(i v)(d.x + i d.y) = v d.y - i v d.x
+            fi -= v * d.x;
+            if (face_kind[f] == 1) { gr += v * d.y; gi -= v * d.x; }
+        }
+    }
     f[r] = make_double2(fr, fi);
+    fres[r] = make_double2(gr, gi);
 }
 
 // ---------------------------------------------------------------------------
@@ -259,12 +410,12 @@ __global__ void k_condense(int64_t n_cell, const double* __restrict__ ref, const
                            float* __restrict__ cg32, int* __restrict__ bad) {
     int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (c >= n_cell) return;
-    double a, b;
-    cell_sides(X, cells + c * 4, a, b);
+    double hh[3];
+    cell_sides(X, 2, cells, c, hh);
     double D[4][8];                              // [D | I] -> [I | D^{-1}]
     for (int i = 0; i < 4; ++i)
         for (int j = 0; j < 4; ++j) {
-            D[i][j] = cell_entry(ref, 12, mu[c], w2, a, b, 8 + i, 8 + j);
+            D[i][j] = cell_entry(2, ref, 12, mu[c], w2, hh, 8 + i, 8 + j);
             D[i][4 + j] = i == j ? 1.0 : 0.0;
         }
     for (int k = 0; k < 4; ++k) {
@@ -291,7 +442,7 @@ __global__ void k_condense(int64_t n_cell, const double* __restrict__ ref, const
     double PEI[8][4];
     for (int e = 0; e < 8; ++e)
         for (int k = 0; k < 4; ++k)
-            PEI[e][k] = (double)signs[c * 12 + e] * cell_entry(ref, 12, mu[c], w2, a, b, e, 8 + k);
+            PEI[e][k] = (double)signs[c * 12 + e] * cell_entry(2, ref, 12, mu[c], w2, hh, e, 8 + k);
     double G[8][4];
     for (int e = 0; e < 8; ++e)
         for (int k = 0; k < 4; ++k) {
@@ -576,30 +727,38 @@ void assemble(thm_sys* s) {
     const int nb = m->dpc;
     const double w2 = s->omega * s->omega;
     const double kw = s->kappa * s->omega;
-    s->ref.alloc(3 * 144);
+    s->dev_err.alloc(1);
+    s->dev_err.zero(st);
+    s->ref.alloc(8 * 144);
     s->ref.zero(st);
-    THM_LAUNCH(THM_K_SETUP, st, k_ref_matrices<<<1, 256, 0, st>>>(m->order, nb, s->ref.p));
+    THM_LAUNCH(THM_K_SETUP, st, k_ref_matrices<<<1, 256, 0, st>>>(m->dim, m->order, nb, s->ref.p));
     THM_CUDA(cudaGetLastError());
     s->val64.alloc(m->n_slots);
     s->val32.alloc(m->n_slots);
     const int th = 256;
     auto grid = [&](int64_t n) { return (unsigned)((n + th - 1) / th); };
-    THM_LAUNCH(THM_K_SETUP, st, k_assemble<<<grid(m->n_loc), th, 0, st>>>(m->n_loc, nb, m->maxc, s->ref.p, m->d_coords.p, m->d_cells.p,
+    THM_LAUNCH(THM_K_SETUP, st, k_assemble<<<grid(m->n_loc), th, 0, st>>>(m->dim, m->n_loc, nb, m->maxc, s->ref.p, m->d_coords.p, m->d_cells.p,
                                               m->d_cell_signs.p, m->d_cell_loc.p, s->mu_inv.p, w2,
                                               m->d_slice_ptr.p, m->d_sell_col.p, m->d_sell_pad.p,
                                               m->d_row_cell.p, m->d_row_k.p, s->val64.p, s->val32.p));
     THM_CUDA(cudaGetLastError());
     s->bg64.alloc(m->n_loc); s->bs64.alloc(m->n_loc);
     s->bg32.alloc(m->n_loc); s->bs32.alloc(m->n_loc);
-    THM_LAUNCH(THM_K_SETUP, st, k_face_terms<<<grid(m->n_loc), th, 0, st>>>(m->n_loc, m->d_coords.p, m->d_edge_lo.p, m->d_edge_hi.p,
-                                                m->d_row_face_kind.p, m->d_row_face_fn.p,
-                                                m->d_row_face_edge.p, kw, s->bg64.p, s->bs64.p,
-                                                s->bg32.p, s->bs32.p));
+    const bool sellb = m->dim == 3;
+    s->bvg64.alloc(sellb ? m->n_slots : 1); s->bvs64.alloc(sellb ? m->n_slots : 1);
+    s->bvg32.alloc(sellb ? m->n_slots : 1); s->bvs32.alloc(sellb ? m->n_slots : 1);
+    THM_LAUNCH(THM_K_SETUP, st, k_face_terms<<<grid(m->n_loc), th, 0, st>>>(
+        m->dim, m->n_loc, m->fd, s->ref.p, m->d_coords.p, m->d_face_v.p, m->d_face_sgn.p, m->d_face_kind.p,
+        m->d_face_loc.p, m->d_row_face.p, m->d_row_face_a.p, m->d_row_face_side.p, m->d_slice_ptr.p,
+        m->d_sell_col.p, m->d_sell_pad.p, kw, s->bg64.p, s->bs64.p, s->bg32.p, s->bs32.p, s->bvg64.p, s->bvs64.p,
+        s->bvg32.p, s->bvs32.p));
     THM_CUDA(cudaGetLastError());
-    s->if_mass.alloc(m->n_if > 0 ? m->n_if : 1);
-    if (m->n_if > 0) {
-        THM_LAUNCH(THM_K_SETUP, st, k_iface_mass<<<grid(m->n_if), th, 0, st>>>(m->n_if, m->d_coords.p, m->d_edge_lo.p, m->d_edge_hi.p,
-                                                   m->d_if_edge.p, m->d_if_fn.p, s->if_mass.p));
+    const int64_t nterm = (int64_t)m->if_tf.size();
+    s->if_val.alloc(nterm > 0 ? nterm : 1);
+    if (nterm > 0) {
+        THM_LAUNCH(THM_K_SETUP, st, k_iface_vals<<<grid(nterm), th, 0, st>>>(m->dim, nterm, m->fd, s->ref.p, m->d_coords.p,
+                                                                            m->d_face_v.p, m->d_face_sgn.p, m->d_if_tf.p,
+                                                                            m->d_if_ta.p, m->d_if_tb.p, s->if_val.p));
         THM_CUDA(cudaGetLastError());
     }
     s->uD.alloc(m->n_dof);
@@ -654,10 +813,12 @@ void assemble(thm_sys* s) {
         THM_CUDA(cudaGetLastError());
     }
     s->f_loc.alloc(m->n_loc);
-    THM_LAUNCH(THM_K_SETUP, st, k_lifting<<<grid(m->n_loc), th, 0, st>>>(m->n_loc, nb, m->maxc, s->ref.p, m->d_coords.p, m->d_cells.p,
-                                             m->d_cell_signs.p, m->d_cell_loc.p, m->d_cell_dofs.p,
-                                             s->mu_inv.p, w2, m->d_row_cell.p, m->d_row_k.p, s->uD.p,
-                                             s->f_loc.p));
+    s->f_res.alloc(m->n_loc);
+    THM_LAUNCH(THM_K_SETUP, st, k_lifting<<<grid(m->n_loc), th, 0, st>>>(
+        m->dim, m->n_loc, nb, m->maxc, s->ref.p, m->d_coords.p, m->d_cells.p, m->d_cell_signs.p, m->d_cell_loc.p,
+        m->d_cell_dofs.p, s->mu_inv.p, w2, m->d_row_cell.p, m->d_row_k.p, s->uD.p, m->fd, m->d_face_v.p,
+        m->d_face_dof.p, m->d_face_sgn.p, m->d_face_loc.p, m->d_row_face.p, m->d_row_face_a.p, m->d_row_face_side.p,
+        m->d_face_kind.p, kw, s->f_loc.p, s->f_res.p));
     THM_CUDA(cudaGetLastError());
     THM_CUDA(cudaStreamSynchronize(st));
 }

@@ -145,10 +145,19 @@ struct thm_mesh {
     // assembly plan: cells holding each local row (ascending), <= maxc
     int maxc = 0;
     std::vector<int32_t> row_cell, row_k;           // [n_loc][maxc]
-    // face terms (2-D: one edge per row at most)
-    std::vector<int8_t> row_face_kind;              // 0 none, 1 Gamma^inf, 2 Sigma
-    std::vector<int8_t> row_face_fn;                // 0 Whitney trace, 1 gradient trace
-    std::vector<int32_t> row_face_edge;
+    // faces with impedance (kind 1, Gamma^inf) or transmission (kind 2, Sigma)
+    // terms; fd DOFs per face (2-D order 1: 1, order 2: 2, 3-D: 4)
+    static constexpr int RF = 4;                     // faces per local row, at most
+    int fd = 0;
+    int64_t n_face = 0;
+    std::vector<int32_t> face_v;                    // [n_face][4] vertices, face-local tensor order
+    std::vector<int32_t> face_dof;                  // [n_face][fd]
+    std::vector<int8_t> face_sgn;                   // [n_face][fd]
+    std::vector<int8_t> face_kind;                  // [n_face]
+    std::vector<int32_t> face_sub;                  // [n_face][2] subdomains (-1: none)
+    std::vector<int32_t> face_loc;                  // [n_face][2][fd] local rows per side (-1: Dirichlet)
+    std::vector<int32_t> row_face;                  // [n_loc][RF] face ids (-1: none)
+    std::vector<int8_t> row_face_a, row_face_side;  // [n_loc][RF]
     // levels of the block-tridiagonal factorisation
     std::vector<thm::Level> levels;
     int max_m = 0;
@@ -163,9 +172,12 @@ struct thm_mesh {
     std::vector<thm::Chunk> chunks;
     // interface entries (directed pairs i <- j, one per free DOF on Sigma_ij)
     int64_t n_if = 0;
-    std::vector<int32_t> if_recv, if_send, if_rowi, if_rowj, if_partner, if_edge;
-    std::vector<int8_t> if_fn;
+    std::vector<int32_t> if_recv, if_send, if_rowi, if_partner;
     std::vector<int64_t> if_gdof;
+    // terms of (M_Sigma_ij u_j)[g] per entry: face, a, b, sender column (-(gdof+1): Dirichlet)
+    std::vector<int64_t> if_ptr;
+    std::vector<int32_t> if_tf, if_tcol;
+    std::vector<int8_t> if_ta, if_tb;
     std::vector<int64_t> rowg_ptr;                  // [n_loc+1] local row -> entries received
     std::vector<int32_t> rowg_idx;
     // global <-> local
@@ -180,10 +192,11 @@ struct thm_mesh {
     thm::DArr<int32_t> d_cells, d_cell_dofs, d_cell_loc, d_sell_col, d_row_cell, d_row_k;
     thm::DArr<int64_t> d_edge_lo, d_edge_hi, d_slice_ptr, d_dir_edges, d_loc_gdof, d_rowg_ptr,
         d_copy_ptr;
-    thm::DArr<int8_t> d_cell_signs, d_row_face_kind, d_row_face_fn, d_if_fn;
+    thm::DArr<int8_t> d_cell_signs, d_face_sgn, d_face_kind, d_row_face_a, d_row_face_side, d_if_ta, d_if_tb;
     thm::DArr<uint8_t> d_sell_pad, d_loc_is_owner, d_loc_is_bub;
-    thm::DArr<int32_t> d_row_face_edge, d_if_rowi, d_if_rowj, d_if_partner, d_if_edge, d_rowg_idx,
-        d_owner_loc, d_copy_idx, d_loc_sub;
+    thm::DArr<int32_t> d_if_rowi, d_if_partner, d_rowg_idx, d_owner_loc, d_copy_idx, d_loc_sub, d_face_v,
+        d_face_dof, d_face_loc, d_row_face, d_if_tf, d_if_tcol;
+    thm::DArr<int64_t> d_if_ptr;
     thm::DArr<thm::Level> d_levels;
     thm::DArr<int32_t> d_cpl_ptr, d_cpl_col;
     thm::DArr<int64_t> d_cpl_slot;
@@ -206,9 +219,12 @@ struct thm_sys {
     thm::DArr<float> val32;            // same, FP32
     thm::DArr<double> bg64, bs64;      // kappa*omega * diagonal face masses: Gamma^inf, Sigma
     thm::DArr<float> bg32, bs32;
-    thm::DArr<double> if_mass;         // [n_if] tangential mass of each interface entry
+    thm::DArr<double> if_val;          // values of the interface-entry terms (face masses)
+    thm::DArr<double> bvg64, bvs64;    // 3-D: kappa*omega face masses on the SELL pattern (Gamma^inf, Sigma)
+    thm::DArr<float> bvg32, bvs32;
     thm::DArr<double2> uD;             // [n_dof] Dirichlet values
-    thm::DArr<double2> f_loc;          // [n_loc] lifting right-hand side
+    thm::DArr<double2> f_loc;          // [n_loc] subdomain sources: -(T_i)_{F,D} u_D (Eq. 5)
+    thm::DArr<double2> f_res;          // [n_loc] split of the global right-hand side: -(K_i^loc)_{F,D} u_D
     // block-tridiagonal factors of P_i (lazily built per precision)
     bool fac64_ok = false, fac32_ok = false;
     thm::DArr<double> fac64;

@@ -20,10 +20,13 @@ __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_doub
 // y = T_i x  (op 0: P + i(B_Gamma + B_Sigma))  or  K_i^loc x (op 2: P + i B_Gamma)
 // SELL-32: one thread per row, slots column-major inside a slice (coalesced).
 // ---------------------------------------------------------------------------
+// 3-D: the face terms are not diagonal; their values (times kappa*omega) ride
+// on the same SELL pattern (bvg: Gamma^inf, bvs: Sigma), non-null only then.
 template <class V, class F>
 __global__ void __launch_bounds__(256) k_spmv(int64_t n, const int64_t* __restrict__ slice_ptr,
                                               const int32_t* __restrict__ col, const F* __restrict__ val,
                                               const F* __restrict__ bg, const F* __restrict__ bs, int use_bs,
+                                              const F* __restrict__ bvg, const F* __restrict__ bvs,
                                               const V* __restrict__ x, V* __restrict__ y) {
     using R = typename VT<V>::R;
     int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -35,13 +38,27 @@ __global__ void __launch_bounds__(256) k_spmv(int64_t n, const int64_t* __restri
     R ar = 0, ai = 0;
     const int32_t* cp = col + base + lane;
     const F* vp = val + base + lane;
+    if (bvg) {
+        const F* gp = bvg + base + lane;
+        const F* sp = bvs + base + lane;
+        for (int t = 0; t < w; ++t) {
+            int32_t c = __ldg(cp + (t << 5));
+            R v = (R)__ldg(vp + (t << 5));
+            R b = (R)__ldg(gp + (t << 5));
+            if (use_bs) b += (R)__ldg(sp + (t << 5));
+            V xv = x[c];
+            ar += v * xv.x - b * xv.y;
+            ai += v * xv.y + b * xv.x;
+        }
+    } else {
 #pragma unroll 4
-    for (int t = 0; t < w; ++t) {
-        int32_t c = __ldg(cp + (t << 5));
-        R v = (R)__ldg(vp + (t << 5));
-        V xv = x[c];
-        ar += v * xv.x;
-        ai += v * xv.y;
+        for (int t = 0; t < w; ++t) {
+            int32_t c = __ldg(cp + (t << 5));
+            R v = (R)__ldg(vp + (t << 5));
+            V xv = x[c];
+            ar += v * xv.x;
+            ai += v * xv.y;
+        }
     }
     R b = (R)bg[r];
     if (use_bs) b += (R)bs[r];
@@ -73,6 +90,43 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// ---- TMA 1-D bulk copies completing on an mbarrier (sm_90+ PTX) ----------
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+// bytes must be a multiple of 16, both addresses 16-byte aligned
+__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+// Bounded wait for the given phase parity; false after the iteration limit
+// (each try_wait itself suspends for a bounded, hardware-defined time).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+    for (int it = 0; it < (1 << 22); ++it) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
 
 // Copy n 4-byte words (16-byte aligned source, readable up to the next 16
 // bytes) into shared memory with cp.async, cooperatively.
@@ -115,6 +169,9 @@ __device__ __forceinline__ void tile_next(TileCursor& c, int nlev, const int* ms
     if (c.l < 0) c.dir = 2;
 }
 
+constexpr int BT_NG = 4;        // column groups of the block GEMV
+constexpr int BT_MAXO = 8;      // outputs per thread: level blocks up to 8 * 512 / BT_NG = 1024 rows
+
 // x = P_i^{-1} y for every subdomain (Eq. 7: the same real P_i^{-1} on the
 // real and on the imaginary part).  Grid (n_sub, 2): blockIdx.y picks the
 // component, so the two independent real solves of a subdomain run on two
@@ -133,14 +190,17 @@ __global__ void __launch_bounds__(512) k_bt_apply(const Sub* __restrict__ subs, 
                                                   const F* __restrict__ av, const int32_t* __restrict__ ci,
                                                   const F* __restrict__ cv, const int32_t* __restrict__ ei,
                                                   const F* __restrict__ ev, int R, int nslot, int slot_bytes,
-                                                  int max_ne, int max_m, int max_lev,
+                                                  int max_ne, int max_m, int max_lev, int* __restrict__ err,
                                                   const V* __restrict__ xin, V* __restrict__ yout) {
     using R_t = typename VT<V>::R;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    unsigned char* slots = smem_raw;
-    R_t* vec = reinterpret_cast<R_t*>(smem_raw + (size_t)nslot * slot_bytes);
+    __shared__ int s_abort;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);                    // [nslot]
+    unsigned char* slots = smem_raw + ((nslot * 8 + 15) / 16) * 16;
+    R_t* vec = reinterpret_cast<R_t*>(slots + (size_t)nslot * slot_bytes);
     R_t* su = vec + ((max_ne + 3) / 4) * 4;
-    int* msz = reinterpret_cast<int*>(su + ((max_m + 3) / 4) * 4);   // [max_lev] level sizes
+    R_t* part = su + ((max_m + 3) / 4) * 4;                            // [BT_NG][max_m] partial sums
+    int* msz = reinterpret_cast<int*>(part + BT_NG * (((max_m + 3) / 4) * 4));   // [max_lev] level sizes
     int* mst = msz + max_lev;                                          // level starts (relative)
     int* enz = mst + max_lev;                                          // coupling entries E, F
     int* fnz = enz + max_lev;
@@ -153,7 +213,14 @@ __global__ void __launch_bounds__(512) k_bt_apply(const Sub* __restrict__ subs, 
     const int comp = blockIdx.y;
     const R_t* x = reinterpret_cast<const R_t*>(xin) + comp;     // stride 2
     R_t* y = reinterpret_cast<R_t*>(yout) + comp;
-    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5, lane = threadIdx.x & 31;
+    // thread groups of the block GEMV, sized to the widest level: tpg threads
+    // (a multiple of 32, >= max_m when it fits) own outputs i0, i0+tpg, ...;
+    // ng groups split the rows of each tile
+    const int tpg = min((int)blockDim.x, ((max_m + 31) / 32) * 32);
+    const int ng = min(BT_NG, (int)blockDim.x / tpg);
+    const int g = threadIdx.x / tpg, i0 = threadIdx.x % tpg;
+    const bool in_group = g < ng;
+    R_t acc[BT_MAXO];
     for (int l = threadIdx.x; l < S.nlev; l += blockDim.x) {
         const Level L = levels[S.lev0 + l];
         msz[l] = L.size;
@@ -161,34 +228,45 @@ __global__ void __launch_bounds__(512) k_bt_apply(const Sub* __restrict__ subs, 
         enz[l] = L.enz; fnz[l] = L.fnz;
         offw[l] = L.offW; eptr[l] = L.eptr; eoff[l] = L.eoff; fptr[l] = L.fptr; foff[l] = L.foff;
     }
+    if (threadIdx.x == 0) {
+        s_abort = 0;
+        for (int q = 0; q < nslot; ++q) mbar_init(&bars[q], 1);
+        mbar_fence_init();
+    }
     __syncthreads();
 
+    // producer (thread 0): one TMA bulk copy per W tile, three per coupling tile
     auto issue = [&](const TileCursor& c, int t) {
-        if (c.dir < 2) {
-            unsigned char* dst = slots + (size_t)(t % nslot) * slot_bytes;
-            const int m = msz[c.l];
-            if (c.r0 < 0) {
-                const bool fwd = c.dir == 0;
-                const int64_t po = fwd ? eptr[c.l] : fptr[c.l], qo = fwd ? eoff[c.l] : foff[c.l];
-                const int nz = fwd ? enz[c.l] : fnz[c.l];
-                const int pw = ((m + 1 + 3) / 4) * 4, cw = ((nz + 3) / 4) * 4;
-                stage_words(dst, cptr + po, m + 1);
-                stage_words(dst + 4 * (size_t)pw, ccol + qo, nz);
-                stage_words(dst + 4 * (size_t)pw + 4 * (size_t)cw, cval + qo, (int64_t)nz * (int64_t)(sizeof(F) / 4));
-            } else {
-                const int nr = min(tile_rows(m, R), m - c.r0);
-                stage_words(dst, fac + offw[c.l] + (int64_t)c.r0 * m, (int64_t)nr * m * (int64_t)(sizeof(F) / 4));
-            }
+        if (threadIdx.x != 0 || c.dir == 2) return;
+        const int q = t % nslot;
+        unsigned char* dst = slots + (size_t)q * slot_bytes;
+        const int m = msz[c.l];
+        fence_proxy_async();
+        if (c.r0 < 0) {
+            const bool fwd = c.dir == 0;
+            const int64_t po = fwd ? eptr[c.l] : fptr[c.l], qo = fwd ? eoff[c.l] : foff[c.l];
+            const int nz = fwd ? enz[c.l] : fnz[c.l];
+            const unsigned pb = (unsigned)(((m + 1) * 4 + 15) / 16 * 16);
+            const unsigned cb = (unsigned)((nz * 4 + 15) / 16 * 16);
+            const unsigned vb = (unsigned)((nz * (int)sizeof(F) + 15) / 16 * 16);
+            mbar_expect_tx(&bars[q], pb + cb + vb);
+            tma_load_1d(dst, cptr + po, pb, &bars[q]);
+            if (cb) tma_load_1d(dst + pb, ccol + qo, cb, &bars[q]);
+            if (vb) tma_load_1d(dst + pb + cb, cval + qo, vb, &bars[q]);
+        } else {
+            const int nr = min(tile_rows(m, R), m - c.r0);
+            const unsigned wb = (unsigned)(((int64_t)nr * m * (int64_t)sizeof(F) + 15) / 16 * 16);
+            mbar_expect_tx(&bars[q], wb);
+            tma_load_1d(dst, fac + offw[c.l] + (int64_t)c.r0 * m, wb, &bars[q]);
         }
-        cp_async_commit();
     };
 
-    // prologue: nslot-2 tiles in flight
+    // prologue: fill the ring
     TileCursor prod{S.nlev > 0 ? 0 : 2, 0, -1};
     int tp = 0;
-    for (int q = 0; q < nslot - 2; ++q) {
+    for (int q = 0; q < nslot && prod.dir < 2; ++q) {
         issue(prod, tp++);
-        if (prod.dir < 2) tile_next(prod, S.nlev, msz, R);
+        tile_next(prod, S.nlev, msz, R);
     }
     // (a)
     for (int64_t e = threadIdx.x; e < S.ne; e += blockDim.x) {
@@ -200,16 +278,15 @@ __global__ void __launch_bounds__(512) k_bt_apply(const Sub* __restrict__ subs, 
         }
         vec[e] = acc;
     }
+    __syncthreads();
     // (b)
     TileCursor cur{S.nlev > 0 ? 0 : 2, 0, -1};
-    for (int t = 0; cur.dir < 2; ++t) {
-        issue(prod, tp++);
-        if (prod.dir < 2) tile_next(prod, S.nlev, msz, R);
-        if (nslot == 3) cp_async_wait<1>();
-        else if (nslot == 4) cp_async_wait<2>();
-        else if (nslot == 5) cp_async_wait<3>();
-        else cp_async_wait<4>();
-        __syncthreads();
+    int t = 0;
+    for (; cur.dir < 2; ++t) {
+        if (!mbar_wait(&bars[t % nslot], (unsigned)((t / nslot) & 1))) {
+            atomicExch(err, 1);
+            s_abort = 1;
+        }
         const unsigned char* buf = slots + (size_t)(t % nslot) * slot_bytes;
         const int m = msz[cur.l];
         const int o = mst[cur.l];
@@ -235,20 +312,61 @@ __global__ void __launch_bounds__(512) k_bt_apply(const Sub* __restrict__ subs, 
                 }
             }
         } else {
-            const F* W = reinterpret_cast<const F*>(buf);
-            const int nr = min(tile_rows(m, R), m - cur.r0);
-            for (int i = warp; i < nr; i += nw) {
-                R_t v = warp_dot<F, R_t>(W + (int64_t)i * m, su, m);
-                if (lane == 0) {
-                    if (cur.dir == 0) vec[o + cur.r0 + i] = v;
-                    else vec[o + cur.r0 + i] -= v;
+            // rows j0..j0+nr of W_l; W_l = S_l^{-1} is symmetric, so these rows
+            // are also columns: y_i += sum_{j in tile} W[j][i] s_j.  Thread
+            // (group g, lane-in-group i0) owns outputs i0, i0+TPG, ... and the
+            // tile rows j0+g, j0+g+BT_NG, ...; consecutive threads read
+            // consecutive words of a row (no bank conflicts), s_j is a broadcast.
+            const F* Wt = reinterpret_cast<const F*>(buf);
+            const int j0 = cur.r0;
+            const int nr = min(tile_rows(m, R), m - j0);
+            const int nout = (m - i0 + tpg - 1) / tpg;     // outputs of this thread (i0 < m)
+            if (j0 == 0)
+#pragma unroll
+                for (int k = 0; k < BT_MAXO; ++k) acc[k] = 0;
+            if (in_group && i0 < m) {
+                if (nout == 1) {
+                    R_t a0 = acc[0];
+                    for (int jj = g; jj < nr; jj += ng) a0 += (R_t)Wt[(int64_t)jj * m + i0] * su[j0 + jj];
+                    acc[0] = a0;
+                } else {
+                    for (int jj = g; jj < nr; jj += ng) {
+                        const R_t sj = su[j0 + jj];
+                        const F* wr = Wt + (int64_t)jj * m + i0;
+#pragma unroll
+                        for (int k = 0; k < BT_MAXO; ++k)
+                            if (k < nout) acc[k] += (R_t)wr[k * tpg] * sj;
+                    }
+                }
+            }
+            if (j0 + nr >= m) {                // last tile of the level: combine the groups
+                if (in_group)
+#pragma unroll
+                    for (int k = 0; k < BT_MAXO; ++k) {
+                        const int i = i0 + k * tpg;
+                        if (i < m) part[g * ((max_m + 3) / 4 * 4) + i] = acc[k];
+                    }
+                __syncthreads();
+                for (int i = threadIdx.x; i < m; i += blockDim.x) {
+                    R_t v = 0;
+                    for (int q = 0; q < ng; ++q) v += part[q * ((max_m + 3) / 4 * 4) + i];
+                    if (cur.dir == 0) vec[o + i] = v;
+                    else vec[o + i] -= v;
                 }
             }
         }
+        __syncthreads();                       // slot t%nslot free, vec/su writes visible
+        if (s_abort) break;
+        issue(prod, tp);                       // refill the freed slot
+        if (prod.dir < 2) { ++tp; tile_next(prod, S.nlev, msz, R); }
         tile_next(cur, S.nlev, msz, R);
     }
-    cp_async_wait<0>();
-    __syncthreads();
+    if (s_abort) {
+        // a copy did not arrive: wait (bounded) for the ones in flight, then leave
+        if (threadIdx.x == 0)
+            for (int q = t + 1; q < tp; ++q) mbar_wait(&bars[q % nslot], (unsigned)((q / nslot) & 1));
+        return;
+    }
     // (c) and write-back
     for (int64_t e = threadIdx.x; e < S.ne; e += blockDim.x) y[2 * (S.off + e)] = vec[e];
     if (condensed)
@@ -259,8 +377,8 @@ __global__ void __launch_bounds__(512) k_bt_apply(const Sub* __restrict__ subs, 
 #pragma unroll
             for (int a = 0; a < 8; ++a) {
                 int64_t e = (int64_t)ei[a * n_loc + b] - S.off;
-                R_t t = (e >= 0 && e < S.ne) ? vec[e] : (R_t)0;
-                acc += (R_t)ev[a * n_loc + b] * t;
+                R_t tt = (e >= 0 && e < S.ne) ? vec[e] : (R_t)0;
+                acc += (R_t)ev[a * n_loc + b] * tt;
             }
             y[2 * b] = acc;
         }

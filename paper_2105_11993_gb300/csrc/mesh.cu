@@ -1,6 +1,8 @@
 // Mesh numbering, orientation signs and the subdomain structure (Section 2:
 // the space N_h^p; Section 3.1: the partition into Omega_i and Sigma_ij).
 #include <algorithm>
+#include <array>
+#include <tuple>
 #include <cmath>
 #include <numeric>
 #include <queue>
@@ -498,62 +500,172 @@ void build_mesh(thm_mesh* m) {
             THM_REQUIRE(m->is_dir[g], "internal: free DOF without a subdomain copy");
         }
 
-    // ---- faces (2-D): impedance and interface edges, interface entries
-    m->row_face_kind.assign(m->n_loc, 0);
-    m->row_face_fn.assign(m->n_loc, 0);
-    m->row_face_edge.assign(m->n_loc, -1);
-    THM_REQUIRE(d == 2, "3-D meshes are not supported by this build of the library");
-    struct IfE { int32_t i, j; int64_t g; int32_t edge; int8_t fn; };
-    std::vector<IfE> ifs;
-    for (int64_t r = 0; r < m->n_loc; ++r) {
-        int64_t g = m->loc_gdof[r];
-        if (m->order == 2 && g >= 2 * m->n_edge) continue;       // bubble
-        int64_t e = m->order == 1 ? g : g / 2;
-        int8_t fn = (m->order == 2 && (g & 1)) ? 1 : 0;
-        int32_t c0 = ecell[2 * e], c1 = ecell[2 * e + 1];
-        int s = m->loc_sub[r];
-        if (c1 < 0) {
-            if (edge_kind[e] == 1) {
-                m->row_face_kind[r] = 1; m->row_face_fn[r] = fn; m->row_face_edge[r] = (int32_t)e;
+    // ---- faces with impedance (Gamma^inf, kind 1) or transmission (Sigma, kind 2)
+    //      terms: 2-D faces are edges (1 or 2 DOFs), 3-D faces are quads (4
+    //      edge DOFs); the tangential face mass couples the face's DOFs
+    constexpr int RF = thm_mesh::RF;
+    m->fd = d == 2 ? (m->order == 1 ? 1 : 2) : 4;
+    const int fd = m->fd;
+    m->face_v.clear(); m->face_dof.clear(); m->face_sgn.clear(); m->face_kind.clear(); m->face_sub.clear();
+    auto add_face = [&](const int64_t* fv, int kind, int s0, int s1) {
+        int32_t v[4] = {(int32_t)fv[0], (int32_t)fv[1], d == 3 ? (int32_t)fv[2] : 0, d == 3 ? (int32_t)fv[3] : 0};
+        for (int k = 0; k < 4; ++k) m->face_v.push_back(v[k]);
+        if (d == 2) {
+            int64_t e = host_find_edge(m, fv[0], fv[1]);
+            int8_t sg = fv[0] < fv[1] ? 1 : -1;
+            if (m->order == 1) { m->face_dof.push_back((int32_t)e); m->face_sgn.push_back(sg); }
+            else {
+                m->face_dof.push_back((int32_t)(2 * e)); m->face_sgn.push_back(sg);
+                m->face_dof.push_back((int32_t)(2 * e + 1)); m->face_sgn.push_back(1);
             }
-        } else if (m->cell_sub[c0] != m->cell_sub[c1]) {
-            int other = m->cell_sub[c0] == s ? m->cell_sub[c1] : m->cell_sub[c0];
-            m->row_face_kind[r] = 2; m->row_face_fn[r] = fn; m->row_face_edge[r] = (int32_t)e;
-            ifs.push_back({s, other, g, (int32_t)e, fn});
+        } else {
+            for (int k = 0; k < 4; ++k) {
+                int64_t a = fv[h_edges2[k][0]], b = fv[h_edges2[k][1]];
+                m->face_dof.push_back((int32_t)host_find_edge(m, a, b));
+                m->face_sgn.push_back(a < b ? 1 : -1);
+            }
+        }
+        m->face_kind.push_back((int8_t)kind);
+        m->face_sub.push_back(s0);
+        m->face_sub.push_back(s1);
+    };
+    if (d == 2) {
+        for (int64_t e = 0; e < m->n_edge; ++e) {
+            int32_t c0 = ecell[2 * e], c1 = ecell[2 * e + 1];
+            int64_t fv[2] = {m->edge_lo[e], m->edge_hi[e]};
+            if (c1 < 0 && edge_kind[e] == 1) add_face(fv, 1, m->cell_sub[c0], -1);
+            else if (c1 >= 0 && m->cell_sub[c0] != m->cell_sub[c1]) add_face(fv, 2, m->cell_sub[c0], m->cell_sub[c1]);
+        }
+    } else {
+        // all hex faces keyed by their sorted vertices
+        struct FK { int64_t k[4]; int32_t cell; int8_t lf; };
+        std::vector<FK> fk;
+        fk.reserve(m->n_cell * 6);
+        static const int lfaces[6][4] = {{0, 2, 4, 6}, {1, 3, 5, 7}, {0, 1, 4, 5}, {2, 3, 6, 7}, {0, 1, 2, 3}, {4, 5, 6, 7}};
+        for (int64_t c = 0; c < m->n_cell; ++c)
+            for (int f = 0; f < 6; ++f) {
+                FK x;
+                for (int k = 0; k < 4; ++k) x.k[k] = m->cells[c * 8 + lfaces[f][k]];
+                std::sort(x.k, x.k + 4);
+                x.cell = (int32_t)c; x.lf = (int8_t)f;
+                fk.push_back(x);
+            }
+        auto less = [](const FK& a, const FK& b) {
+            for (int k = 0; k < 4; ++k)
+                if (a.k[k] != b.k[k]) return a.k[k] < b.k[k];
+            return a.cell < b.cell;
+        };
+        std::sort(fk.begin(), fk.end(), less);
+        auto same = [](const FK& a, const FK& b) { return std::equal(a.k, a.k + 4, b.k); };
+        // impedance boundary faces: sorted keys of tag-0 bfaces
+        std::vector<std::array<int64_t, 4>> imp;
+        for (int64_t f = 0; f < m->n_bface; ++f)
+            if (m->btag[f] == THM_TAG_IMPEDANCE) {
+                std::array<int64_t, 4> k{m->bfaces[f * 4], m->bfaces[f * 4 + 1], m->bfaces[f * 4 + 2], m->bfaces[f * 4 + 3]};
+                std::sort(k.begin(), k.end());
+                imp.push_back(k);
+            }
+        std::sort(imp.begin(), imp.end());
+        for (size_t p = 0; p < fk.size();) {
+            size_t q = p + 1;
+            while (q < fk.size() && same(fk[p], fk[q])) ++q;
+            THM_REQUIRE(q - p <= 2, "a face is shared by more than two cells");
+            int64_t fv[4];
+            for (int k = 0; k < 4; ++k) fv[k] = m->cells[(int64_t)fk[p].cell * 8 + lfaces[fk[p].lf][k]];
+            if (q - p == 1) {
+                std::array<int64_t, 4> k{fk[p].k[0], fk[p].k[1], fk[p].k[2], fk[p].k[3]};
+                if (std::binary_search(imp.begin(), imp.end(), k)) add_face(fv, 1, m->cell_sub[fk[p].cell], -1);
+            } else if (m->cell_sub[fk[p].cell] != m->cell_sub[fk[p + 1].cell]) {
+                add_face(fv, 2, m->cell_sub[fk[p].cell], m->cell_sub[fk[p + 1].cell]);
+            }
+            p = q;
         }
     }
-    std::sort(ifs.begin(), ifs.end(), [](const IfE& a, const IfE& b) {
-        if (a.i != b.i) return a.i < b.i;
-        if (a.j != b.j) return a.j < b.j;
-        return a.g < b.g;
-    });
-    m->n_if = (int64_t)ifs.size();
-    m->if_recv.resize(m->n_if); m->if_send.resize(m->n_if); m->if_gdof.resize(m->n_if);
-    m->if_rowi.resize(m->n_if); m->if_rowj.resize(m->n_if); m->if_partner.resize(m->n_if);
-    m->if_edge.resize(m->n_if); m->if_fn.resize(m->n_if);
+    m->n_face = (int64_t)m->face_kind.size();
     auto loc_in = [&](int64_t g, int s) -> int32_t {
+        if (s < 0 || m->is_dir[g]) return -1;
         for (int64_t p = m->copy_ptr[g]; p < m->copy_ptr[g + 1]; ++p)
             if (m->loc_sub[m->copy_idx[p]] == s) return m->copy_idx[p];
         return -1;
     };
-    for (int64_t k = 0; k < m->n_if; ++k) {
-        m->if_recv[k] = ifs[k].i; m->if_send[k] = ifs[k].j; m->if_gdof[k] = ifs[k].g;
-        m->if_edge[k] = ifs[k].edge; m->if_fn[k] = ifs[k].fn;
-        m->if_rowi[k] = loc_in(ifs[k].g, ifs[k].i);
-        m->if_rowj[k] = loc_in(ifs[k].g, ifs[k].j);
-        THM_REQUIRE(m->if_rowi[k] >= 0 && m->if_rowj[k] >= 0, "internal: interface DOF without copies");
+    m->face_loc.assign(m->n_face * 2 * fd, -1);
+    for (int64_t f = 0; f < m->n_face; ++f)
+        for (int side = 0; side < 2; ++side)
+            for (int a = 0; a < fd; ++a)
+                m->face_loc[(f * 2 + side) * fd + a] = loc_in(m->face_dof[f * fd + a], m->face_sub[f * 2 + side]);
+    // per local row: the faces (of its subdomain) whose terms reach it
+    m->row_face.assign(m->n_loc * RF, -1);
+    m->row_face_a.assign(m->n_loc * RF, 0);
+    m->row_face_side.assign(m->n_loc * RF, 0);
+    {
+        std::vector<int> cnt(m->n_loc, 0);
+        for (int64_t f = 0; f < m->n_face; ++f)
+            for (int side = 0; side < 2; ++side)
+                for (int a = 0; a < fd; ++a) {
+                    int32_t r = m->face_loc[(f * 2 + side) * fd + a];
+                    if (r < 0) continue;
+                    THM_REQUIRE(cnt[r] < RF, "internal: too many boundary faces at one DOF");
+                    m->row_face[r * RF + cnt[r]] = (int32_t)f;
+                    m->row_face_a[r * RF + cnt[r]] = (int8_t)a;
+                    m->row_face_side[r * RF + cnt[r]] = (int8_t)side;
+                    cnt[r]++;
+                }
     }
+    // interface entries: one per (receiver i, sender j, free DOF g on Sigma_ij),
+    // with the terms (face, a, b, sender column) of (M_Sigma_ij u_j)[g]
+    struct Term { int32_t i, j; int64_t g; int32_t f; int8_t a, b; int32_t col; };
+    std::vector<Term> terms;
+    for (int64_t f = 0; f < m->n_face; ++f) {
+        if (m->face_kind[f] != 2) continue;
+        for (int side = 0; side < 2; ++side) {
+            const int i = m->face_sub[f * 2 + side], j = m->face_sub[f * 2 + 1 - side];
+            for (int a = 0; a < fd; ++a) {
+                if (m->face_loc[(f * 2 + side) * fd + a] < 0) continue;       // Dirichlet DOF: no entry
+                const int64_t g = m->face_dof[f * fd + a];
+                for (int b = 0; b < fd; ++b) {
+                    int32_t col = m->face_loc[(f * 2 + 1 - side) * fd + b];
+                    if (col < 0) col = -(m->face_dof[f * fd + b] + 1);
+                    terms.push_back({i, j, g, (int32_t)f, (int8_t)a, (int8_t)b, col});
+                }
+            }
+        }
+    }
+    std::sort(terms.begin(), terms.end(), [](const Term& x, const Term& y) {
+        if (x.i != y.i) return x.i < y.i;
+        if (x.j != y.j) return x.j < y.j;
+        if (x.g != y.g) return x.g < y.g;
+        if (x.f != y.f) return x.f < y.f;
+        return x.b < y.b;
+    });
+    m->if_recv.clear(); m->if_send.clear(); m->if_gdof.clear(); m->if_rowi.clear();
+    m->if_ptr.assign(1, 0); m->if_tf.clear(); m->if_ta.clear(); m->if_tb.clear(); m->if_tcol.clear();
+    for (size_t p = 0; p < terms.size(); ++p) {
+        const Term& t = terms[p];
+        if (p == 0 || t.i != terms[p - 1].i || t.j != terms[p - 1].j || t.g != terms[p - 1].g) {
+            if (p > 0) m->if_ptr.push_back((int64_t)m->if_tf.size());
+            m->if_recv.push_back(t.i); m->if_send.push_back(t.j); m->if_gdof.push_back(t.g);
+            m->if_rowi.push_back(loc_in(t.g, t.i));
+            THM_REQUIRE(m->if_rowi.back() >= 0, "internal: interface DOF without a receiver copy");
+        }
+        m->if_tf.push_back(t.f); m->if_ta.push_back(t.a); m->if_tb.push_back(t.b); m->if_tcol.push_back(t.col);
+    }
+    if (!terms.empty()) m->if_ptr.push_back((int64_t)m->if_tf.size());
+    m->n_if = (int64_t)m->if_recv.size();
+    m->if_partner.assign(m->n_if, -1);
     for (int64_t k = 0; k < m->n_if; ++k) {
-        // partner entry (j <- i, same DOF): binary search in the sorted list
-        IfE key{ifs[k].j, ifs[k].i, ifs[k].g, 0, 0};
-        auto it = std::lower_bound(ifs.begin(), ifs.end(), key, [](const IfE& a, const IfE& b) {
-            if (a.i != b.i) return a.i < b.i;
-            if (a.j != b.j) return a.j < b.j;
-            return a.g < b.g;
-        });
-        THM_REQUIRE(it != ifs.end() && it->i == key.i && it->j == key.j && it->g == key.g,
-                    "internal: interface entry without partner");
-        m->if_partner[k] = (int32_t)(it - ifs.begin());
+        // partner entry (j <- i, same DOF): binary search in the sorted entry list
+        int64_t lo = 0, hi = m->n_if - 1, found = -1;
+        const int32_t ki = m->if_send[k], kj = m->if_recv[k];
+        const int64_t kg = m->if_gdof[k];
+        while (lo <= hi) {
+            int64_t mid = (lo + hi) / 2;
+            auto c = std::make_tuple(m->if_recv[mid], m->if_send[mid], m->if_gdof[mid]);
+            auto w = std::make_tuple(ki, kj, kg);
+            if (c == w) { found = mid; break; }
+            if (c < w) lo = mid + 1; else hi = mid - 1;
+        }
+        THM_REQUIRE(found >= 0, "internal: interface entry without partner");
+        m->if_partner[k] = (int32_t)found;
     }
     m->rowg_ptr.assign(m->n_loc + 1, 0);
     for (int64_t k = 0; k < m->n_if; ++k) m->rowg_ptr[m->if_rowi[k] + 1]++;
@@ -572,9 +684,19 @@ void build_mesh(thm_mesh* m) {
     m->d_slice_ptr.upload(m->slice_ptr);
     m->d_row_cell.upload(m->row_cell);
     m->d_row_k.upload(m->row_k);
-    m->d_row_face_kind.upload(m->row_face_kind);
-    m->d_row_face_fn.upload(m->row_face_fn);
-    m->d_row_face_edge.upload(m->row_face_edge);
+    m->d_face_v.upload(m->face_v);
+    m->d_face_dof.upload(m->face_dof);
+    m->d_face_sgn.upload(m->face_sgn);
+    m->d_face_kind.upload(m->face_kind);
+    m->d_face_loc.upload(m->face_loc);
+    m->d_row_face.upload(m->row_face);
+    m->d_row_face_a.upload(m->row_face_a);
+    m->d_row_face_side.upload(m->row_face_side);
+    m->d_if_ptr.upload(m->if_ptr);
+    m->d_if_tf.upload(m->if_tf);
+    m->d_if_ta.upload(m->if_ta);
+    m->d_if_tb.upload(m->if_tb);
+    m->d_if_tcol.upload(m->if_tcol);
     m->d_levels.upload(m->levels);
     m->d_cpl_ptr.upload(m->cpl_ptr);
     m->d_cpl_col.upload(m->cpl_col);
@@ -585,10 +707,7 @@ void build_mesh(thm_mesh* m) {
     m->d_loc_gdof.upload(m->loc_gdof);
     m->d_loc_sub.upload(m->loc_sub);
     m->d_if_rowi.upload(m->if_rowi);
-    m->d_if_rowj.upload(m->if_rowj);
     m->d_if_partner.upload(m->if_partner);
-    m->d_if_edge.upload(m->if_edge);
-    m->d_if_fn.upload(m->if_fn);
     m->d_rowg_ptr.upload(m->rowg_ptr);
     m->d_rowg_idx.upload(m->rowg_idx);
     m->d_owner_loc.upload(m->owner_loc);

@@ -30,7 +30,8 @@ static __device__ __align__(256) double g_na_scratch[2 * NA_MAX_BLOCKS];
 __global__ void __launch_bounds__(NA_THREADS) k_na_residual(
     int64_t n_dof, const int64_t* __restrict__ copy_ptr, const int32_t* __restrict__ copy_idx,
     const int64_t* __restrict__ loc_gdof, const int64_t* __restrict__ slice_ptr, const int32_t* __restrict__ col,
-    const double* __restrict__ val, const double* __restrict__ bg, const double2* __restrict__ f_loc,
+    const double* __restrict__ val, const double* __restrict__ bg, const double* __restrict__ bvg,
+    const double2* __restrict__ f_loc,
     const double2* __restrict__ u, double* __restrict__ scratch) {
     __shared__ double sr[NA_THREADS / 32], sf[NA_THREADS / 32];
     double rr = 0, ff = 0;
@@ -47,11 +48,12 @@ __global__ void __launch_bounds__(NA_THREADS) k_na_residual(
             for (int t = 0; t < w; ++t) {
                 const int64_t idx = base + ((int64_t)t << 5) + lane;
                 const double2 x = u[loc_gdof[col[idx]]];
-                ar += val[idx] * x.x;
-                ai += val[idx] * x.y;
+                const double b = bvg ? bvg[idx] : 0.0;   // 3-D: + i B_Gamma u on the SELL pattern
+                ar += val[idx] * x.x - b * x.y;
+                ai += val[idx] * x.y + b * x.x;
             }
             const double2 xr = u[loc_gdof[r]];
-            ar -= bg[r] * xr.y;                       // + i B_Gamma u (diagonal impedance term)
+            ar -= bg[r] * xr.y;                       // 2-D: + i B_Gamma u (diagonal impedance term)
             ai += bg[r] * xr.x;
             const double2 fl = f_loc[r];
             fr += fl.x; fi += fl.y;
@@ -131,7 +133,7 @@ extern "C" int thm_residual_noalloc(const thm_sys* s, const double* u, double* o
             THM_LAUNCH(THM_K_DDM, s->st,
                        k_na_residual<<<(unsigned)nb, NA_THREADS, 0, s->st>>>(
                            m->n_dof, m->d_copy_ptr.p, m->d_copy_idx.p, m->d_loc_gdof.p, m->d_slice_ptr.p,
-                           m->d_sell_col.p, s->val64.p, s->bg64.p, s->f_loc.p,
+                           m->d_sell_col.p, s->val64.p, s->bg64.p, m->dim == 3 ? s->bvg64.p : nullptr, s->f_res.p,
                            reinterpret_cast<const double2*>(u), scratch));
         }
         THM_LAUNCH(THM_K_DDM, s->st, k_na_finish<<<1, 256, 0, s->st>>>((int)nb, scratch, out));

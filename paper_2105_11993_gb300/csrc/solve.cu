@@ -58,53 +58,70 @@ __global__ void k_cycle_start(int nseg, int m, const double* __restrict__ nrm2, 
 // Column j of the Hessenberg matrix (h1 + h2 from the two Gram-Schmidt passes,
 // ||w|| below the diagonal), previous Givens rotations, a new rotation, the
 // updated residual estimate |g_{j+1}| and the per-segment convergence flag.
-__global__ void k_givens(int nseg, int j, int m, const double2* __restrict__ h1, const double2* __restrict__ h2,
-                         int ldh, const double* __restrict__ nrm2, double2* __restrict__ Rm,
-                         double* __restrict__ cs, double2* __restrict__ sn, double2* __restrict__ gv,
-                         const double* __restrict__ target, int* __restrict__ active, int* __restrict__ kused,
-                         double* __restrict__ beta, int* __restrict__ nact, int* __restrict__ flag) {
-    int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= nseg) return;
-    if (!active[s]) { beta[s] = 0.0; return; }
-    double2* col = Rm + ((int64_t)s * m + j) * m;      // column j, rows 0..j
-    for (int i = 0; i <= j; ++i) col[i] = cadd(h1[(int64_t)s * ldh + i], h2[(int64_t)s * ldh + i]);
-    double hn = sqrt(nrm2[s]);
-    if (!isfinite(hn)) { atomicExch(flag, 1); active[s] = 0; beta[s] = 0.0; return; }
-    double* c = cs + (int64_t)s * m;
-    double2* sg = sn + (int64_t)s * m;
-    for (int i = 0; i < j; ++i) {
-        double2 a = col[i], b = col[i + 1];
-        // [a; b] <- [[c, s], [-conj(s), c]] [a; b]
-        double2 t = make_double2(c[i] * a.x + sg[i].x * b.x - sg[i].y * b.y, c[i] * a.y + sg[i].x * b.y + sg[i].y * b.x);
-        double2 u = make_double2(-(sg[i].x * a.x + sg[i].y * a.y) + c[i] * b.x, -(sg[i].x * a.y - sg[i].y * a.x) + c[i] * b.y);
-        col[i] = t;
-        col[i + 1] = u;
+__global__ void __launch_bounds__(32) k_givens(int nseg, int j, int m, const double2* __restrict__ h1,
+                                               const double2* __restrict__ h2, int ldh,
+                                               const double* __restrict__ nrm2, double2* __restrict__ Rm,
+                                               double* __restrict__ cs, double2* __restrict__ sn,
+                                               double2* __restrict__ gv, const double* __restrict__ target,
+                                               int* __restrict__ active, int* __restrict__ kused,
+                                               double* __restrict__ beta, int* __restrict__ nact,
+                                               int* __restrict__ flag) {
+    // one warp per segment: the column and the rotations are staged in shared
+    // memory in parallel; the rotations themselves run on lane 0
+    extern __shared__ unsigned char gsm[];
+    double2* col = reinterpret_cast<double2*>(gsm);          // [j+1]
+    double2* sg = col + (j + 1);                             // [j]
+    double* c = reinterpret_cast<double*>(sg + j);           // [j]
+    const int s = blockIdx.x;
+    const int lane = threadIdx.x;
+    if (!active[s]) {
+        if (lane == 0) beta[s] = 0.0;
+        return;
     }
-    double2 a = col[j];
-    double am = hypot(a.x, a.y);
-    double d = hypot(am, hn);
-    double cj;
-    double2 sj;
-    if (d == 0.0) { cj = 1.0; sj = make_double2(0, 0); }
-    else if (am == 0.0) { cj = 0.0; sj = make_double2(1.0, 0.0); }
-    else {
-        cj = am / d;
-        // s = (a/|a|) * conj(hn) / d, hn real
-        sj = make_double2(a.x / am * hn / d, a.y / am * hn / d);
+    for (int i = lane; i <= j; i += 32) col[i] = cadd(h1[(int64_t)s * ldh + i], h2[(int64_t)s * ldh + i]);
+    for (int i = lane; i < j; i += 32) { c[i] = cs[(int64_t)s * m + i]; sg[i] = sn[(int64_t)s * m + i]; }
+    __syncwarp();
+    if (lane == 0) {
+        const double hn = sqrt(nrm2[s]);
+        if (!isfinite(hn)) {
+            atomicExch(flag, 1);
+            active[s] = 0;
+            beta[s] = 0.0;
+        } else {
+            for (int i = 0; i < j; ++i) {
+                double2 a = col[i], b = col[i + 1];
+                // [a; b] <- [[c, s], [-conj(s), c]] [a; b]
+                col[i] = make_double2(c[i] * a.x + sg[i].x * b.x - sg[i].y * b.y, c[i] * a.y + sg[i].x * b.y + sg[i].y * b.x);
+                col[i + 1] = make_double2(-(sg[i].x * a.x + sg[i].y * a.y) + c[i] * b.x, -(sg[i].x * a.y - sg[i].y * a.x) + c[i] * b.y);
+            }
+            double2 a = col[j];
+            double am = hypot(a.x, a.y);
+            double d = hypot(am, hn);
+            double cj;
+            double2 sj;
+            if (d == 0.0) { cj = 1.0; sj = make_double2(0, 0); }
+            else if (am == 0.0) { cj = 0.0; sj = make_double2(1.0, 0.0); }
+            else {
+                cj = am / d;
+                sj = make_double2(a.x / am * hn / d, a.y / am * hn / d);      // (a/|a|) conj(hn)/d
+            }
+            cs[(int64_t)s * m + j] = cj;
+            sn[(int64_t)s * m + j] = sj;
+            col[j] = make_double2(cj * a.x + sj.x * hn, cj * a.y + sj.y * hn);
+            double2* g = gv + (int64_t)s * (m + 1);
+            double2 gj = g[j];
+            g[j + 1] = make_double2(-(sj.x * gj.x + sj.y * gj.y), -(sj.x * gj.y - sj.y * gj.x));   // -conj(s) g_j
+            g[j] = make_double2(cj * gj.x, cj * gj.y);
+            kused[s] = j + 1;
+            beta[s] = hn;
+            double res = hypot(g[j + 1].x, g[j + 1].y);
+            if (res <= target[s] || hn == 0.0) active[s] = 0;
+            else atomicAdd(nact, 1);
+        }
     }
-    c[j] = cj;
-    sg[j] = sj;
-    col[j] = make_double2(cj * a.x + (sj.x * hn), cj * a.y + (sj.y * hn));
-    double2* g = gv + (int64_t)s * (m + 1);
-    double2 gj = g[j];
-    // g_{j+1} = -conj(s) g_j ; g_j = c g_j
-    g[j + 1] = make_double2(-(sj.x * gj.x + sj.y * gj.y), -(sj.x * gj.y - sj.y * gj.x));
-    g[j] = make_double2(cj * gj.x, cj * gj.y);
-    kused[s] = j + 1;
-    beta[s] = hn;
-    double res = hypot(g[j + 1].x, g[j + 1].y);
-    if (res <= target[s] || hn == 0.0) active[s] = 0;
-    else atomicAdd(nact, 1);
+    __syncwarp();
+    double2* out = Rm + ((int64_t)s * m + j) * m;             // column j, rows 0..j
+    for (int i = lane; i <= j; i += 32) out[i] = col[i];
 }
 
 // y = R^{-1} g (upper triangular, k = kused[s])
@@ -141,16 +158,24 @@ __global__ void k_rhs(int64_t n, const double2* __restrict__ src, const int64_t*
     b[r] = v;
 }
 
-// Impedance-trace exchange (Eq. 6):  G_{i<-j} = -G_{j<-i} + 2 i kappa omega M_Sigma u_j
-__global__ void k_exchange(int64_t n_if, const int32_t* __restrict__ partner, const int32_t* __restrict__ rowj,
-                           const double* __restrict__ mass, double kw, const double2* __restrict__ g_in,
-                           const double2* __restrict__ u, double2* __restrict__ g_out) {
+// Impedance-trace exchange (Eq. 6):  G_{i<-j} = -G_{j<-i} + 2 i kappa omega (M_Sigma_ij u_j)[g],
+// the face-mass product summed over the entry's terms; a term on a Dirichlet
+// DOF of u_j uses u_D when the sweep carries the Dirichlet lifting, else 0.
+__global__ void k_exchange(int64_t n_if, const int32_t* __restrict__ partner, const int64_t* __restrict__ ptr,
+                           const int32_t* __restrict__ tcol, const double* __restrict__ val, double kw,
+                           const double2* __restrict__ g_in, const double2* __restrict__ u,
+                           const double2* __restrict__ uD, double2* __restrict__ g_out) {
     int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (k >= n_if) return;
+    double ar = 0, ai = 0;
+    for (int64_t p = ptr[k]; p < ptr[k + 1]; ++p) {
+        const int32_t c = tcol[p];
+        double2 x = c >= 0 ? u[c] : (uD ? uD[-(int64_t)c - 1] : make_double2(0, 0));
+        ar += val[p] * x.x;
+        ai += val[p] * x.y;
+    }
     double2 gp = g_in ? g_in[partner[k]] : make_double2(0, 0);
-    double2 uj = u[rowj[k]];
-    double f = 2.0 * kw * mass[k];
-    g_out[k] = make_double2(-gp.x - f * uj.y, -gp.y + f * uj.x);
+    g_out[k] = make_double2(-gp.x - 2.0 * kw * ai, -gp.y + 2.0 * kw * ar);
 }
 
 // u[d] += u_loc[owner(d)] on free DOFs
@@ -379,7 +404,8 @@ struct Krylov {
                 THM_LAUNCH(THM_K_UPDATE, st, k_chunk_update<V><<<nch, KT, nk * sizeof(double2), st>>>(d_chunks, basis.p, n, nk, h2.p, m + 1, w.p, nrm_part.p));
                 THM_LAUNCH(THM_K_KRYLOV, st, k_seg_reduce_real<<<nblk(nseg), 256, 0, st>>>(nseg, seg_ch.p, nrm_part.p, nrm.p));
                 nact.zero(st);
-                THM_LAUNCH(THM_K_KRYLOV, st, k_givens<<<nblk(nseg), 128, 0, st>>>(nseg, j, m, h1.p, h2.p, m + 1, nrm.p, Rm.p, cs.p, sn.p, gv.p,
+                const size_t gsm = (size_t)(j + 1) * sizeof(double2) + (size_t)j * (sizeof(double2) + sizeof(double));
+                THM_LAUNCH(THM_K_KRYLOV, st, k_givens<<<nseg, 32, gsm, st>>>(nseg, j, m, h1.p, h2.p, m + 1, nrm.p, Rm.p, cs.p, sn.p, gv.p,
                                                      target.p, active.p, kused.p, beta.p, nact.p, flag.p));
                 THM_LAUNCH(THM_K_KRYLOV, st, k_chunk_scale<V><<<nch, 256, 0, st>>>(d_chunks, w.p, beta.p, basis.p + (int64_t)(j + 1) * n));
                 ++total;
@@ -513,11 +539,24 @@ SolveCfg make_cfg(const thm_solve_opts* o) {
     return c;
 }
 
+// The SELL face-term arrays of a precision (3-D only; 2-D keeps them diagonal).
+static inline void bv_arrays(const thm_sys* s, const double*, const double** g, const double** sg) {
+    *g = s->m->dim == 3 ? s->bvg64.p : nullptr;
+    *sg = s->m->dim == 3 ? s->bvs64.p : nullptr;
+}
+static inline void bv_arrays(const thm_sys* s, const float*, const float** g, const float** sg) {
+    *g = s->m->dim == 3 ? s->bvg32.p : nullptr;
+    *sg = s->m->dim == 3 ? s->bvs32.p : nullptr;
+}
+
 template <class V, class F>
 static void apply_T(const thm_sys* s, const F* val, const F* bg, const F* bs, int use_bs, const V* x, V* y) {
     const thm_mesh* m = s->m;
-    THM_LAUNCH(THM_K_SPMV, 0, k_spmv<V, F><<<nblk(m->n_loc), 256, 0, s->st>>>(m->n_loc, m->d_slice_ptr.p, m->d_sell_col.p, val, bg, bs,
-                                                    use_bs, x, y));
+    const F *bvg, *bvs;
+    bv_arrays(s, val, &bvg, &bvs);
+    THM_LAUNCH(THM_K_SPMV, s->st,
+               k_spmv<V, F><<<nblk(m->n_loc), 256, 0, s->st>>>(m->n_loc, m->d_slice_ptr.p, m->d_sell_col.p, val, bg, bs,
+                                                                use_bs, bvg, bvs, x, y));
 }
 
 template <class V, class F>
@@ -528,22 +567,28 @@ static void apply_Pinv(const thm_sys* s, const F* fac, const F* cval, const int3
     auto r4 = [](int64_t v) { return (int64_t)((v + 3) / 4 * 4); };
     int max_lev = 0;
     for (const auto& S : m->subs) max_lev = std::max(max_lev, S.nlev);
-    const size_t tail = (size_t)(r4(m->max_ne) + r4(m->max_m)) * sizeof(R) + 4 * (size_t)(max_lev + 1) * sizeof(int) +
-                        5 * (size_t)max_lev * sizeof(long long) + 16;
+    THM_REQUIRE(m->max_m <= BT_MAXO * 512 / BT_NG, "level block larger than the block-solve kernel supports");
+    const size_t tail = (size_t)(r4(m->max_ne) + (1 + BT_NG) * r4(m->max_m)) * sizeof(R) +
+                        4 * (size_t)(max_lev + 1) * sizeof(int) + 5 * (size_t)max_lev * sizeof(long long) + 16;
     const size_t csr = (size_t)r4(m->max_m + 1) * 4 + (size_t)r4(m->max_cnz) * (4 + sizeof(F)) + 16;
     const size_t cap = 220 * 1024;
     THM_REQUIRE(tail + 3 * csr <= cap, "subdomain too large for the shared-memory block solve");
     // tile height: the largest multiple of 4 rows (<= 64) whose ring of 3..6 slots fits
-    int rows = 64, nslot = 6;
+    // ring depth: as many slots as requested (default 8) with the tallest tiles
+    // that fit; fewer slots only when even 16-row tiles do not fit
+    static const int want = getenv("THM_BT_SLOTS") ? std::max(3, std::min(8, atoi(getenv("THM_BT_SLOTS")))) : 8;
+    int rows = 0, nslot = 0;
     size_t slot = 0;
-    for (;; rows -= 4) {
-        THM_REQUIRE(rows >= 4, "level block too wide for the shared-memory block solve");
-        slot = std::max(csr, (size_t)rows * m->max_m * sizeof(F) + 16);
-        slot = (slot + 15) / 16 * 16;
-        nslot = (int)std::min<size_t>(6, (cap - tail) / slot);
-        if (nslot >= 3) break;
+    for (int ns = want; ns >= 3 && rows == 0; --ns) {
+        const size_t per = (cap - tail - 128) / ns;
+        for (int r = (int)r4(m->max_m); r >= 4; r -= 4) {
+            size_t sb = std::max(csr, (size_t)r * m->max_m * sizeof(F) + 16);
+            sb = (sb + 15) / 16 * 16;
+            if (sb <= per && (r >= 16 || ns == 3)) { rows = r; nslot = ns; slot = sb; break; }
+        }
     }
-    const size_t smem = (size_t)nslot * slot + tail;
+    THM_REQUIRE(rows >= 4, "level block too wide for the shared-memory block solve");
+    const size_t smem = (size_t)nslot * slot + tail + ((nslot * 8 + 15) / 16) * 16;
     static size_t attr = 0;
     if (smem > 48 * 1024 && smem > attr) {
         THM_CUDA(cudaFuncSetAttribute(k_bt_apply<V, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -554,7 +599,7 @@ static void apply_Pinv(const thm_sys* s, const F* fac, const F* cval, const int3
                k_bt_apply<V, F><<<grid, 512, smem, s->st>>>(m->d_subs.p, m->d_levels.p, fac, m->d_cpl_ptr.p,
                                                             m->d_cpl_col.p, cval, m->n_loc, m->order == 2 ? 1 : 0,
                                                             ai, av, ci, cv, ei, ev, rows, nslot, (int)slot,
-                                                            (int)m->max_ne, m->max_m, max_lev, x, y));
+                                                            (int)m->max_ne, m->max_m, max_lev, s->dev_err.p, x, y));
 }
 
 template <class V>
@@ -622,7 +667,7 @@ static void subdomain_solves(thm_sys* s, const SolveCfg& c, const double2* b, do
 
 // One sweep: x = T^{-1}(src + R g_in), g_out = exchange(g_in, x).
 static void sweep(thm_sys* s, const SolveCfg& c, const double2* src, const double2* g_in, double2* g_out,
-                  double2* x, RunStats& rs) {
+                  double2* x, RunStats& rs, const double2* uD = nullptr) {
     const thm_mesh* m = s->m;
     Work* w = s->w;
     cudaStream_t st = s->st;
@@ -630,14 +675,16 @@ static void sweep(thm_sys* s, const SolveCfg& c, const double2* src, const doubl
                                           m->n_if > 0 ? g_in : nullptr, w->b64.p));
     subdomain_solves(s, c, w->b64.p, x, rs);
     if (m->n_if > 0 && g_out)
-        THM_LAUNCH(THM_K_DDM, st, k_exchange<<<nblk(m->n_if), 256, 0, st>>>(m->n_if, m->d_if_partner.p, m->d_if_rowj.p, s->if_mass.p,
-                                                  s->kappa * s->omega, g_in, x, g_out));
+        THM_LAUNCH(THM_K_DDM, st, k_exchange<<<nblk(m->n_if), 256, 0, st>>>(m->n_if, m->d_if_partner.p, m->d_if_ptr.p,
+                                                                           m->d_if_tcol.p, s->if_val.p,
+                                                                           s->kappa * s->omega, g_in, x, uD, g_out));
     rs.sweeps++;
     THM_CUDA(cudaGetLastError());
 }
 
 // DDM solve of Eq. 8 for local sources src -> local solution uloc.
-static void ddm_solve(thm_sys* s, const SolveCfg& c, const double2* src, double2* uloc, RunStats& rs) {
+static void ddm_solve(thm_sys* s, const SolveCfg& c, const double2* src, double2* uloc, RunStats& rs,
+                      const double2* uD) {
     const thm_mesh* m = s->m;
     Work* w = s->w;
     cudaStream_t st = s->st;
@@ -647,7 +694,7 @@ static void ddm_solve(thm_sys* s, const SolveCfg& c, const double2* src, double2
     }
     // b = A_src(0): sweep with sources and zero interface data
     w->g0.zero(st);
-    sweep(s, c, src, w->g0.p, w->gb.p, uloc, rs);
+    sweep(s, c, src, w->g0.p, w->gb.p, uloc, rs, uD);
     auto A = [&](const double2* v, double2* out) {
         SolveCfg cr = c;
         if (c.relax) {
@@ -674,7 +721,7 @@ static void ddm_solve(thm_sys* s, const SolveCfg& c, const double2* src, double2
     KStats ko = w->outer.solve(Av, none, w->gb.p, w->gsol.p, true, c.outer_tol, c.outer_maxit, st);
     rs.outer += (int)ko.iters;
     if (ko.status != THM_OK && rs.status == THM_OK) rs.status = ko.status;
-    sweep(s, c, src, w->gsol.p, nullptr, uloc, rs);
+    sweep(s, c, src, w->gsol.p, nullptr, uloc, rs, uD);
 }
 
 static double global_norm(thm_sys* s, const double2* x, int64_t n) {
@@ -689,6 +736,17 @@ static double global_norm(thm_sys* s, const double2* x, int64_t n) {
     return std::sqrt(t);
 }
 
+// A bounded device-side wait that gave up leaves a flag: report THM_ETIMEOUT.
+static void check_device_error(thm_sys* s) {
+    int h = 0;
+    THM_CUDA(cudaMemcpyAsync(&h, s->dev_err.p, sizeof(int), cudaMemcpyDeviceToHost, s->st));
+    THM_CUDA(cudaStreamSynchronize(s->st));
+    if (h) {
+        THM_CUDA(cudaMemsetAsync(s->dev_err.p, 0, sizeof(int), s->st));
+        fail(THM_ETIMEOUT, "a bounded wait for a TMA copy in the block-preconditioner apply gave up");
+    }
+}
+
 // FP64 true residual r = f - K u for a local right-hand-side split f_loc of f.
 static double true_residual_rhs(thm_sys* s, const double2* f_loc, const double2* u, double2* rglob) {
     const thm_mesh* m = s->m;
@@ -701,10 +759,12 @@ static double true_residual_rhs(thm_sys* s, const double2* f_loc, const double2*
     return global_norm(s, rglob, m->n_dof);
 }
 
-// Refined DDM solve of K_FF u_F = f (f given by its local split f_loc), u
-// initialised with u0 on all DOFs (the Dirichlet values, or zeros).
-int solve_rhs(thm_sys* s, const SolveCfg& c, const double2* f_loc, const double2* u0, double2* u, RunStats& rs,
-              double& rel) {
+// Refined DDM solve of K_FF u_F = f, u initialised with u0 on all DOFs (the
+// Dirichlet values, or zeros).  f_res is the local split of f (summed over
+// copies it is f); f_src the sources of the first DDM solve, which differ from
+// f_res by the transmission terms of u0 on Dirichlet DOFs of Sigma.
+int solve_rhs(thm_sys* s, const SolveCfg& c, const double2* f_src, const double2* f_loc, const double2* u0,
+              double2* u, RunStats& rs, double& rel) {
     const thm_mesh* m = s->m;
     Work* w = s->w;
     cudaStream_t st = s->st;
@@ -712,10 +772,12 @@ int solve_rhs(thm_sys* s, const SolveCfg& c, const double2* f_loc, const double2
     double fn = global_norm(s, w->rglob.p, m->n_dof);
     if (u0) THM_CUDA(cudaMemcpyAsync(u, u0, m->n_dof * sizeof(double2), cudaMemcpyDeviceToDevice, st));
     else THM_CUDA(cudaMemsetAsync(u, 0, m->n_dof * sizeof(double2), st));
-    THM_CUDA(cudaMemcpyAsync(w->src.p, f_loc, m->n_loc * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+    THM_CUDA(cudaMemcpyAsync(w->src.p, f_src, m->n_loc * sizeof(double2), cudaMemcpyDeviceToDevice, st));
     rel = fn > 0 ? 1.0 : 0.0;
     for (int it = 0; it < c.max_refine && fn > 0; ++it) {
-        ddm_solve(s, c, w->src.p, w->x64.p, rs);
+        // the first DDM solve carries the Dirichlet lifting (u0 = u_D); the
+        // refinement corrections have zero Dirichlet values
+        ddm_solve(s, c, w->src.p, w->x64.p, rs, it == 0 ? u0 : nullptr);
         rs.refine++;
         THM_LAUNCH(THM_K_DDM, st, k_glue_add<<<nblk(m->n_dof), 256, 0, st>>>(m->n_dof, m->d_owner_loc.p, w->x64.p, u));
         double rn = true_residual_rhs(s, f_loc, u, w->rglob.p);
@@ -727,6 +789,7 @@ int solve_rhs(thm_sys* s, const SolveCfg& c, const double2* f_loc, const double2
     }
     THM_CUDA(cudaStreamSynchronize(st));
     THM_CUDA(cudaGetLastError());
+    check_device_error(s);
     if (rs.status == THM_EBREAKDOWN) return THM_EBREAKDOWN;
     if (rel > c.rtol) return THM_ENOCONV;
     return THM_OK;
@@ -755,7 +818,7 @@ int solve(thm_sys* s, const thm_solve_opts* opts, double2* u, thm_stats* stats) 
     prepare(s, c);
     RunStats rs;
     double rel = 0;
-    int rc = solve_rhs(s, c, s->f_loc.p, s->uD.p, u, rs, rel);
+    int rc = solve_rhs(s, c, s->f_loc.p, s->f_res.p, s->uD.p, u, rs, rel);
     double sec = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     fill_stats(rs, rel, sec, stats);
     return rc;
@@ -768,6 +831,8 @@ void apply_local(thm_sys* s, int op, int mode, const double2* x, double2* y) {
     if (op == THM_OP_PINV) {
         ensure_factor(s, f32);
         apply_Pinv_mode<double2>(s, f32, x, y);
+        THM_CUDA(cudaStreamSynchronize(s->st));
+        check_device_error(s);
     } else {
         int use_bs = op == THM_OP_T;
         if (f32) apply_T<double2, float>(s, s->val32.p, s->bg32.p, s->bs32.p, use_bs, x, y);
@@ -783,7 +848,7 @@ int sweep_diag(thm_sys* s, const thm_solve_opts* opts, int with_sources, const d
     ensure_factor(s, c.fp32);
     ensure_work(s, c.fp32, c.m_in, c.m_out);
     RunStats rs;
-    sweep(s, c, with_sources ? s->f_loc.p : nullptr, g_in, g_out, uloc, rs);
+    sweep(s, c, with_sources ? s->f_loc.p : nullptr, g_in, g_out, uloc, rs, with_sources ? s->uD.p : nullptr);
     THM_CUDA(cudaStreamSynchronize(s->st));
     if (stats) {
         memset(stats, 0, sizeof(*stats));

@@ -21,8 +21,8 @@ struct RunStats {
 
 SolveCfg make_cfg(const thm_solve_opts* o);
 void prepare(thm_sys* s, const SolveCfg& c);
-int solve_rhs(thm_sys* s, const SolveCfg& c, const double2* f_loc, const double2* u0, double2* u, RunStats& rs,
-              double& rel);
+int solve_rhs(thm_sys* s, const SolveCfg& c, const double2* f_src, const double2* f_loc, const double2* u0,
+              double2* u, RunStats& rs, double& rel);
 void fill_stats(const RunStats& rs, double rel, double sec, thm_stats* stats);
 
 }  // namespace thm

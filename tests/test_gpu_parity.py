@@ -41,6 +41,18 @@ def ragged_problem(order=1, n=10, omega=9.0):
     return W.Problem("ragged", mesh, order, mu, omega, 1.0, pol, d)
 
 
+def ragged_cube(n=6, omega=7.0):
+    """Eight subdomains of unequal size in 3-D (cut at x=2h, y=4h, z=3h)."""
+    mesh = W.structured_mesh_3d(n, 1, relabel=True, rotate_cells=True)
+    X = mesh.coords[mesh.cells].mean(1)
+    mesh.cell_sub = ((X[:, 0] > 2.0 / n).astype(np.int32) + 2 * (X[:, 1] > 4.0 / n)
+                     + 4 * (X[:, 2] > 3.0 / n)).astype(np.int32)
+    mesh.n_sub = 8
+    pol, d = W.plane_wave_y(3)
+    mu = W.mu_inv_lognormal(mesh.n_cell, 0.3, "ragged3")
+    return W.Problem("ragged3", mesh, 1, mu, omega, 1.0, pol, d)
+
+
 CASES = {
     "c0": lambda: W.config("square32_p1"),
     "p1_rot": lambda: W.square_problem(12, 3, 1, 11.0, mu_inv=W.mu_inv_lognormal(144, 0.3, "a"),
@@ -50,6 +62,10 @@ CASES = {
     "ragged_p1": lambda: ragged_problem(1),
     "ragged_p2": lambda: ragged_problem(2, n=8),
     "single": lambda: W.square_problem(8, 1, 2, 7.0),
+    "cube_rot": lambda: W.cube_problem(4, 2, 6.0, mu_inv=W.mu_inv_lognormal(64, 0.3, "c3"),
+                                       relabel=True, rotate_cells=True),
+    "cube_pw": lambda: W.cube_problem(6, 3, 7.0, bc="planewave"),
+    "cube_ragged": lambda: ragged_cube(),
 }
 
 
@@ -58,7 +74,7 @@ def test_numbering_and_signs_bit_exact(name):
     P = CASES[name]()
     mesh, _ = make_system(P)
     info = mesh.info(with_dofs=True)
-    d = fem.number_dofs(P.mesh.cells, 2, P.order)
+    d = fem.number_dofs(P.mesh.cells, P.mesh.dim, P.order)
     assert info["n_dof"] == d.n_dof and info["n_edge"] == d.n_edge
     assert np.array_equal(info["cell_dofs"], d.cell_dofs)
     assert np.array_equal(info["cell_signs"], d.cell_signs)
@@ -116,7 +132,7 @@ def test_local_operators(name, op, mode):
         assert err <= tol, (s.idx, err)
 
 
-@pytest.mark.parametrize("name", ["c0", "p2_rot", "ragged_p2"])
+@pytest.mark.parametrize("name", ["c0", "p2_rot", "ragged_p2", "cube_rot", "cube_ragged"])
 def test_dirichlet_values_and_lifting(name):
     P = CASES[name]()
     mesh, sysg = make_system(P)
@@ -133,7 +149,7 @@ def test_dirichlet_values_and_lifting(name):
         assert np.linalg.norm(f[idx] - ref) <= 1e-13 * max(1.0, np.linalg.norm(ref))
 
 
-@pytest.mark.parametrize("name", ["c0", "p2_rot", "ragged_p1"])
+@pytest.mark.parametrize("name", ["c0", "p2_rot", "ragged_p1", "cube_rot", "cube_ragged"])
 def test_sweep_and_exchange(name):
     """One sweep (Eqs. 5-6) on random interface data vs the oracle's sweep
     with direct subdomain solves."""
