@@ -505,33 +505,35 @@ __global__ void k_condensed_values(int64_t n_loc, int nb, int maxc, int condense
 }
 
 // ---------------------------------------------------------------------------
-// Level-block-tridiagonal factorisation of S (= P_i, or its edge Schur
-// complement for order 2), one CTA per subdomain.  With levels l = 0..L-1
-// (BFS layers of the DOF graph, merged up to max_block), S is block
-// tridiagonal with diagonal blocks D_l and off-diagonal blocks
-// E_l = S_{l,l-1}, F_l = S_{l,l+1} = E_{l+1}^T:
-//   S_0 = D_0,  S_l = D_l - E_l W_{l-1} E_l^T,  W_l = S_l^{-1}.
-// Apply (x = S^{-1} r):  z_l = W_l (r_l - E_l z_{l-1});  x_{L-1} = z_{L-1},
-// x_l = z_l - W_l F_l x_{l+1}.  Only the dense W_l are stored; E_l, F_l are
-// read from the sparse S.  S_l^{-1} by Gauss-Jordan with partial pivoting.
+// Twisted level-block-tridiagonal factorisation of S (= P_i, or its edge
+// Schur complement for order 2).  With levels l = 0..L-1 (BFS layers of the
+// DOF graph, merged up to max_block), S is block tridiagonal with diagonal
+// blocks D_l and couplings E_l = S_{l,l-1}, F_l = S_{l,l+1} = E_{l+1}^T.
+// Eliminating from both ends towards the middle level k:
+//   top    (l = 0..k-1):    S_l = D_l - E_l W_{l-1} E_l^T      (no term for l = 0)
+//   bottom (l = L-1..k+1):  S_l = D_l - F_l W_{l+1} F_l^T      (no term for l = L-1)
+//   middle:                 S_k = D_k - E_k W_{k-1} E_k^T - F_k W_{k+1} F_k^T
+// with W_l = S_l^{-1} by Gauss-Jordan with partial pivoting, all in FP64.
+// Each W_l is stored with row stride r4(m_l) (zero padding).
 // ---------------------------------------------------------------------------
 template <class F>
-__device__ void cta_gemm(F* C, const F* A, const F* B, int m, int k, int n, bool b_transposed, bool subtract) {
+__device__ void cta_gemm(F* C, int ldc, const F* A, int lda, const F* B, int ldb, int m, int k, int n,
+                         bool b_transposed, bool subtract) {
     // C (m x n) (-)= A (m x k) * (B (k x n) or B^T with B (n x k)); row-major, no aliasing
     for (int t = threadIdx.x; t < m * n; t += blockDim.x) {
         int i = t / n, j = t % n;
         F acc = 0;
         if (b_transposed)
-            for (int q = 0; q < k; ++q) acc += A[(int64_t)i * k + q] * B[(int64_t)j * k + q];
+            for (int q = 0; q < k; ++q) acc += A[(int64_t)i * lda + q] * B[(int64_t)j * ldb + q];
         else
-            for (int q = 0; q < k; ++q) acc += A[(int64_t)i * k + q] * B[(int64_t)q * n + j];
-        if (subtract) C[t] -= acc;
-        else C[t] = acc;
+            for (int q = 0; q < k; ++q) acc += A[(int64_t)i * lda + q] * B[(int64_t)q * ldb + j];
+        if (subtract) C[(int64_t)i * ldc + j] -= acc;
+        else C[(int64_t)i * ldc + j] = acc;
     }
 }
 
 template <class F>
-__device__ bool cta_gauss_jordan(F* W, int m, int* perm, F* fcol, F* rv, int* ri) {
+__device__ bool cta_gauss_jordan(F* W, int m, int ld, int* perm, F* fcol, F* rv, int* ri) {
     __shared__ int s_piv;
     __shared__ int s_bad;
     if (threadIdx.x == 0) s_bad = 0;
@@ -541,7 +543,7 @@ __device__ bool cta_gauss_jordan(F* W, int m, int* perm, F* fcol, F* rv, int* ri
         F best = -1;
         int bi = -1;
         for (int i = k + threadIdx.x; i < m; i += blockDim.x) {
-            F v = W[(int64_t)i * m + k];
+            F v = W[(int64_t)i * ld + k];
             v = v < 0 ? -v : v;
             if (v > best) { best = v; bi = i; }
         }
@@ -569,25 +571,26 @@ __device__ bool cta_gauss_jordan(F* W, int m, int* perm, F* fcol, F* rv, int* ri
         int p = s_piv;
         if (p != k)
             for (int j = threadIdx.x; j < m; j += blockDim.x) {
-                F a = W[(int64_t)k * m + j];
-                W[(int64_t)k * m + j] = W[(int64_t)p * m + j];
-                W[(int64_t)p * m + j] = a;
+                F a = W[(int64_t)k * ld + j];
+                W[(int64_t)k * ld + j] = W[(int64_t)p * ld + j];
+                W[(int64_t)p * ld + j] = a;
             }
         __syncthreads();
-        for (int i = threadIdx.x; i < m; i += blockDim.x) fcol[i] = (i == k) ? F(0) : W[(int64_t)i * m + k];
+        for (int i = threadIdx.x; i < m; i += blockDim.x) fcol[i] = (i == k) ? F(0) : W[(int64_t)i * ld + k];
         __syncthreads();
-        F piv = W[(int64_t)k * m + k];
+        F piv = W[(int64_t)k * ld + k];
         __syncthreads();
         for (int j = threadIdx.x; j < m; j += blockDim.x) {
-            F v = (j == k) ? F(1) : W[(int64_t)k * m + j];
-            W[(int64_t)k * m + j] = v / piv;
+            F v = (j == k) ? F(1) : W[(int64_t)k * ld + j];
+            W[(int64_t)k * ld + j] = v / piv;
         }
         __syncthreads();
         for (int64_t t = threadIdx.x; t < (int64_t)m * m; t += blockDim.x) {
             int i = (int)(t / m), j = (int)(t % m);
             if (i == k) continue;
-            F a = (j == k) ? F(0) : W[t];
-            W[t] = a - fcol[i] * W[(int64_t)k * m + j];
+            const int64_t o = (int64_t)i * ld + j;
+            F a = (j == k) ? F(0) : W[o];
+            W[o] = a - fcol[i] * W[(int64_t)k * ld + j];
         }
         __syncthreads();
     }
@@ -596,9 +599,9 @@ __device__ bool cta_gauss_jordan(F* W, int m, int* perm, F* fcol, F* rv, int* ri
         int p = perm[k];
         if (p != k)
             for (int i = threadIdx.x; i < m; i += blockDim.x) {
-                F a = W[(int64_t)i * m + k];
-                W[(int64_t)i * m + k] = W[(int64_t)i * m + p];
-                W[(int64_t)i * m + p] = a;
+                F a = W[(int64_t)i * ld + k];
+                W[(int64_t)i * ld + k] = W[(int64_t)i * ld + p];
+                W[(int64_t)i * ld + p] = a;
             }
         __syncthreads();
     }
@@ -606,10 +609,10 @@ __device__ bool cta_gauss_jordan(F* W, int m, int* perm, F* fcol, F* rv, int* ri
 }
 
 template <class F>
-__device__ void extract_block(const Level& L, int64_t c0, int mc, F* dst, const int64_t* slice_ptr,
+__device__ void extract_block(const Level& L, int64_t c0, int mc, F* dst, int ld, const int64_t* slice_ptr,
                               const int32_t* col, const uint8_t* pad, const double* val) {
-    // dst (L.size x mc) = S rows of level L, columns in [c0, c0 + mc)
-    for (int64_t t = threadIdx.x; t < (int64_t)L.size * mc; t += blockDim.x) dst[t] = F(0);
+    // dst (L.size x mc, row stride ld, padding zeroed) = S rows of level L, columns in [c0, c0 + mc)
+    for (int64_t t = threadIdx.x; t < (int64_t)L.size * ld; t += blockDim.x) dst[t] = F(0);
     __syncthreads();
     for (int i = threadIdx.x; i < L.size; i += blockDim.x) {
         int64_t r = L.start + i;
@@ -621,13 +624,29 @@ __device__ void extract_block(const Level& L, int64_t c0, int mc, F* dst, const 
             int64_t idx = base + (int64_t)t * SELL_C + lane;
             if (pad[idx]) continue;
             int64_t cc = col[idx];
-            if (cc >= c0 && cc < c0 + mc) dst[(int64_t)i * mc + (cc - c0)] = (F)val[idx];
+            if (cc >= c0 && cc < c0 + mc) dst[(int64_t)i * ld + (cc - c0)] = (F)val[idx];
         }
     }
     __syncthreads();
 }
 
-__global__ void k_bt_factor(const Sub* __restrict__ subs, const Level* __restrict__ levels,
+__device__ __forceinline__ int ld4(int m) { return (m + 3) / 4 * 4; }
+
+// W (m_l rows, stride r4(m_l)) -= C W_n C^T with C = S_{l,n} (the coupling of
+// level l to the already-eliminated neighbour n).
+__device__ void schur_update(const Level& L, const Level& N, double* W, const double* Wn, double* tC, double* tT,
+                             const int64_t* slice_ptr, const int32_t* col, const uint8_t* pad,
+                             const double* sval) {
+    extract_block(L, N.start, N.size, tC, N.size, slice_ptr, col, pad, sval);              // C
+    cta_gemm(tT, N.size, tC, N.size, Wn, ld4(N.size), L.size, N.size, N.size, false, false);  // C W_n
+    __syncthreads();
+    cta_gemm(W, ld4(L.size), tT, N.size, tC, N.size, L.size, N.size, L.size, true, true);    // -= (C W_n) C^T
+    __syncthreads();
+}
+
+// mid == 0: grid (n_sub, 2), blockIdx.y = 0 the top chain, 1 the bottom chain.
+// mid == 1: grid n_sub, the middle level (after both chains).
+__global__ void k_bt_factor(int mid, const Sub* __restrict__ subs, const Level* __restrict__ levels,
                             const int64_t* __restrict__ slice_ptr, const int32_t* __restrict__ col,
                             const uint8_t* __restrict__ pad, const double* __restrict__ sval, double* fac,
                             double* tmp_all, int64_t tmp_stride, int* perm_all, int max_m, int* status) {
@@ -635,24 +654,39 @@ __global__ void k_bt_factor(const Sub* __restrict__ subs, const Level* __restric
     double* fcol = reinterpret_cast<double*>(smem_raw);
     double* rv = fcol + max_m;
     int* ri = reinterpret_cast<int*>(rv + blockDim.x);
-    const int s = blockIdx.x;
+    const int s = blockIdx.x, chain = mid ? 0 : blockIdx.y;
     const Sub S = subs[s];
-    double* tE = tmp_all + (int64_t)s * tmp_stride;
-    double* tT = tE + (int64_t)max_m * max_m;
-    int* perm = perm_all + (int64_t)s * max_m;
-    for (int l = 0; l < S.nlev; ++l) {
+    if (S.nlev == 0) return;
+    double* tC = tmp_all + ((int64_t)s * 2 + chain) * tmp_stride;
+    double* tT = tC + (int64_t)max_m * max_m;
+    int* perm = perm_all + ((int64_t)s * 2 + chain) * max_m;
+    const int k = S.kmid;
+    if (mid) {
+        const Level L = levels[S.lev0 + k];
+        double* W = fac + L.offW;
+        extract_block(L, L.start, L.size, W, ld4(L.size), slice_ptr, col, pad, sval);
+        if (k > 0) {
+            const Level N = levels[S.lev0 + k - 1];
+            schur_update(L, N, W, fac + N.offW, tC, tT, slice_ptr, col, pad, sval);
+        }
+        if (k + 1 < S.nlev) {
+            const Level N = levels[S.lev0 + k + 1];
+            schur_update(L, N, W, fac + N.offW, tC, tT, slice_ptr, col, pad, sval);
+        }
+        if (!cta_gauss_jordan(W, L.size, ld4(L.size), perm, fcol, rv, ri) && threadIdx.x == 0) atomicExch(status, 1);
+        return;
+    }
+    const int n = chain == 0 ? k : S.nlev - 1 - k;
+    for (int q = 0; q < n; ++q) {
+        const int l = chain == 0 ? q : S.nlev - 1 - q;
         const Level L = levels[S.lev0 + l];
         double* W = fac + L.offW;
-        extract_block(L, L.start, L.size, W, slice_ptr, col, pad, sval);
-        if (l > 0) {
-            const Level Lp = levels[S.lev0 + l - 1];
-            extract_block(L, Lp.start, Lp.size, tE, slice_ptr, col, pad, sval);          // E_l
-            cta_gemm(tT, tE, fac + Lp.offW, L.size, Lp.size, Lp.size, false, false);   // E_l W_{l-1}
-            __syncthreads();
-            cta_gemm(W, tT, tE, L.size, Lp.size, L.size, true, true);                   // S_l
-            __syncthreads();
+        extract_block(L, L.start, L.size, W, ld4(L.size), slice_ptr, col, pad, sval);
+        if (q > 0) {
+            const Level N = levels[S.lev0 + (chain == 0 ? l - 1 : l + 1)];
+            schur_update(L, N, W, fac + N.offW, tC, tT, slice_ptr, col, pad, sval);
         }
-        if (!cta_gauss_jordan(W, L.size, perm, fcol, rv, ri)) {
+        if (!cta_gauss_jordan(W, L.size, ld4(L.size), perm, fcol, rv, ri)) {
             if (threadIdx.x == 0) atomicExch(status, 1);
             return;
         }
@@ -827,20 +861,24 @@ static void factor64(thm_sys* s) {
     const thm_mesh* m = s->m;
     cudaStream_t st = s->st;
     s->fac64.alloc(m->fac_elems);
+    s->fac64.zero(st);
     DArr<double> tmp;
     const int64_t stride = 2 * (int64_t)m->max_m * m->max_m;
-    tmp.alloc((size_t)stride * m->n_sub);
+    tmp.alloc((size_t)stride * m->n_sub * 2);
     DArr<int> perm, status;
-    perm.alloc((size_t)m->max_m * m->n_sub);
+    perm.alloc((size_t)m->max_m * m->n_sub * 2);
     status.alloc(1);
     status.zero(st);
     const int threads = 512;
     size_t smem = (size_t)m->max_m * sizeof(double) + threads * (sizeof(double) + sizeof(int));
     if (smem > 48 * 1024)
         THM_CUDA(cudaFuncSetAttribute(k_bt_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    THM_LAUNCH(THM_K_SETUP, st, k_bt_factor<<<m->n_sub, threads, smem, st>>>(m->d_subs.p, m->d_levels.p, m->d_slice_ptr.p, m->d_sell_col.p,
-                                                m->d_sell_pad.p, s->sval64.p, s->fac64.p, tmp.p, stride, perm.p,
-                                                m->max_m, status.p));
+    THM_LAUNCH(THM_K_SETUP, st, k_bt_factor<<<dim3(m->n_sub, 2), threads, smem, st>>>(
+        0, m->d_subs.p, m->d_levels.p, m->d_slice_ptr.p, m->d_sell_col.p, m->d_sell_pad.p, s->sval64.p, s->fac64.p,
+        tmp.p, stride, perm.p, m->max_m, status.p));
+    THM_LAUNCH(THM_K_SETUP, st, k_bt_factor<<<m->n_sub, threads, smem, st>>>(
+        1, m->d_subs.p, m->d_levels.p, m->d_slice_ptr.p, m->d_sell_col.p, m->d_sell_pad.p, s->sval64.p, s->fac64.p,
+        tmp.p, stride, perm.p, m->max_m, status.p));
     THM_CUDA(cudaGetLastError());
     std::vector<int> hs;
     status.download(hs, st);

@@ -1,0 +1,461 @@
+// x = P_i^{-1} r for every subdomain at once (the block preconditioner of
+// Eq. 7: the same real P_i^{-1} applied to the real and the imaginary part).
+//
+// P_i (for order 2 its edge Schur complement after the per-cell bubble
+// condensation) is block tridiagonal over the BFS levels l = 0..L-1 of the
+// subdomain's DOF graph, with diagonal blocks D_l and couplings
+// E_l = P_{l,l-1}, F_l = P_{l,l+1} = E_{l+1}^T.  It is factored from both
+// ends towards a middle level k (a "twisted" block LU):
+//   top    (l < k):  S_0 = D_0,      S_l = D_l - E_l S_{l-1}^{-1} F_{l-1}
+//   bottom (l > k):  S_{L-1} = D_{L-1}, S_l = D_l - F_l S_{l+1}^{-1} E_{l+1}
+//   middle:          S_k = D_k - E_k S_{k-1}^{-1} F_{k-1} - F_k S_{k+1}^{-1} E_{k+1}
+// and only the dense W_l = S_l^{-1} are stored (row stride r4(m_l), symmetric).
+// The solve runs the two chains concurrently on the two CTAs of a cluster:
+//   rank 0, l = 0..k-1:    z_l = W_l (r_l - E_l z_{l-1})
+//   rank 1, l = L-1..k+1:  z_l = W_l (r_l - F_l z_{l+1})
+//   middle, both ranks:    x_k = W_k (r_k - E_k z_{k-1} - F_k z_{k+1})
+//                          (each rank forms its own coupling term and half of
+//                           the product; the halves meet through DSMEM)
+//   rank 0, l = k-1..0:    x_l = z_l - W_l F_l x_{l+1}
+//   rank 1, l = k+1..L-1:  x_l = z_l - W_l E_l x_{l-1}
+// so each SM streams half of the factor and the dependent chain is half as
+// long as a one-sided sweep.
+//
+// Per CTA, one producer warp streams the tiles (the coupling CSR block of a
+// step, then row tiles of W_l) with 1-D TMA bulk copies into a ring of
+// shared-memory slots (full/empty mbarriers); 12 consumer warps hold the
+// CTA's half of the subdomain vector in shared memory and run the block
+// GEMVs, both vector components at once (each W element feeds two FMAs).
+// Every wait is bounded: on expiry the CTA raises *err, stops issuing, lets
+// its copies in flight land and finishes its (then meaningless) control flow
+// so that no barrier is left waiting.
+#pragma once
+
+#include <cooperative_groups.h>
+
+#include "kernels.cuh"
+
+namespace thm {
+
+constexpr int BT_NT = 384;                  // consumer threads
+constexpr int BT_NW = BT_NT / 32;           // consumer warps
+constexpr int BT_THREADS = BT_NT + 32;      // + one producer warp
+constexpr int BT_MAXG = 8;                  // row groups of a block GEMV
+constexpr int BT_QMAX = 2;                  // output quads per thread: m_l <= 4 * BT_QMAX * BT_NT
+constexpr int BT_MAX_M = 4 * BT_QMAX * BT_NT;
+
+__host__ __device__ constexpr int bt_r4(int v) { return (v + 3) / 4 * 4; }
+__host__ __device__ constexpr size_t bt_r16(size_t v) { return (v + 15) / 16 * 16; }
+
+// One step of a rank's chain: level l, coupling block (0 none, 1 E_l to
+// level l-1, 2 F_l to level l+1), rows [ra, rb) of W_l that this rank
+// streams, and the kind (0 forward, 1 middle, 2 backward).
+struct BtStep {
+    int l, cpl, ra, rb, kind;
+};
+
+__device__ __forceinline__ int bt_nsteps(int rank, int L, int k) { return 2 * (rank == 0 ? k : L - 1 - k) + 1; }
+
+__device__ __forceinline__ BtStep bt_step(int rank, int L, int k, int i, const Level* lv) {
+    BtStep s;
+    const int nf = rank == 0 ? k : L - 1 - k;
+    if (i < nf) {
+        s.kind = 0;
+        s.l = rank == 0 ? i : L - 1 - i;
+        s.cpl = i == 0 ? 0 : (rank == 0 ? 1 : 2);
+    } else if (i == nf) {
+        s.kind = 1;
+        s.l = k;
+        s.cpl = nf == 0 ? 0 : (rank == 0 ? 1 : 2);
+    } else {
+        s.kind = 2;
+        const int d = i - nf;
+        s.l = rank == 0 ? k - d : k + d;
+        s.cpl = rank == 0 ? 2 : 1;
+    }
+    const int m = lv[s.l].size;
+    if (s.kind == 1) {
+        const int h = m / 2;
+        s.ra = rank == 0 ? 0 : h;
+        s.rb = rank == 0 ? h : m;
+    } else {
+        s.ra = 0;
+        s.rb = m;
+    }
+    return s;
+}
+
+// ---- cluster-scope mbarrier helpers ---------------------------------------
+__device__ __forceinline__ unsigned mapa_u32(const void* p, unsigned rank) {
+    unsigned r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;\n" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void mbar_arrive_local(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_remote(unsigned cluster_addr) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];\n" ::"r"(cluster_addr) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, unsigned parity) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+__device__ __forceinline__ bool mbar_try_cluster(uint64_t* bar, unsigned parity) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// Bounded wait that gives up at once when the CTA has already aborted.
+template <bool CLUSTER>
+__device__ __forceinline__ bool bt_wait(uint64_t* bar, unsigned parity, volatile int* abort, int* err) {
+    for (int it = 0; it < (1 << 22); ++it) {
+        if (CLUSTER ? mbar_try_cluster(bar, parity) : mbar_try(bar, parity)) return true;
+        if (*abort) return false;
+    }
+    *abort = 1;
+    atomicExch(err, 1);
+    return false;
+}
+
+__device__ __forceinline__ void bt_bar_consumers() { asm volatile("bar.sync 1, %0;\n" ::"n"(BT_NT) : "memory"); }
+
+template <class F, class R>
+__device__ __forceinline__ void bt_load4(const F* p, R* w);
+template <>
+__device__ __forceinline__ void bt_load4<float, float>(const float* p, float* w) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+}
+template <>
+__device__ __forceinline__ void bt_load4<float, double>(const float* p, double* w) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+}
+template <>
+__device__ __forceinline__ void bt_load4<double, double>(const double* p, double* w) {
+    const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+    w[0] = a.x; w[1] = a.y; w[2] = b.x; w[3] = b.y;
+}
+template <>
+__device__ __forceinline__ void bt_load4<double, float>(const double* p, float* w) {
+    const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+    w[0] = (float)a.x; w[1] = (float)a.y; w[2] = (float)b.x; w[3] = (float)b.y;
+}
+
+// Shared-memory layout of k_bt_solve (host and device agree through this).
+struct BtLayout {
+    size_t bars, lv, slots, vec, su, tx, rx, ry, part, total;
+};
+template <class V>
+__host__ __device__ inline BtLayout bt_layout(int ns, int slot_bytes, int max_lev, int nvec, int max_m) {
+    BtLayout L;
+    size_t o = 0;
+    L.bars = o; o += bt_r16((size_t)(2 * ns + 2) * 8);
+    L.lv = o; o += bt_r16((size_t)max_lev * sizeof(Level));
+    L.slots = o; o += (size_t)ns * slot_bytes;
+    const size_t vm = bt_r16((size_t)bt_r4(max_m) * sizeof(V));
+    L.vec = o; o += bt_r16((size_t)nvec * sizeof(V));
+    L.su = o; o += vm;
+    L.tx = o; o += vm;
+    L.rx = o; o += vm;
+    L.ry = o; o += vm;
+    const int np = 4 * BT_NT > bt_r4(max_m) ? 4 * BT_NT : bt_r4(max_m);
+    L.part = o; o += bt_r16((size_t)np * sizeof(V));
+    L.total = o;
+    return L;
+}
+
+template <class V, class F>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(BT_THREADS, 1)
+k_bt_solve(const Sub* __restrict__ subs, const Level* __restrict__ levels, const F* __restrict__ fac,
+           const int32_t* __restrict__ cptr, const int32_t* __restrict__ ccol, const F* __restrict__ cval,
+           int64_t n_loc, int condensed, const int32_t* __restrict__ ai, const F* __restrict__ av,
+           const int32_t* __restrict__ ci, const F* __restrict__ cv, const int32_t* __restrict__ ei,
+           const F* __restrict__ ev, int R, int ns, int slot_bytes, int max_lev, int nvec, int max_m,
+           int* __restrict__ err, const V* __restrict__ x, V* __restrict__ y) {
+    using Rt = typename VT<V>::R;
+    namespace cg = cooperative_groups;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ int s_abort;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    const int peer = rank ^ 1;
+    const BtLayout lay = bt_layout<V>(ns, slot_bytes, max_lev, nvec, max_m);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + lay.bars);
+    uint64_t* empty = full + ns;
+    uint64_t* xbar = empty + ns;          // [0]: coupling terms of the middle level, [1]: halves of x_k
+    Level* lv = reinterpret_cast<Level*>(smem + lay.lv);
+    unsigned char* slots = smem + lay.slots;
+    V* vec = reinterpret_cast<V*>(smem + lay.vec);
+    V* su = reinterpret_cast<V*>(smem + lay.su);
+    V* tx = reinterpret_cast<V*>(smem + lay.tx);
+    V* rx = reinterpret_cast<V*>(smem + lay.rx);
+    V* ry = reinterpret_cast<V*>(smem + lay.ry);
+    V* part = reinterpret_cast<V*>(smem + lay.part);
+    V* prx = cluster.map_shared_rank(rx, peer);
+    V* pry = cluster.map_shared_rank(ry, peer);
+    volatile int* abort = &s_abort;
+
+    const Sub S = subs[blockIdx.y];
+    const int L = S.nlev, k = S.kmid;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int l = tid; l < L; l += blockDim.x) lv[l] = levels[S.lev0 + l];
+    if (tid == 0) {
+        s_abort = 0;
+        for (int q = 0; q < ns; ++q) {
+            mbar_init(&full[q], 1);
+            mbar_init(&empty[q], BT_NW);
+        }
+        mbar_init(&xbar[0], BT_NW);
+        mbar_init(&xbar[1], BT_NW);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    cluster.sync();                       // the peer's barriers exist before any remote arrive
+
+    const int nst = L > 0 ? bt_nsteps(rank, L, k) : 0;
+    if (warp == BT_NW) {
+        // ---------------- producer warp: lane 0 streams the tiles ----------------
+        if (lane == 0 && nst > 0) {
+            int p = 0;
+            bool ok = true;
+            for (int si = 0; si < nst && ok; ++si) {
+                const BtStep st = bt_step(rank, L, k, si, lv);
+                const Level& Lv = lv[st.l];
+                const int m = Lv.size, ldm = bt_r4(m);
+                const int nt = (st.cpl ? 1 : 0) + (st.rb - st.ra + R - 1) / R;
+                for (int u = 0; u < nt && ok; ++u, ++p) {
+                    const int q = p % ns, n = p / ns;
+                    if (n > 0 && !bt_wait<false>(&empty[q], (unsigned)((n - 1) & 1), abort, err)) { ok = false; break; }
+                    unsigned char* dst = slots + (size_t)q * slot_bytes;
+                    fence_proxy_async();
+                    if (st.cpl && u == 0) {
+                        const bool e = st.cpl == 1;
+                        const int64_t po = e ? Lv.eptr : Lv.fptr, qo = e ? Lv.eoff : Lv.foff;
+                        const int nz = e ? Lv.enz : Lv.fnz;
+                        const unsigned pb = (unsigned)bt_r16((size_t)(m + 1) * 4);
+                        const unsigned cb = (unsigned)bt_r16((size_t)nz * 4);
+                        const unsigned vb = (unsigned)bt_r16((size_t)nz * sizeof(F));
+                        mbar_expect_tx(&full[q], pb + cb + vb);
+                        tma_load_1d(dst, cptr + po, pb, &full[q]);
+                        if (cb) tma_load_1d(dst + pb, ccol + qo, cb, &full[q]);
+                        if (vb) tma_load_1d(dst + pb + cb, cval + qo, vb, &full[q]);
+                    } else {
+                        const int r0 = st.ra + (u - (st.cpl ? 1 : 0)) * R;
+                        const int nr = min(R, st.rb - r0);
+                        const unsigned wb = (unsigned)((size_t)nr * ldm * sizeof(F));
+                        mbar_expect_tx(&full[q], wb);
+                        tma_load_1d(dst, fac + Lv.offW + (int64_t)r0 * ldm, wb, &full[q]);
+                    }
+                }
+            }
+            // let every issued copy land before the CTA may leave
+            for (int q = 0; q < ns && q < p; ++q) {
+                const int last = q + ((p - 1 - q) / ns) * ns;      // last tile issued into slot q
+                for (int it = 0; it < (1 << 22); ++it)
+                    if (mbar_try(&full[q], (unsigned)((last / ns) & 1))) break;
+            }
+        }
+        __syncwarp();
+    } else if (nst > 0) {
+        // ---------------- consumer warps ----------------
+        const int vbase = rank == 0 ? lv[0].start : lv[k].start;
+        const int vend = rank == 0 ? lv[k].start + lv[k].size : lv[L - 1].start + lv[L - 1].size;
+        // (a) load r for this rank's levels; order 2: r_E <- r_E - G r_I
+        for (int e = vbase + tid; e < vend; e += BT_NT) {
+            V a = x[e];
+            Rt ar = a.x, aim = a.y;
+            if (condensed) {
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const Rt g = (Rt)av[u * n_loc + e];
+                    const V xb = x[ai[u * n_loc + e]];
+                    ar -= g * xb.x;
+                    aim -= g * xb.y;
+                }
+            }
+            vec[e - vbase] = mk<V>(ar, aim);
+        }
+        bt_bar_consumers();
+        int t = 0;
+        for (int si = 0; si < nst; ++si) {
+            const BtStep st = bt_step(rank, L, k, si, lv);
+            const int m = lv[st.l].size, o = lv[st.l].start - vbase, ldm = bt_r4(m);
+            // (b1) coupling term of the step
+            if (st.cpl) {
+                const int q = t % ns;
+                bt_wait<false>(&full[q], (unsigned)((t / ns) & 1), abort, err);
+                const unsigned char* buf = slots + (size_t)q * slot_bytes;
+                const int nb = st.cpl == 1 ? st.l - 1 : st.l + 1;
+                const int ob = lv[nb].start - vbase;
+                const int nz = st.cpl == 1 ? lv[st.l].enz : lv[st.l].fnz;
+                const int* P = reinterpret_cast<const int*>(buf);
+                const int* C = P + bt_r4(m + 1);
+                const F* Cv = reinterpret_cast<const F*>(C + bt_r4(nz));
+                for (int i = tid; i < m; i += BT_NT) {
+                    Rt ar = 0, aim = 0;
+                    for (int pp = P[i]; pp < P[i + 1]; ++pp) {
+                        const Rt f = (Rt)Cv[pp];
+                        const V v = vec[ob + C[pp]];
+                        ar += f * v.x;
+                        aim += f * v.y;
+                    }
+                    if (st.kind == 0) {
+                        const V r = vec[o + i];
+                        su[i] = mk<V>(r.x - ar, r.y - aim);
+                    } else if (st.kind == 1) {
+                        tx[i] = mk<V>(ar, aim);
+                        prx[i] = mk<V>(ar, aim);
+                    } else {
+                        su[i] = mk<V>(ar, aim);
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive_local(&empty[q]);
+                ++t;
+            } else {
+                for (int i = tid; i < m; i += BT_NT) {
+                    if (st.kind == 0) {
+                        su[i] = vec[o + i];
+                    } else {
+                        tx[i] = mk<V>(0, 0);
+                        prx[i] = mk<V>(0, 0);
+                    }
+                }
+            }
+            if (st.kind == 1) {
+                // the peer's coupling term of the middle level arrives in rx
+                __syncwarp();
+                if (lane == 0) mbar_arrive_remote(mapa_u32(&xbar[0], (unsigned)peer));
+                bt_wait<true>(&xbar[0], 0u, abort, err);
+                for (int i = tid; i < m; i += BT_NT) {
+                    const V r = vec[o + i], a = tx[i], b = rx[i];
+                    su[i] = mk<V>(r.x - a.x - b.x, r.y - a.y - b.y);
+                }
+            }
+            bt_bar_consumers();
+            // (b2) y = W_l^T s over the rows [ra, rb) this rank streams
+            const int nq = ldm / 4;
+            const int tq = min(nq, BT_NT);
+            const int ng = min(BT_MAXG, BT_NT / tq);
+            const int g = tid / tq, i0 = tid % tq;
+            Rt acc[BT_QMAX][4][2];
+#pragma unroll
+            for (int u = 0; u < BT_QMAX; ++u)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[u][c][0] = acc[u][c][1] = 0;
+            for (int r0 = st.ra; r0 < st.rb; r0 += R) {
+                const int q = t % ns;
+                bt_wait<false>(&full[q], (unsigned)((t / ns) & 1), abort, err);
+                const F* Wt = reinterpret_cast<const F*>(slots + (size_t)q * slot_bytes);
+                const int nr = min(R, st.rb - r0);
+                if (g < ng) {
+                    for (int jj = g; jj < nr; jj += ng) {
+                        const V sj = su[r0 + jj];
+                        const F* wr = Wt + (size_t)jj * ldm;
+#pragma unroll
+                        for (int u = 0; u < BT_QMAX; ++u) {
+                            const int qq = i0 + u * tq;
+                            if (qq < nq) {
+                                Rt w[4];
+                                bt_load4<F, Rt>(wr + 4 * qq, w);
+#pragma unroll
+                                for (int c = 0; c < 4; ++c) {
+                                    acc[u][c][0] += w[c] * sj.x;
+                                    acc[u][c][1] += w[c] * sj.y;
+                                }
+                            }
+                        }
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive_local(&empty[q]);
+                ++t;
+            }
+            // (b3) combine the row groups
+            if (g < ng) {
+#pragma unroll
+                for (int u = 0; u < BT_QMAX; ++u) {
+                    const int qq = i0 + u * tq;
+                    if (qq < nq)
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) part[g * ldm + 4 * qq + c] = mk<V>(acc[u][c][0], acc[u][c][1]);
+                }
+            }
+            bt_bar_consumers();
+            for (int i = tid; i < m; i += BT_NT) {
+                Rt yr = 0, yi = 0;
+                for (int gg = 0; gg < ng; ++gg) {
+                    const V pv = part[gg * ldm + i];
+                    yr += pv.x;
+                    yi += pv.y;
+                }
+                if (st.kind == 0) {
+                    vec[o + i] = mk<V>(yr, yi);
+                } else if (st.kind == 1) {
+                    tx[i] = mk<V>(yr, yi);
+                    pry[i] = mk<V>(yr, yi);
+                } else {
+                    const V z = vec[o + i];
+                    vec[o + i] = mk<V>(z.x - yr, z.y - yi);
+                }
+            }
+            if (st.kind == 1) {
+                // x_k = own half + the peer's half
+                __syncwarp();
+                if (lane == 0) mbar_arrive_remote(mapa_u32(&xbar[1], (unsigned)peer));
+                bt_wait<true>(&xbar[1], 0u, abort, err);
+                for (int i = tid; i < m; i += BT_NT) {
+                    const V a = tx[i], b = ry[i];
+                    vec[o + i] = mk<V>(a.x + b.x, a.y + b.y);
+                }
+            }
+            bt_bar_consumers();
+        }
+        // write back: rank 0 levels 0..k, rank 1 levels k+1..L-1
+        const int w0 = rank == 0 ? vbase : lv[k].start + lv[k].size;
+        for (int e = w0 + tid; e < vend; e += BT_NT) y[e] = vec[e - vbase];
+    }
+    // (c) order 2: x_I = D^{-1} r_I - G^T x_E, once both ranks' edge values are in y
+    cluster.sync();
+    if (condensed) {
+        const int64_t b0 = S.off + S.ne, nbub = S.n - S.ne;
+        const int64_t half = (nbub + 1) / 2;
+        const int64_t lo = b0 + (rank == 0 ? 0 : half), hi = b0 + (rank == 0 ? half : nbub);
+        for (int64_t b = lo + tid; b < hi; b += blockDim.x) {
+            Rt ar = 0, aim = 0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const Rt c = (Rt)cv[j * n_loc + b];
+                const V xb = x[ci[j * n_loc + b]];
+                ar += c * xb.x;
+                aim += c * xb.y;
+            }
+#pragma unroll
+            for (int a = 0; a < 8; ++a) {
+                const int64_t e = (int64_t)ei[a * n_loc + b];
+                if (e >= S.off && e < S.off + S.ne) {
+                    const Rt c = (Rt)ev[a * n_loc + b];
+                    const V xe = y[e];
+                    ar += c * xe.x;
+                    aim += c * xe.y;
+                }
+            }
+            y[b] = mk<V>(ar, aim);
+        }
+    }
+}
+
+}  // namespace thm

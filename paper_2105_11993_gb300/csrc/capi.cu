@@ -260,7 +260,7 @@ int thm_alg_bytes(const thm_sys* s, int mode, int cls, double* bytes) {
             for (const auto& S : m->subs) {
                 for (int l = 0; l < S.nlev; ++l) {
                     const Level& L = m->levels[S.lev0 + l];
-                    w += (double)L.size * L.size * (l + 1 < S.nlev ? 2 : 1);
+                    w += (double)L.size * L.size * (l == S.kmid ? 1 : 2);   // the middle level once
                     cpl += L.enz + L.fnz;
                 }
                 ne += (double)S.ne;

@@ -90,7 +90,7 @@ struct Level {
     int32_t size;     // m_l
     int32_t prev;     // m_{l-1} (0 for the first level of a subdomain)
     int32_t next;     // m_{l+1} (0 for the last)
-    int64_t offW;     // m_l x m_l  inverse of the Schur block S_l (16-byte aligned)
+    int64_t offW;     // W_l = S_l^{-1}: m_l rows of stride r4(m_l) (16-byte aligned)
     // coupling blocks of S to level l-1 (E) and l+1 (F): m_l+1 row pointers
     // (0-based, at cpl_ptr[eptr..]) and nz (column local to the neighbour
     // level, value) entries at cpl_col/cpl_val[eoff..]; offsets 16-byte aligned
@@ -104,6 +104,8 @@ struct Sub {
     int64_t ne;       // free edge DOFs (rows off .. off+ne-1); cell bubbles follow
     int32_t lev0;     // first level
     int32_t nlev;
+    int32_t kmid;     // middle level of the twisted factorisation (0 <= kmid < nlev)
+    int32_t pad_;
 };
 
 // A contiguous piece of one segment, used for deterministic segmented reductions.
@@ -161,6 +163,8 @@ struct thm_mesh {
     // levels of the block-tridiagonal factorisation
     std::vector<thm::Level> levels;
     int max_m = 0;
+    int max_lev = 0;                                // most levels of a subdomain
+    int64_t bt_nvec = 0;                            // longest half-chain vector of the twisted solve
     int64_t fac_elems = 0;
     // level couplings of S as compact CSR lists (columns local to the
     // neighbouring level; slot = position of the value in the SELL arrays)

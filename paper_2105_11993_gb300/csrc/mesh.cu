@@ -379,18 +379,43 @@ void build_mesh(thm_mesh* m) {
     m->row_cell.swap(row_cell_v);
     m->row_k.swap(row_k_v);
 
-    // ---- level offsets into the factor storage
+    // ---- level offsets into the factor storage (rows padded to a multiple
+    //      of 4 entries, so every row and every block is 16-byte aligned) and
+    //      the middle level of the twisted factorisation: the level that
+    //      balances the factor bytes (plus a per-level latency allowance) of
+    //      the two chains
     m->max_m = 0;
+    m->max_lev = 0;
+    m->bt_nvec = 0;
     int64_t fo = 0;
     for (int s = 0; s < ns; ++s) {
         auto& S = m->subs[s];
+        m->max_lev = std::max(m->max_lev, S.nlev);
+        std::vector<double> cost(S.nlev);
         for (int l = 0; l < S.nlev; ++l) {
             Level& L = m->levels[S.lev0 + l];
             L.prev = l > 0 ? m->levels[S.lev0 + l - 1].size : 0;
             L.next = l + 1 < S.nlev ? m->levels[S.lev0 + l + 1].size : 0;
             m->max_m = std::max(m->max_m, L.size);
             L.offW = fo;
-            fo += ((int64_t)L.size * L.size + 3) / 4 * 4;     // keep every block 16-byte aligned
+            fo += (int64_t)L.size * (((int64_t)L.size + 3) / 4 * 4);
+            cost[l] = (double)L.size * L.size + 16384.0;
+        }
+        S.kmid = 0;
+        if (S.nlev > 0) {
+            double tot = 0, below = 0, best = 1e300;
+            for (double c : cost) tot += c;
+            for (int k = 0; k < S.nlev; ++k) {
+                const double above = tot - below - cost[k];
+                const double w = std::max(below, above);
+                if (w < best) { best = w; S.kmid = k; }
+                below += cost[k];
+            }
+            const Level& Lk = m->levels[S.lev0 + S.kmid];
+            const Level& L0 = m->levels[S.lev0];
+            const Level& Le = m->levels[S.lev0 + S.nlev - 1];
+            m->bt_nvec = std::max<int64_t>(m->bt_nvec, (int64_t)Lk.start + Lk.size - L0.start);
+            m->bt_nvec = std::max<int64_t>(m->bt_nvec, (int64_t)Le.start + Le.size - Lk.start);
         }
     }
     m->fac_elems = fo + 4;

@@ -8,6 +8,7 @@
 #include <cstdlib>
 #include <functional>
 
+#include "btsolve.cuh"
 #include "kernels.cuh"
 #include "solver.cuh"
 
@@ -559,47 +560,41 @@ static void apply_T(const thm_sys* s, const F* val, const F* bg, const F* bs, in
                                                                 use_bs, bvg, bvs, x, y));
 }
 
+// Twisted block-tridiagonal solve, one 2-CTA cluster per subdomain.  The
+// ring of shared-memory slots takes what the rest of the layout leaves: W
+// tiles of about THM_BT_TILE_BYTES (default 16 KB) each, 2..16 slots.
 template <class V, class F>
 static void apply_Pinv(const thm_sys* s, const F* fac, const F* cval, const int32_t* ai, const F* av,
                        const int32_t* ci, const F* cv, const int32_t* ei, const F* ev, const V* x, V* y) {
     const thm_mesh* m = s->m;
-    using R = typename VT<V>::R;
-    auto r4 = [](int64_t v) { return (int64_t)((v + 3) / 4 * 4); };
-    int max_lev = 0;
-    for (const auto& S : m->subs) max_lev = std::max(max_lev, S.nlev);
-    THM_REQUIRE(m->max_m <= BT_MAXO * 512 / BT_NG, "level block larger than the block-solve kernel supports");
-    const size_t tail = (size_t)(r4(m->max_ne) + (1 + BT_NG) * r4(m->max_m)) * sizeof(R) +
-                        4 * (size_t)(max_lev + 1) * sizeof(int) + 5 * (size_t)max_lev * sizeof(long long) + 16;
-    const size_t csr = (size_t)r4(m->max_m + 1) * 4 + (size_t)r4(m->max_cnz) * (4 + sizeof(F)) + 16;
-    const size_t cap = 220 * 1024;
-    THM_REQUIRE(tail + 3 * csr <= cap, "subdomain too large for the shared-memory block solve");
-    // tile height: the largest multiple of 4 rows (<= 64) whose ring of 3..6 slots fits
-    // ring depth: as many slots as requested (default 8) with the tallest tiles
-    // that fit; fewer slots only when even 16-row tiles do not fit
-    static const int want = getenv("THM_BT_SLOTS") ? std::max(3, std::min(8, atoi(getenv("THM_BT_SLOTS")))) : 8;
-    int rows = 0, nslot = 0;
-    size_t slot = 0;
-    for (int ns = want; ns >= 3 && rows == 0; --ns) {
-        const size_t per = (cap - tail - 128) / ns;
-        for (int r = (int)r4(m->max_m); r >= 4; r -= 4) {
-            size_t sb = std::max(csr, (size_t)r * m->max_m * sizeof(F) + 16);
-            sb = (sb + 15) / 16 * 16;
-            if (sb <= per && (r >= 16 || ns == 3)) { rows = r; nslot = ns; slot = sb; break; }
-        }
-    }
-    THM_REQUIRE(rows >= 4, "level block too wide for the shared-memory block solve");
-    const size_t smem = (size_t)nslot * slot + tail + ((nslot * 8 + 15) / 16) * 16;
+    THM_REQUIRE(m->max_m <= BT_MAX_M, "level block larger than the block-solve kernel supports (" +
+                                          std::to_string(m->max_m) + " > " + std::to_string(BT_MAX_M) + ")");
+    static const size_t target = getenv("THM_BT_TILE_BYTES") ? (size_t)std::max(1024, atoi(getenv("THM_BT_TILE_BYTES")))
+                                                              : (size_t)16384;
+    const size_t cap = 227 * 1024 - 256;
+    const size_t row_bytes = (size_t)bt_r4(m->max_m) * sizeof(F);
+    const size_t cpl_bytes = bt_r16((size_t)(m->max_m + 1) * 4) + bt_r16((size_t)m->max_cnz * 4) +
+                             bt_r16((size_t)m->max_cnz * sizeof(F));
+    const int rows = (int)std::max<size_t>(1, target / row_bytes);
+    const size_t slot = bt_r16(std::max(cpl_bytes, (size_t)rows * row_bytes));
+    THM_REQUIRE(slot < (size_t)INT32_MAX && m->bt_nvec < INT32_MAX, "block-solve tile too large");
+    const size_t fixed = bt_layout<V>(0, 0, m->max_lev, (int)m->bt_nvec, m->max_m).total;
+    int ns = 0;
+    for (int q = 16; q >= 2 && ns == 0; --q)
+        if (bt_layout<V>(q, (int)slot, m->max_lev, (int)m->bt_nvec, m->max_m).total <= cap) ns = q;
+    THM_REQUIRE(ns >= 2, "subdomain too large for the shared-memory block solve (" + std::to_string(fixed) +
+                             " bytes of vectors and level data, " + std::to_string(slot) + "-byte tiles)");
+    const size_t smem = bt_layout<V>(ns, (int)slot, m->max_lev, (int)m->bt_nvec, m->max_m).total;
     static size_t attr = 0;
     if (smem > 48 * 1024 && smem > attr) {
-        THM_CUDA(cudaFuncSetAttribute(k_bt_apply<V, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        THM_CUDA(cudaFuncSetAttribute(k_bt_solve<V, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         attr = smem;
     }
-    dim3 grid(m->n_sub, 2);
     THM_LAUNCH(THM_K_PINV, s->st,
-               k_bt_apply<V, F><<<grid, 512, smem, s->st>>>(m->d_subs.p, m->d_levels.p, fac, m->d_cpl_ptr.p,
-                                                            m->d_cpl_col.p, cval, m->n_loc, m->order == 2 ? 1 : 0,
-                                                            ai, av, ci, cv, ei, ev, rows, nslot, (int)slot,
-                                                            (int)m->max_ne, m->max_m, max_lev, s->dev_err.p, x, y));
+               k_bt_solve<V, F><<<dim3(2, m->n_sub), BT_THREADS, smem, s->st>>>(
+                   m->d_subs.p, m->d_levels.p, fac, m->d_cpl_ptr.p, m->d_cpl_col.p, cval, m->n_loc,
+                   m->order == 2 ? 1 : 0, ai, av, ci, cv, ei, ev, rows, ns, (int)slot, m->max_lev, (int)m->bt_nvec,
+                   m->max_m, s->dev_err.p, x, y));
 }
 
 template <class V>
