@@ -44,7 +44,7 @@ UNIT = "DOF*iter/s"
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--steps", type=int, default=2)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--mode", default="mixed", choices=["mixed", "fp64"])
@@ -244,6 +244,20 @@ def reference_arm(args):
 # --------------------------------------------------------------------------
 # our arm
 # --------------------------------------------------------------------------
+def measured_traffic(kernel, mode):
+    """DRAM bytes (read + write) per launch of `kernel` from the committed ncu
+    summary, or None when the kernel source changed since that capture."""
+    import hashlib
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[kernel]
+        src = open(os.path.join(ROOT, rec["source"]), "rb").read()
+    except (OSError, ValueError, KeyError):
+        return None
+    if hashlib.sha256(src).hexdigest() != rec["source_sha256"] or rec.get("mode") != mode:
+        return None
+    return rec["dram_bytes_per_launch"]
+
+
 def bytes_per_launch(sysg, mode, cls):
     import paper_2105_11993_gb300 as thm
     return thm.algorithmic_bytes(sysg, mode, cls)
@@ -331,9 +345,10 @@ def main():
     achieved = alg_bytes / per_launch_s / 1e9 if n_launch else None
     spmv_n, spmv_ms = prof["spmv"]
     spmv_bytes = thm.algorithmic_bytes(sysg, mode, thm.K_SPMV)
-    roofline = {"kernel": "k_bt_apply (block-preconditioner apply, Eq. 7)", "bound": "hbm",
+    roofline = {"kernel": "k_bt_solve (block-preconditioner apply, Eq. 7)", "bound": "hbm",
                 "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": (achieved / hbm_peak) if achieved else None, "traffic": None,
+                "frac": (achieved / hbm_peak) if achieved else None,
+                "traffic": measured_traffic("k_bt_solve", mode),
                 "peak_source": peak_src, "launches": n_launch, "avg_launch_us": 1e6 * per_launch_s,
                 "alg_bytes_per_launch": alg_bytes,
                 "share_of_step": (pinv_ms / ms) if ms > 0 else None,

@@ -139,9 +139,9 @@ typedef struct thm_solve_opts {
     int    outer_maxit;    /* (<=0: 2000) */
     int    max_refine;     /* iterative-refinement steps (<=0: 6) */
     int    relax;          /* 1: inexact-Krylov relaxation of the subdomain tolerance as the
-                              interface residual falls (clamp(outer_tol/||r_k||, inner_tol,
-                              1e-3)); the refinement on the FP64 residual still decides
-                              convergence.  0: fixed inner_tol */
+                              interface residual falls (clamp(1e-2 * outer_tol/||r_k||,
+                              inner_tol, 1e-6)); the refinement on the FP64 residual still
+                              decides convergence.  0: fixed inner_tol */
 } thm_solve_opts;
 
 typedef struct thm_stats {

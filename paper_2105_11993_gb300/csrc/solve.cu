@@ -337,11 +337,17 @@ struct Krylov {
             THM_CUDA(cudaMallocHost(&h_gring, RING * sizeof(double2)));
             for (auto& e : ring_ev) THM_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         }
+        // the kernels are shared by every Krylov instance of this vector
+        // type (inner and outer solvers): only ever raise their limit
         size_t dots_smem = (size_t)(m + 1) * (KT / 32) * sizeof(double2);
         THM_REQUIRE(dots_smem <= 200 * 1024, "restart length too large");
-        THM_CUDA(cudaFuncSetAttribute(k_chunk_dots<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dots_smem));
-        THM_CUDA(cudaFuncSetAttribute(k_chunk_update<V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)((m + 1) * sizeof(double2))));
+        static size_t dots_attr = 0;
+        if (dots_smem > dots_attr) {
+            THM_CUDA(cudaFuncSetAttribute(k_chunk_dots<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dots_smem));
+            THM_CUDA(cudaFuncSetAttribute(k_chunk_update<V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)((m + 1) * sizeof(double2))));
+            dots_attr = dots_smem;
+        }
         THM_CUDA(cudaDeviceSynchronize());
     }
 
@@ -693,10 +699,14 @@ static void ddm_solve(thm_sys* s, const SolveCfg& c, const double2* src, double2
     auto A = [&](const double2* v, double2* out) {
         SolveCfg cr = c;
         if (c.relax) {
-            // inexact Krylov: the sweep may be as inaccurate as the outer
-            // residual is small (GMRES tolerates matvec errors ~ tol / ||r_k||)
-            double eta = c.outer_tol / std::max(w->outer.last_rel, 1e-300);
-            cr.inner_tol = std::min(1e-3, std::max(c.inner_tol, eta));
+            // inexact Krylov: GMRES tolerates matvec errors of about
+            // tol / ||r_k|| (relative), so the subdomain solves may loosen as
+            // the outer residual falls.  The subdomain residual only bounds
+            // the sweep error up to a constant, hence the safety factor
+            // 1e-2 and the ceiling 1e-6 (looser settings stall the outer
+            // iteration).
+            const double eta = 1e-2 * c.outer_tol / std::max(w->outer.last_rel, 1e-300);
+            cr.inner_tol = std::min(1e-6, std::max(c.inner_tol, eta));
         }
         sweep(s, cr, nullptr, v, w->gtmp.p, w->ytmp.p, rs);
         THM_LAUNCH(THM_K_KRYLOV, st, k_sub<double2><<<nblk(m->n_if), 256, 0, st>>>(m->n_if, v, w->gtmp.p, out));   // (I - A) v

@@ -219,3 +219,20 @@ def test_host_entry_point_matches_device():
     ud, _ = sysg.solve(mode="fp64", rtol=1e-10)
     uh, _ = sysg.solve_host(mode="fp64", rtol=1e-10)
     assert np.linalg.norm(ud.cpu().numpy() - uh) <= 1e-12 * np.linalg.norm(uh)
+
+
+def test_long_outer_cycle_after_inner_reinit():
+    """The dot-product kernels are shared by the inner and the outer Krylov
+    solvers; re-creating the inner solver with a shorter restart must not
+    lower the shared-memory limit the long outer cycles need (an outer cycle
+    of 400 steps needs more than 48 KB)."""
+    import paper_2105_11993_gb300 as thm
+    P = CASES["c0"]()
+    mesh, sysg = make_system(P)
+    sysg.solve(mode="fp64", rtol=1e-8, inner_restart=50)
+    sysg.solve(mode="fp64", rtol=1e-8, inner_restart=60)
+    _, st = sysg.solve(mode="fp64", rtol=1e-30, inner_restart=60, outer_tol=1e-30, outer_maxit=400,
+                       max_refine=1, check=False)
+    from paper_2105_11993_gb300 import _binding as B
+    assert st["status"] in (0, -2), (st["status"], B.load().thm_last_error().decode())
+    assert st["outer_iters"] >= 390
