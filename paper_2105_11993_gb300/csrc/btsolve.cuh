@@ -22,8 +22,10 @@
 // long as a one-sided sweep.
 //
 // Per CTA, one producer warp streams the tiles (the coupling CSR block of a
-// step, then row tiles of W_l) with 1-D TMA bulk copies into a ring of
-// shared-memory slots (full/empty mbarriers); 12 consumer warps hold the
+// step, then row tiles of W_l) with 1-D TMA bulk copies into two rings of
+// shared-memory slots (full/empty mbarriers): large slots for the W tiles,
+// small ones for the coupling blocks, so that a few-KB coupling block does not
+// hold a W-sized slot and the W ring reaches further ahead; 12 consumer warps hold the
 // CTA's half of the subdomain vector in shared memory and run the block
 // GEMVs, both vector components at once (each W element feeds two FMAs).
 // Every wait is bounded: on expiry the CTA raises *err, stops issuing, lets
@@ -43,6 +45,7 @@ constexpr int BT_THREADS = BT_NT + 32;      // + one producer warp
 constexpr int BT_MAXG = 8;                  // row groups of a block GEMV
 constexpr int BT_QMAX = 2;                  // output quads per thread: m_l <= 4 * BT_QMAX * BT_NT
 constexpr int BT_MAX_M = 4 * BT_QMAX * BT_NT;
+constexpr int BT_NC = 4;                    // slots of the coupling ring
 
 __host__ __device__ constexpr int bt_r4(int v) { return (v + 3) / 4 * 4; }
 __host__ __device__ constexpr size_t bt_r16(size_t v) { return (v + 15) / 16 * 16; }
@@ -156,15 +159,17 @@ __device__ __forceinline__ void bt_load4<double, float>(const double* p, float* 
 
 // Shared-memory layout of k_bt_solve (host and device agree through this).
 struct BtLayout {
-    size_t bars, lv, slots, vec, su, tx, rx, ry, part, total;
+    size_t bars, lv, slots, cslots, vec, su, tx, rx, ry, part, total;
 };
 template <class V>
-__host__ __device__ inline BtLayout bt_layout(int ns, int slot_bytes, int max_lev, int nvec, int max_m) {
+__host__ __device__ inline BtLayout bt_layout(int ns, int slot_bytes, int cslot_bytes, int max_lev, int nvec,
+                                              int max_m) {
     BtLayout L;
     size_t o = 0;
-    L.bars = o; o += bt_r16((size_t)(2 * ns + 2) * 8);
+    L.bars = o; o += bt_r16((size_t)(2 * ns + 2 * BT_NC + 2) * 8);
     L.lv = o; o += bt_r16((size_t)max_lev * sizeof(Level));
     L.slots = o; o += (size_t)ns * slot_bytes;
+    L.cslots = o; o += (size_t)BT_NC * cslot_bytes;
     const size_t vm = bt_r16((size_t)bt_r4(max_m) * sizeof(V));
     L.vec = o; o += bt_r16((size_t)nvec * sizeof(V));
     L.su = o; o += vm;
@@ -183,7 +188,7 @@ k_bt_solve(const Sub* __restrict__ subs, const Level* __restrict__ levels, const
            const int32_t* __restrict__ cptr, const int32_t* __restrict__ ccol, const F* __restrict__ cval,
            int64_t n_loc, int condensed, const int32_t* __restrict__ ai, const F* __restrict__ av,
            const int32_t* __restrict__ ci, const F* __restrict__ cv, const int32_t* __restrict__ ei,
-           const F* __restrict__ ev, int R, int ns, int slot_bytes, int max_lev, int nvec, int max_m,
+           const F* __restrict__ ev, int R, int ns, int slot_bytes, int cslot_bytes, int max_lev, int nvec, int max_m,
            int* __restrict__ err, const V* __restrict__ x, V* __restrict__ y) {
     using Rt = typename VT<V>::R;
     namespace cg = cooperative_groups;
@@ -192,12 +197,15 @@ k_bt_solve(const Sub* __restrict__ subs, const Level* __restrict__ levels, const
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
     const int peer = rank ^ 1;
-    const BtLayout lay = bt_layout<V>(ns, slot_bytes, max_lev, nvec, max_m);
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem + lay.bars);
+    const BtLayout lay = bt_layout<V>(ns, slot_bytes, cslot_bytes, max_lev, nvec, max_m);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + lay.bars);   // W ring
     uint64_t* empty = full + ns;
-    uint64_t* xbar = empty + ns;          // [0]: coupling terms of the middle level, [1]: halves of x_k
+    uint64_t* cfull = empty + ns;                                      // coupling ring
+    uint64_t* cempty = cfull + BT_NC;
+    uint64_t* xbar = cempty + BT_NC;      // [0]: coupling terms of the middle level, [1]: halves of x_k
     Level* lv = reinterpret_cast<Level*>(smem + lay.lv);
     unsigned char* slots = smem + lay.slots;
+    unsigned char* cslots = smem + lay.cslots;
     V* vec = reinterpret_cast<V*>(smem + lay.vec);
     V* su = reinterpret_cast<V*>(smem + lay.su);
     V* tx = reinterpret_cast<V*>(smem + lay.tx);
@@ -218,6 +226,10 @@ k_bt_solve(const Sub* __restrict__ subs, const Level* __restrict__ levels, const
             mbar_init(&full[q], 1);
             mbar_init(&empty[q], BT_NW);
         }
+        for (int q = 0; q < BT_NC; ++q) {
+            mbar_init(&cfull[q], 1);
+            mbar_init(&cempty[q], BT_NW);
+        }
         mbar_init(&xbar[0], BT_NW);
         mbar_init(&xbar[1], BT_NW);
         mbar_fence_init();
@@ -229,43 +241,50 @@ k_bt_solve(const Sub* __restrict__ subs, const Level* __restrict__ levels, const
     if (warp == BT_NW) {
         // ---------------- producer warp: lane 0 streams the tiles ----------------
         if (lane == 0 && nst > 0) {
-            int p = 0;
+            int pw = 0, pc = 0;                  // tiles issued into the W ring / the coupling ring
             bool ok = true;
             for (int si = 0; si < nst && ok; ++si) {
                 const BtStep st = bt_step(rank, L, k, si, lv);
                 const Level& Lv = lv[st.l];
                 const int m = Lv.size, ldm = bt_r4(m);
-                const int nt = (st.cpl ? 1 : 0) + (st.rb - st.ra + R - 1) / R;
-                for (int u = 0; u < nt && ok; ++u, ++p) {
-                    const int q = p % ns, n = p / ns;
+                if (st.cpl) {
+                    const int q = pc % BT_NC, n = pc / BT_NC;
+                    if (n > 0 && !bt_wait<false>(&cempty[q], (unsigned)((n - 1) & 1), abort, err)) { ok = false; break; }
+                    unsigned char* dst = cslots + (size_t)q * cslot_bytes;
+                    fence_proxy_async();
+                    const bool e = st.cpl == 1;
+                    const int64_t po = e ? Lv.eptr : Lv.fptr, qo = e ? Lv.eoff : Lv.foff;
+                    const int nz = e ? Lv.enz : Lv.fnz;
+                    const unsigned pb = (unsigned)bt_r16((size_t)(m + 1) * 4);
+                    const unsigned cb = (unsigned)bt_r16((size_t)nz * 4);
+                    const unsigned vb = (unsigned)bt_r16((size_t)nz * sizeof(F));
+                    mbar_expect_tx(&cfull[q], pb + cb + vb);
+                    tma_load_1d(dst, cptr + po, pb, &cfull[q]);
+                    if (cb) tma_load_1d(dst + pb, ccol + qo, cb, &cfull[q]);
+                    if (vb) tma_load_1d(dst + pb + cb, cval + qo, vb, &cfull[q]);
+                    ++pc;
+                }
+                for (int r0 = st.ra; r0 < st.rb && ok; r0 += R, ++pw) {
+                    const int q = pw % ns, n = pw / ns;
                     if (n > 0 && !bt_wait<false>(&empty[q], (unsigned)((n - 1) & 1), abort, err)) { ok = false; break; }
                     unsigned char* dst = slots + (size_t)q * slot_bytes;
                     fence_proxy_async();
-                    if (st.cpl && u == 0) {
-                        const bool e = st.cpl == 1;
-                        const int64_t po = e ? Lv.eptr : Lv.fptr, qo = e ? Lv.eoff : Lv.foff;
-                        const int nz = e ? Lv.enz : Lv.fnz;
-                        const unsigned pb = (unsigned)bt_r16((size_t)(m + 1) * 4);
-                        const unsigned cb = (unsigned)bt_r16((size_t)nz * 4);
-                        const unsigned vb = (unsigned)bt_r16((size_t)nz * sizeof(F));
-                        mbar_expect_tx(&full[q], pb + cb + vb);
-                        tma_load_1d(dst, cptr + po, pb, &full[q]);
-                        if (cb) tma_load_1d(dst + pb, ccol + qo, cb, &full[q]);
-                        if (vb) tma_load_1d(dst + pb + cb, cval + qo, vb, &full[q]);
-                    } else {
-                        const int r0 = st.ra + (u - (st.cpl ? 1 : 0)) * R;
-                        const int nr = min(R, st.rb - r0);
-                        const unsigned wb = (unsigned)((size_t)nr * ldm * sizeof(F));
-                        mbar_expect_tx(&full[q], wb);
-                        tma_load_1d(dst, fac + Lv.offW + (int64_t)r0 * ldm, wb, &full[q]);
-                    }
+                    const int nr = min(R, st.rb - r0);
+                    const unsigned wb = (unsigned)((size_t)nr * ldm * sizeof(F));
+                    mbar_expect_tx(&full[q], wb);
+                    tma_load_1d(dst, fac + Lv.offW + (int64_t)r0 * ldm, wb, &full[q]);
                 }
             }
             // let every issued copy land before the CTA may leave
-            for (int q = 0; q < ns && q < p; ++q) {
-                const int last = q + ((p - 1 - q) / ns) * ns;      // last tile issued into slot q
+            for (int q = 0; q < ns && q < pw; ++q) {
+                const int last = q + ((pw - 1 - q) / ns) * ns;      // last tile issued into slot q
                 for (int it = 0; it < (1 << 22); ++it)
                     if (mbar_try(&full[q], (unsigned)((last / ns) & 1))) break;
+            }
+            for (int q = 0; q < BT_NC && q < pc; ++q) {
+                const int last = q + ((pc - 1 - q) / BT_NC) * BT_NC;
+                for (int it = 0; it < (1 << 22); ++it)
+                    if (mbar_try(&cfull[q], (unsigned)((last / BT_NC) & 1))) break;
             }
         }
         __syncwarp();
@@ -289,15 +308,15 @@ k_bt_solve(const Sub* __restrict__ subs, const Level* __restrict__ levels, const
             vec[e - vbase] = mk<V>(ar, aim);
         }
         bt_bar_consumers();
-        int t = 0;
+        int t = 0, tc = 0;                       // W / coupling tiles consumed
         for (int si = 0; si < nst; ++si) {
             const BtStep st = bt_step(rank, L, k, si, lv);
             const int m = lv[st.l].size, o = lv[st.l].start - vbase, ldm = bt_r4(m);
             // (b1) coupling term of the step
             if (st.cpl) {
-                const int q = t % ns;
-                bt_wait<false>(&full[q], (unsigned)((t / ns) & 1), abort, err);
-                const unsigned char* buf = slots + (size_t)q * slot_bytes;
+                const int q = tc % BT_NC;
+                bt_wait<false>(&cfull[q], (unsigned)((tc / BT_NC) & 1), abort, err);
+                const unsigned char* buf = cslots + (size_t)q * cslot_bytes;
                 const int nb = st.cpl == 1 ? st.l - 1 : st.l + 1;
                 const int ob = lv[nb].start - vbase;
                 const int nz = st.cpl == 1 ? lv[st.l].enz : lv[st.l].fnz;
@@ -306,7 +325,20 @@ k_bt_solve(const Sub* __restrict__ subs, const Level* __restrict__ levels, const
                 const F* Cv = reinterpret_cast<const F*>(C + bt_r4(nz));
                 for (int i = tid; i < m; i += BT_NT) {
                     Rt ar = 0, aim = 0;
-                    for (int pp = P[i]; pp < P[i + 1]; ++pp) {
+                    int pp = P[i];
+                    const int pe = P[i + 1];
+                    for (; pp + 4 <= pe; pp += 4) {       // four independent gathers in flight
+                        int c[4];
+                        Rt f[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) { c[u] = C[pp + u]; f[u] = (Rt)Cv[pp + u]; }
+                        V v[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) v[u] = vec[ob + c[u]];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) { ar += f[u] * v[u].x; aim += f[u] * v[u].y; }
+                    }
+                    for (; pp < pe; ++pp) {
                         const Rt f = (Rt)Cv[pp];
                         const V v = vec[ob + C[pp]];
                         ar += f * v.x;
@@ -323,8 +355,8 @@ k_bt_solve(const Sub* __restrict__ subs, const Level* __restrict__ levels, const
                     }
                 }
                 __syncwarp();
-                if (lane == 0) mbar_arrive_local(&empty[q]);
-                ++t;
+                if (lane == 0) mbar_arrive_local(&cempty[q]);
+                ++tc;
             } else {
                 for (int i = tid; i < m; i += BT_NT) {
                     if (st.kind == 0) {
@@ -362,7 +394,31 @@ k_bt_solve(const Sub* __restrict__ subs, const Level* __restrict__ levels, const
                 const F* Wt = reinterpret_cast<const F*>(slots + (size_t)q * slot_bytes);
                 const int nr = min(R, st.rb - r0);
                 if (g < ng) {
-                    for (int jj = g; jj < nr; jj += ng) {
+                    int jj = g;
+                    // four rows per pass: their loads are independent
+                    for (; jj + 3 * ng < nr; jj += 4 * ng) {
+                        V sj[4];
+#pragma unroll
+                        for (int r = 0; r < 4; ++r) sj[r] = su[r0 + jj + r * ng];
+#pragma unroll
+                        for (int u = 0; u < BT_QMAX; ++u) {
+                            const int qq = i0 + u * tq;
+                            if (qq < nq) {
+                                Rt w[4][4];
+#pragma unroll
+                                for (int r = 0; r < 4; ++r)
+                                    bt_load4<F, Rt>(Wt + (size_t)(jj + r * ng) * ldm + 4 * qq, w[r]);
+#pragma unroll
+                                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                                    for (int c = 0; c < 4; ++c) {
+                                        acc[u][c][0] += w[r][c] * sj[r].x;
+                                        acc[u][c][1] += w[r][c] * sj[r].y;
+                                    }
+                            }
+                        }
+                    }
+                    for (; jj < nr; jj += ng) {
                         const V sj = su[r0 + jj];
                         const F* wr = Wt + (size_t)jj * ldm;
 #pragma unroll

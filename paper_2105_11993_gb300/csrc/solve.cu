@@ -567,8 +567,9 @@ static void apply_T(const thm_sys* s, const F* val, const F* bg, const F* bs, in
 }
 
 // Twisted block-tridiagonal solve, one 2-CTA cluster per subdomain.  The
-// ring of shared-memory slots takes what the rest of the layout leaves: W
-// tiles of about THM_BT_TILE_BYTES (default 16 KB) each, 2..16 slots.
+// coupling blocks get a small ring of their own; the W ring takes what the
+// rest of the layout leaves: tiles of about THM_BT_TILE_BYTES (default 48 KB;
+// fewer, larger bulk copies stream faster per SM) each, 2..16 slots.
 template <class V, class F>
 static void apply_Pinv(const thm_sys* s, const F* fac, const F* cval, const int32_t* ai, const F* av,
                        const int32_t* ci, const F* cv, const int32_t* ei, const F* ev, const V* x, V* y) {
@@ -576,21 +577,28 @@ static void apply_Pinv(const thm_sys* s, const F* fac, const F* cval, const int3
     THM_REQUIRE(m->max_m <= BT_MAX_M, "level block larger than the block-solve kernel supports (" +
                                           std::to_string(m->max_m) + " > " + std::to_string(BT_MAX_M) + ")");
     static const size_t target = getenv("THM_BT_TILE_BYTES") ? (size_t)std::max(1024, atoi(getenv("THM_BT_TILE_BYTES")))
-                                                              : (size_t)16384;
+                                                              : (size_t)49152;
     const size_t cap = 227 * 1024 - 256;
     const size_t row_bytes = (size_t)bt_r4(m->max_m) * sizeof(F);
-    const size_t cpl_bytes = bt_r16((size_t)(m->max_m + 1) * 4) + bt_r16((size_t)m->max_cnz * 4) +
-                             bt_r16((size_t)m->max_cnz * sizeof(F));
-    const int rows = (int)std::max<size_t>(1, target / row_bytes);
-    const size_t slot = bt_r16(std::max(cpl_bytes, (size_t)rows * row_bytes));
-    THM_REQUIRE(slot < (size_t)INT32_MAX && m->bt_nvec < INT32_MAX, "block-solve tile too large");
-    const size_t fixed = bt_layout<V>(0, 0, m->max_lev, (int)m->bt_nvec, m->max_m).total;
+    const size_t cslot = bt_r16((size_t)(m->max_m + 1) * 4) + bt_r16((size_t)m->max_cnz * 4) +
+                         bt_r16((size_t)m->max_cnz * sizeof(F));
+    THM_REQUIRE(m->bt_nvec < INT32_MAX && cslot < (size_t)INT32_MAX, "block-solve data too large");
+    const int nvec = (int)m->bt_nvec;
+    auto layout = [&](int ns, size_t slot) {
+        return bt_layout<V>(ns, (int)slot, (int)cslot, m->max_lev, nvec, m->max_m).total;
+    };
+    // the largest tile height (<= the target) that leaves room for at least 3 slots
+    int rows = (int)std::max<size_t>(1, target / row_bytes);
+    while (rows > 1 && layout(3, bt_r16((size_t)rows * row_bytes)) > cap) --rows;
+    const size_t slot = bt_r16((size_t)rows * row_bytes);
+    THM_REQUIRE(slot < (size_t)INT32_MAX, "block-solve tile too large");
     int ns = 0;
     for (int q = 16; q >= 2 && ns == 0; --q)
-        if (bt_layout<V>(q, (int)slot, m->max_lev, (int)m->bt_nvec, m->max_m).total <= cap) ns = q;
-    THM_REQUIRE(ns >= 2, "subdomain too large for the shared-memory block solve (" + std::to_string(fixed) +
-                             " bytes of vectors and level data, " + std::to_string(slot) + "-byte tiles)");
-    const size_t smem = bt_layout<V>(ns, (int)slot, m->max_lev, (int)m->bt_nvec, m->max_m).total;
+        if (layout(q, slot) <= cap) ns = q;
+    THM_REQUIRE(ns >= 2, "subdomain too large for the shared-memory block solve (" +
+                             std::to_string(layout(0, 0)) + " bytes of vectors and level data, " +
+                             std::to_string(slot) + "-byte tiles)");
+    const size_t smem = layout(ns, slot);
     static size_t attr = 0;
     if (smem > 48 * 1024 && smem > attr) {
         THM_CUDA(cudaFuncSetAttribute(k_bt_solve<V, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -599,8 +607,8 @@ static void apply_Pinv(const thm_sys* s, const F* fac, const F* cval, const int3
     THM_LAUNCH(THM_K_PINV, s->st,
                k_bt_solve<V, F><<<dim3(2, m->n_sub), BT_THREADS, smem, s->st>>>(
                    m->d_subs.p, m->d_levels.p, fac, m->d_cpl_ptr.p, m->d_cpl_col.p, cval, m->n_loc,
-                   m->order == 2 ? 1 : 0, ai, av, ci, cv, ei, ev, rows, ns, (int)slot, m->max_lev, (int)m->bt_nvec,
-                   m->max_m, s->dev_err.p, x, y));
+                   m->order == 2 ? 1 : 0, ai, av, ci, cv, ei, ev, rows, ns, (int)slot, (int)cslot, m->max_lev,
+                   nvec, m->max_m, s->dev_err.p, x, y));
 }
 
 template <class V>

@@ -226,9 +226,11 @@ def test_long_outer_cycle_after_inner_reinit():
     solvers; re-creating the inner solver with a shorter restart must not
     lower the shared-memory limit the long outer cycles need (an outer cycle
     of 400 steps needs more than 48 KB)."""
-    import paper_2105_11993_gb300 as thm
-    P = CASES["c0"]()
+    # 4x4 subdomains of 6x6 order-2 cells: 576 interface unknowns, so 400
+    # Arnoldi steps run without a (happy) breakdown
+    P = W.square_problem(24, 4, 2, 12.0)
     mesh, sysg = make_system(P)
+    assert sysg.n_iface >= 500
     sysg.solve(mode="fp64", rtol=1e-8, inner_restart=50)
     sysg.solve(mode="fp64", rtol=1e-8, inner_restart=60)
     _, st = sysg.solve(mode="fp64", rtol=1e-30, inner_restart=60, outer_tol=1e-30, outer_maxit=400,
