@@ -25,7 +25,10 @@
 // step, then row tiles of W_l) with 1-D TMA bulk copies into two rings of
 // shared-memory slots (full/empty mbarriers): large slots for the W tiles,
 // small ones for the coupling blocks, so that a few-KB coupling block does not
-// hold a W-sized slot and the W ring reaches further ahead; 12 consumer warps hold the
+// hold a W-sized slot and the W ring reaches further ahead.  When a coupling
+// block is too large for a small slot (3-D levels of several hundred rows),
+// the consumers read it from global memory instead (cglob); a level step then
+// streams megabytes of W, next to which those loads are cheap.  12 consumer warps hold the
 // CTA's half of the subdomain vector in shared memory and run the block
 // GEMVs, both vector components at once (each W element feeds two FMAs).
 // Every wait is bounded: on expiry the CTA raises *err, stops issuing, lets
@@ -188,7 +191,8 @@ k_bt_solve(const Sub* __restrict__ subs, const Level* __restrict__ levels, const
            const int32_t* __restrict__ cptr, const int32_t* __restrict__ ccol, const F* __restrict__ cval,
            int64_t n_loc, int condensed, const int32_t* __restrict__ ai, const F* __restrict__ av,
            const int32_t* __restrict__ ci, const F* __restrict__ cv, const int32_t* __restrict__ ei,
-           const F* __restrict__ ev, int R, int ns, int slot_bytes, int cslot_bytes, int max_lev, int nvec, int max_m,
+           const F* __restrict__ ev, int R, int ns, int slot_bytes, int cslot_bytes, int cglob, int max_lev, int nvec,
+           int max_m,
            int* __restrict__ err, const V* __restrict__ x, V* __restrict__ y) {
     using Rt = typename VT<V>::R;
     namespace cg = cooperative_groups;
@@ -247,7 +251,7 @@ k_bt_solve(const Sub* __restrict__ subs, const Level* __restrict__ levels, const
                 const BtStep st = bt_step(rank, L, k, si, lv);
                 const Level& Lv = lv[st.l];
                 const int m = Lv.size, ldm = bt_r4(m);
-                if (st.cpl) {
+                if (st.cpl && !cglob) {
                     const int q = pc % BT_NC, n = pc / BT_NC;
                     if (n > 0 && !bt_wait<false>(&cempty[q], (unsigned)((n - 1) & 1), abort, err)) { ok = false; break; }
                     unsigned char* dst = cslots + (size_t)q * cslot_bytes;
@@ -315,14 +319,25 @@ k_bt_solve(const Sub* __restrict__ subs, const Level* __restrict__ levels, const
             // (b1) coupling term of the step
             if (st.cpl) {
                 const int q = tc % BT_NC;
-                bt_wait<false>(&cfull[q], (unsigned)((tc / BT_NC) & 1), abort, err);
-                const unsigned char* buf = cslots + (size_t)q * cslot_bytes;
                 const int nb = st.cpl == 1 ? st.l - 1 : st.l + 1;
                 const int ob = lv[nb].start - vbase;
                 const int nz = st.cpl == 1 ? lv[st.l].enz : lv[st.l].fnz;
-                const int* P = reinterpret_cast<const int*>(buf);
-                const int* C = P + bt_r4(m + 1);
-                const F* Cv = reinterpret_cast<const F*>(C + bt_r4(nz));
+                const int* P;
+                const int* C;
+                const F* Cv;
+                if (cglob) {
+                    const int64_t po = st.cpl == 1 ? lv[st.l].eptr : lv[st.l].fptr;
+                    const int64_t qo = st.cpl == 1 ? lv[st.l].eoff : lv[st.l].foff;
+                    P = cptr + po;
+                    C = ccol + qo;
+                    Cv = cval + qo;
+                } else {
+                    bt_wait<false>(&cfull[q], (unsigned)((tc / BT_NC) & 1), abort, err);
+                    const unsigned char* buf = cslots + (size_t)q * cslot_bytes;
+                    P = reinterpret_cast<const int*>(buf);
+                    C = P + bt_r4(m + 1);
+                    Cv = reinterpret_cast<const F*>(C + bt_r4(nz));
+                }
                 for (int i = tid; i < m; i += BT_NT) {
                     Rt ar = 0, aim = 0;
                     int pp = P[i];
@@ -354,9 +369,11 @@ k_bt_solve(const Sub* __restrict__ subs, const Level* __restrict__ levels, const
                         su[i] = mk<V>(ar, aim);
                     }
                 }
-                __syncwarp();
-                if (lane == 0) mbar_arrive_local(&cempty[q]);
-                ++tc;
+                if (!cglob) {
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive_local(&cempty[q]);
+                    ++tc;
+                }
             } else {
                 for (int i = tid; i < m; i += BT_NT) {
                     if (st.kind == 0) {

@@ -580,9 +580,14 @@ static void apply_Pinv(const thm_sys* s, const F* fac, const F* cval, const int3
                                                               : (size_t)49152;
     const size_t cap = 227 * 1024 - 256;
     const size_t row_bytes = (size_t)bt_r4(m->max_m) * sizeof(F);
-    const size_t cslot = bt_r16((size_t)(m->max_m + 1) * 4) + bt_r16((size_t)m->max_cnz * 4) +
+    const size_t cfull = bt_r16((size_t)(m->max_m + 1) * 4) + bt_r16((size_t)m->max_cnz * 4) +
                          bt_r16((size_t)m->max_cnz * sizeof(F));
-    THM_REQUIRE(m->bt_nvec < INT32_MAX && cslot < (size_t)INT32_MAX, "block-solve data too large");
+    // coupling blocks larger than 12 KB are read from global memory in place
+    // (THM_BT_CPL_GLOBAL=1 forces that path, for tests)
+    const char* force = getenv("THM_BT_CPL_GLOBAL");
+    const int cglob = (cfull > 12 * 1024 || (force && atoi(force) != 0)) ? 1 : 0;
+    const size_t cslot = cglob ? 16 : cfull;
+    THM_REQUIRE(m->bt_nvec < INT32_MAX, "block-solve data too large");
     const int nvec = (int)m->bt_nvec;
     auto layout = [&](int ns, size_t slot) {
         return bt_layout<V>(ns, (int)slot, (int)cslot, m->max_lev, nvec, m->max_m).total;
@@ -607,8 +612,8 @@ static void apply_Pinv(const thm_sys* s, const F* fac, const F* cval, const int3
     THM_LAUNCH(THM_K_PINV, s->st,
                k_bt_solve<V, F><<<dim3(2, m->n_sub), BT_THREADS, smem, s->st>>>(
                    m->d_subs.p, m->d_levels.p, fac, m->d_cpl_ptr.p, m->d_cpl_col.p, cval, m->n_loc,
-                   m->order == 2 ? 1 : 0, ai, av, ci, cv, ei, ev, rows, ns, (int)slot, (int)cslot, m->max_lev,
-                   nvec, m->max_m, s->dev_err.p, x, y));
+                   m->order == 2 ? 1 : 0, ai, av, ci, cv, ei, ev, rows, ns, (int)slot, (int)cslot, cglob,
+                   m->max_lev, nvec, m->max_m, s->dev_err.p, x, y));
 }
 
 template <class V>

@@ -238,3 +238,33 @@ def test_long_outer_cycle_after_inner_reinit():
     from paper_2105_11993_gb300 import _binding as B
     assert st["status"] in (0, -2), (st["status"], B.load().thm_last_error().decode())
     assert st["outer_iters"] >= 390
+
+
+@pytest.mark.parametrize("name", ["p2_rot", "cube_ragged"])
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+def test_pinv_coupling_from_global_memory(name, mode, monkeypatch):
+    """The block solve reads large coupling blocks from global memory instead
+    of its shared-memory ring; forced here on small cases, both paths must
+    give the oracle's P_i^{-1}."""
+    import scipy.sparse.linalg as spla
+    import paper_2105_11993_gb300 as thm
+    P = CASES[name]()
+    mesh, sysg = make_system(P)
+    D = _oracle_blocks(P)
+    gd, sub, pos = _local_perm(sysg, D)
+    x = _rand_local(sysg.n_local, 3)
+    xt = torch.tensor(x, device="cuda")
+    y_ring = sysg.apply_local(thm.OP_PINV, xt, mode=mode).cpu().numpy()
+    monkeypatch.setenv("THM_BT_CPL_GLOBAL", "1")
+    y_glob = sysg.apply_local(thm.OP_PINV, xt, mode=mode).cpu().numpy()
+    tol = 1e-10 if mode == "fp64" else 2e-3
+    for s in D.subs:
+        idx = np.flatnonzero(sub == s.idx)
+        xs = np.zeros(len(s.free), np.complex128)
+        xs[pos[idx]] = x[idx]
+        lu = spla.splu(s.P)
+        ys = lu.solve(xs.real) + 1j * lu.solve(xs.imag)
+        for y in (y_ring, y_glob):
+            assert np.linalg.norm(y[idx] - ys[pos[idx]]) / np.linalg.norm(ys) <= tol
+    # same arithmetic in the same order: the two paths agree to rounding
+    assert np.linalg.norm(y_glob - y_ring) <= (1e-13 if mode == "fp64" else 1e-5) * np.linalg.norm(y_ring)
