@@ -180,9 +180,12 @@ int thm_ddm_solve_host(thm_sys* s, const thm_solve_opts* opts, double* u_host, t
  * [n_dof] (for L = u^H M_R u this is M_R u), solves K^T lambda = dLdu_conj on
  * the free DOFs (K^T = K, the same DDM-GMRES solve) and returns
  *   grad_mu_inv[c] = -2 Re(lambda_c^T A_c u_c)           (device double [n_cell])
- *   grad_omega     = -2 Re(lambda^T (dK/domega) u)       (host double)
- * with dK/domega = -2 omega M + i kappa M_Gamma.  u is the forward solution
- * (device complex [n_dof]); lambda is zero on Dirichlet DOFs.
+ *   grad_omega     = -2 Re(lambda^T [(dK/domega) u + K du_D/domega])
+ *                    + 2 Re(a^T du_D/domega)              (host double)
+ * with dK/domega = -2 omega M + i kappa M_Gamma, a = dLdu_conj and du_D/domega
+ * the derivative of the Dirichlet moments.  2-D (orders 1, 2) and 3-D.  u is
+ * the forward solution (device complex [n_dof]); lambda is zero on Dirichlet
+ * DOFs.
  */
 int thm_adjoint(thm_sys* s, const thm_solve_opts* opts, const double* u, const double* dLdu_conj,
                 double* grad_mu_inv, double* grad_omega, thm_stats* stats);

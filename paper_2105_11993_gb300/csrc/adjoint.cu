@@ -10,6 +10,7 @@
 #include <chrono>
 #include <cmath>
 
+#include "element.cuh"
 #include "solver.cuh"
 
 namespace thm {
@@ -68,17 +69,16 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
 }
 
 // Per cell: dL/dmu_c and the cell's share of dL/domega (volume terms).
-__global__ void k_adj_cells(int64_t n_cell, int nb, const double* __restrict__ ref, const double* __restrict__ X,
-                            const int32_t* __restrict__ cells, const int32_t* __restrict__ cdofs,
-                            const int8_t* __restrict__ signs, const double* __restrict__ mu, double omega,
-                            const double2* __restrict__ lam, const double2* __restrict__ u,
-                            const double2* __restrict__ duD, double* __restrict__ gmu, double* __restrict__ gw) {
+__global__ void k_adj_cells(int dim, int64_t n_cell, int nb, const double* __restrict__ ref,
+                            const double* __restrict__ X, const int32_t* __restrict__ cells,
+                            const int32_t* __restrict__ cdofs, const int8_t* __restrict__ signs,
+                            const double* __restrict__ mu, double omega, const double2* __restrict__ lam,
+                            const double2* __restrict__ u, const double2* __restrict__ duD,
+                            double* __restrict__ gmu, double* __restrict__ gw) {
     int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (c >= n_cell) return;
-    const int32_t* cv = cells + c * 4;
-    double ax = X[cv[1] * 2] - X[cv[0] * 2], ay = X[cv[1] * 2 + 1] - X[cv[0] * 2 + 1];
-    double bx = X[cv[2] * 2] - X[cv[0] * 2], by = X[cv[2] * 2 + 1] - X[cv[0] * 2 + 1];
-    double a = sqrt(ax * ax + ay * ay), b = sqrt(bx * bx + by * by);
+    double h[3];
+    cell_sides(X, dim, cells, c, h);
     double2 lc[12], uc[12], dc[12];
     for (int i = 0; i < nb; ++i) {
         double s = (double)signs[c * nb + i];
@@ -92,8 +92,8 @@ __global__ void k_adj_cells(int64_t n_cell, int nb, const double* __restrict__ r
     for (int i = 0; i < nb; ++i) {
         double2 tA = make_double2(0, 0), tM = make_double2(0, 0), tD = make_double2(0, 0);
         for (int j = 0; j < nb; ++j) {
-            double A = ref[i * nb + j] / (a * b);
-            double M = (b / a) * ref[144 + i * nb + j] + (a / b) * ref[288 + i * nb + j];
+            double A, M;
+            cell_am(dim, ref, nb, h, i, j, A, M);
             tA.x += A * uc[j].x; tA.y += A * uc[j].y;
             tM.x += M * uc[j].x; tM.y += M * uc[j].y;
             double K = mu[c] * A - w2 * M;
@@ -108,18 +108,34 @@ __global__ void k_adj_cells(int64_t n_cell, int nb, const double* __restrict__ r
     gw[c] = -2.0 * (-2.0 * omega * sM.x) - 2.0 * sD.x;
 }
 
-// Impedance-face share of dL/domega (2-D: diagonal face mass per DOF) and the
-// explicit dependence of L on the Dirichlet data.
-// -2 Re(lambda^T (i kappa M_Gamma) u) per local row, 2-D: the Gamma^inf face
-// mass is diagonal and bg holds kappa*omega*m per row (each boundary edge lies
-// in one cell, so each term is counted once).
-__global__ void k_adj_rows(int64_t n_loc, const int64_t* __restrict__ gdof, const double* __restrict__ bg,
-                           double inv_omega, const double2* __restrict__ lam, const double2* __restrict__ u,
-                           double* __restrict__ gw) {
-    int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (r >= n_loc) return;
-    double2 p = cmul(lam[gdof[r]], u[gdof[r]]);
-    gw[r] = 2.0 * bg[r] * inv_omega * p.y;
+// Gamma^inf face share of dL/domega: with m_f the signed face mass and
+// K's face term i kappa omega m_f,
+//   -2 Re(lambda^T (i kappa m_f) u) - 2 Re(lambda^T (i kappa omega m_f) du_D/domega)
+// (u includes the Dirichlet values; in 3-D an impedance face may hold edges
+// of the Dirichlet boundary, so both terms reach Dirichlet columns).
+__global__ void k_adj_faces(int dim, int64_t n_face, int fd, const double* __restrict__ ref,
+                            const double* __restrict__ X, const int32_t* __restrict__ face_v,
+                            const int32_t* __restrict__ face_dof, const int8_t* __restrict__ face_sgn,
+                            const int8_t* __restrict__ face_kind, double kappa, double omega,
+                            const double2* __restrict__ lam, const double2* __restrict__ u,
+                            const double2* __restrict__ duD, double* __restrict__ gw) {
+    int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (f >= n_face) return;
+    if (face_kind[f] != 1) { gw[f] = 0; return; }
+    double2 s1 = make_double2(0, 0), s2 = make_double2(0, 0);
+    for (int a = 0; a < fd; ++a) {
+        const int32_t da = face_dof[f * fd + a];
+        const double2 la = lam[da];
+        for (int b = 0; b < fd; ++b) {
+            const int32_t db = face_dof[f * fd + b];
+            const double mab = face_sgn[f * fd + a] * face_sgn[f * fd + b] *
+                               face_mass(dim, ref, X, face_v + f * 4, a, b);
+            const double2 p = cmul(la, u[db]), q = cmul(la, duD[db]);
+            s1.x += mab * p.x; s1.y += mab * p.y;
+            s2.x += mab * q.x; s2.y += mab * q.y;
+        }
+    }
+    gw[f] = 2.0 * kappa * s1.y + 2.0 * kappa * omega * s2.y;      // -2 Re(i c z) = 2 c Im(z)
 }
 
 __global__ void k_adj_dir(int64_t n_dof, const double2* __restrict__ a, const double2* __restrict__ duD,
@@ -157,15 +173,16 @@ int adjoint(thm_sys* s, const thm_solve_opts* opts, const double2* u, const doub
             double* grad_omega, thm_stats* stats) {
     auto t0 = std::chrono::steady_clock::now();
     const thm_mesh* m = s->m;
-    THM_REQUIRE(m->dim == 2, "the adjoint is available for 2-D meshes");
     cudaStream_t st = s->st;
     SolveCfg c = make_cfg(opts);
     prepare(s, c);
     auto nb = [](int64_t n) { return (unsigned)((n + 255) / 256); };
     DArr<double2> rhs, lam, duD;
-    DArr<double> gw_cell, gw_row, gw_dof, part;
+    DArr<double> gw_cell, gw_face, gw_dof, part;
     rhs.alloc(m->n_loc); lam.alloc(m->n_dof); duD.alloc(m->n_dof);
-    gw_cell.alloc(m->n_cell); gw_row.alloc(m->n_loc); gw_dof.alloc(m->n_dof); part.alloc(256);
+    gw_cell.alloc(m->n_cell); gw_face.alloc(std::max<int64_t>(1, m->n_face)); gw_dof.alloc(m->n_dof);
+    part.alloc(256);
+    gw_face.zero(st);
     THM_LAUNCH(THM_K_DDM, st, k_adj_rhs<<<nb(m->n_loc), 256, 0, st>>>(m->n_loc, m->d_loc_gdof.p, m->d_loc_is_owner.p, a, rhs.p));
     RunStats rs;
     double rel = 0;
@@ -176,15 +193,17 @@ int adjoint(thm_sys* s, const thm_solve_opts* opts, const double2* u, const doub
             (int64_t)m->dir_edges.size(), m->dim, m->order, m->d_dir_edges.p, m->d_coords.p, m->d_edge_lo.p,
             m->d_edge_hi.p, s->omega, s->pol[0], s->pol[1], s->pol[2], s->pol[3], s->pol[4], s->pol[5], s->dir[0],
             s->dir[1], s->dir[2], duD.p));
-    THM_LAUNCH(THM_K_DDM, st, k_adj_cells<<<nb(m->n_cell), 256, 0, st>>>(m->n_cell, m->dpc, s->ref.p, m->d_coords.p,
+    THM_LAUNCH(THM_K_DDM, st, k_adj_cells<<<nb(m->n_cell), 256, 0, st>>>(m->dim, m->n_cell, m->dpc, s->ref.p, m->d_coords.p,
                                                                         m->d_cells.p, m->d_cell_dofs.p, m->d_cell_signs.p,
                                                                         s->mu_inv.p, s->omega, lam.p, u, duD.p, grad_mu,
                                                                         gw_cell.p));
-    THM_LAUNCH(THM_K_DDM, st, k_adj_rows<<<nb(m->n_loc), 256, 0, st>>>(m->n_loc, m->d_loc_gdof.p, s->bg64.p,
-                                                                      1.0 / s->omega, lam.p, u, gw_row.p));
+    if (m->n_face > 0)
+        THM_LAUNCH(THM_K_DDM, st, k_adj_faces<<<nb(m->n_face), 256, 0, st>>>(
+            m->dim, m->n_face, m->fd, s->ref.p, m->d_coords.p, m->d_face_v.p, m->d_face_dof.p, m->d_face_sgn.p,
+            m->d_face_kind.p, s->kappa, s->omega, lam.p, u, duD.p, gw_face.p));
     THM_LAUNCH(THM_K_DDM, st, k_adj_dir<<<nb(m->n_dof), 256, 0, st>>>(m->n_dof, a, duD.p, gw_dof.p));
     THM_CUDA(cudaGetLastError());
-    *grad_omega = device_sum(st, gw_cell.p, m->n_cell, part) + device_sum(st, gw_row.p, m->n_loc, part) +
+    *grad_omega = device_sum(st, gw_cell.p, m->n_cell, part) + device_sum(st, gw_face.p, std::max<int64_t>(1, m->n_face), part) +
                   device_sum(st, gw_dof.p, m->n_dof, part);
     double sec = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     fill_stats(rs, rel, sec, stats);

@@ -78,3 +78,63 @@ def test_adjoint_vs_central_differences_and_autograd():
             assert abs(g_mu[c] - fd) <= 1e-5 * max(abs(fd), 1e-3 * scale)
         fdw = (float(L_of(mu.detach(), P.omega + h)) - float(L_of(mu.detach(), P.omega - h))) / (2 * h)
         assert abs(g_w - fdw) <= 1e-5 * abs(fdw)
+
+
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+def test_adjoint_3d_matches_oracle_adjoint(mode):
+    """3-D hexes over 2x2x2 subdomains, oblique incidence (omega-dependent
+    Dirichlet data on a face that borders impedance faces)."""
+    import paper_2105_11993_gb300 as thm
+    P = W.cube_problem(4, 2, 6.0, mu_inv=W.mu_inv_lognormal(64, 0.3, "gadj3"), relabel=True, rotate_cells=True)
+    P.direction = np.array([0.6, 0.8, 0.0])
+    S = fem.assemble(P)
+    X = P.mesh.coords[P.mesh.cells].mean(1)
+    region = np.flatnonzero(np.all((X > 0.2) & (X < 0.8), axis=1))
+    MR = adj.region_mass(P, S, region)
+    mesh = thm.Mesh.from_workload(P.mesh, P.order)
+    sysg = thm.System(mesh, P.mu_inv, P.omega, P.kappa, P.pol, P.direction)
+    tol = 1e-12 if mode == "fp64" else 1e-11
+    u, _ = sysg.solve(mode=mode, rtol=tol)
+    a = MR @ np.conj(u.cpu().numpy())
+    g_mu, g_w, _ = sysg.adjoint(u, torch.tensor(a, device="cuda"), mode=mode, rtol=tol)
+    u0 = fem.solve_monolithic(S)
+    g_ref, gw_ref, _ = adj.adjoint_gradients(P, S, u0, MR @ np.conj(u0))
+    assert np.linalg.norm(g_mu.cpu().numpy() - g_ref) <= 1e-8 * np.linalg.norm(g_ref)
+    assert abs(g_w - gw_ref) <= 1e-8 * abs(gw_ref)
+
+
+def test_adjoint_3d_vs_central_differences():
+    """3-D (12^3 hexes, 3x3x3 subdomains, smooth random mu^{-1} as in the
+    48^3 differentiation workload, oblique incidence): gradients from one
+    adjoint solve against central differences (h = 1e-4) of the GPU solve
+    itself, to 1e-5 relative."""
+    import paper_2105_11993_gb300 as thm
+    n = 12
+    mu = W.mu_inv_smooth_3d(n, 0.3, 3.0, "adj12/mu")
+    P = W.cube_problem(n, 3, 3 * np.pi, mu_inv=mu)
+    P.direction = np.array([0.6, 0.8, 0.0])
+    X = P.mesh.coords[P.mesh.cells].mean(1)
+    region = np.flatnonzero(np.all((X >= 5 / n) & (X < 7 / n), axis=1))
+    S = fem.assemble(P)
+    MR = torch.tensor(adj.region_mass(P, S, region).toarray(), dtype=torch.complex128, device="cuda")
+    mesh = thm.Mesh.from_workload(P.mesh, P.order)
+
+    def solve(mu_c, omega):
+        s = thm.System(mesh, mu_c, omega, P.kappa, P.pol, P.direction)
+        u, _ = s.solve(mode="mixed", rtol=1e-13)
+        return s, u
+
+    s, u = solve(P.mu_inv, P.omega)
+    a = MR @ torch.conj(u)
+    g_mu, g_w, _ = s.adjoint(u, a, mode="mixed", rtol=1e-13)
+    g_mu = g_mu.cpu().numpy()
+    L = lambda uu: float(torch.real(torch.vdot(uu, MR @ uu)))
+    h = 1e-4
+    scale = np.abs(g_mu).max()
+    for c in np.random.default_rng(7).choice(P.mesh.n_cell, 3, replace=False):
+        mp = P.mu_inv.copy(); mp[c] += h
+        mm = P.mu_inv.copy(); mm[c] -= h
+        fd = (L(solve(mp, P.omega)[1]) - L(solve(mm, P.omega)[1])) / (2 * h)
+        assert abs(g_mu[c] - fd) <= 1e-5 * max(abs(fd), 1e-3 * scale), (c, g_mu[c], fd)
+    fdw = (L(solve(P.mu_inv, P.omega + h)[1]) - L(solve(P.mu_inv, P.omega - h)[1])) / (2 * h)
+    assert abs(g_w - fdw) <= 1e-5 * abs(fdw), (g_w, fdw)
