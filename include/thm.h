@@ -125,6 +125,34 @@ int thm_assemble(thm_sys** out, const thm_mesh* m, const double* mu_inv, int mu_
                  double omega, double kappa, const double* pol, const double* dir,
                  void* stream);
 
+/*
+ * Batches of independent problems (the paper solves one problem at a time;
+ * this is the batched form of the same solve).  A batch mesh is the disjoint
+ * union of the problems' meshes, built with thm_mesh_create: subdomain ids are
+ * unique across the batch, each problem's subdomains form a contiguous,
+ * increasing range of ids and its vertices a contiguous range of vertex ids
+ * (so its global DOFs are a contiguous range).
+ *
+ * thm_mesh_set_problems -- declare the batch: sub_problem (host int32
+ *   [n_sub]) gives each subdomain's problem in [0, n_prob), non-decreasing.
+ *   Must come before the first thm_assemble on the mesh.  Errors: THM_EINVAL
+ *   when the ranges are not contiguous, problems share a DOF or an interface.
+ *
+ * thm_assemble_batch -- thm_assemble with one omega per problem (host double
+ *   [n_prob]); mu_inv, kappa, pol and dir as in thm_assemble (shared).  A batch
+ *   mesh must be assembled with this call.
+ *
+ * thm_ddm_solve on a batch system runs every problem's DDM together: one set
+ * of kernel launches per step covers all subdomains of all problems, the
+ * interface GMRES keeps one Krylov segment (Hessenberg, Givens, convergence
+ * flag) per problem, and the refinement stops when every problem's relative
+ * FP64 residual is <= rtol (stats->rel_residual is the largest).  The adjoint
+ * takes single problems only.
+ */
+int thm_mesh_set_problems(thm_mesh* m, int32_t n_prob, const int32_t* sub_problem);
+int thm_assemble_batch(thm_sys** out, const thm_mesh* m, const double* mu_inv, int mu_inv_on_device,
+                       const double* omega, double kappa, const double* pol, const double* dir, void* stream);
+
 typedef struct thm_solve_opts {
     int    mode;           /* THM_MODE_FP64 or THM_MODE_MIXED */
     double rtol;           /* target ||f - K u|| / ||f|| (global, FP64), e.g. 1e-8 */
@@ -142,7 +170,14 @@ typedef struct thm_solve_opts {
                               interface residual falls (clamp(1e-2 * outer_tol/||r_k||,
                               inner_tol, 1e-6)); the refinement on the FP64 residual still
                               decides convergence.  0: fixed inner_tol */
+    int    outer_method;   /* THM_OUTER_GMRES (0): GMRES on (I - A) g = b (Eq. 8);
+                              THM_OUTER_JACOBI (1): the fixed-point iteration
+                              g <- A g + b of the same map, stopped when
+                              ||(I - A) g - b|| <= outer_tol ||b|| */
 } thm_solve_opts;
+
+#define THM_OUTER_GMRES 0
+#define THM_OUTER_JACOBI 1
 
 typedef struct thm_stats {
     int    outer_iters;        /* interface GMRES iterations, summed over refinement */

@@ -23,7 +23,7 @@ symbols = [
     "thm_ddm_solve_host", "thm_adjoint", "thm_sys_destroy", "thm_last_error", "thm_sys_info",
     "thm_local_dofs", "thm_iface_dofs", "thm_apply_local", "thm_sweep", "thm_local_sources",
     "thm_dirichlet_values", "thm_kernel_launches", "thm_profile_enable", "thm_profile_read",
-    "thm_alg_bytes", "thm_residual_noalloc",
+    "thm_alg_bytes", "thm_residual_noalloc", "thm_mesh_set_problems", "thm_assemble_batch",
 ]
 
 
@@ -37,7 +37,7 @@ class SolveOptions(C.Structure):
     _fields_ = [("mode", C.c_int), ("rtol", C.c_double), ("inner_restart", C.c_int),
                 ("inner_tol", C.c_double), ("inner_maxit", C.c_int), ("outer_restart", C.c_int),
                 ("outer_tol", C.c_double), ("outer_maxit", C.c_int), ("max_refine", C.c_int),
-                ("relax", C.c_int)]
+                ("relax", C.c_int), ("outer_method", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -69,6 +69,8 @@ def load():
         "thm_mesh_info": [P, P, P, P, P, P, P],
         "thm_mesh_destroy": [P],
         "thm_assemble": [C.POINTER(P), P, P, C.c_int, C.c_double, C.c_double, P, P, P],
+        "thm_mesh_set_problems": [P, C.c_int32, P],
+        "thm_assemble_batch": [C.POINTER(P), P, P, C.c_int, P, C.c_double, P, P, P],
         "thm_ddm_solve": [P, P, P, P],
         "thm_ddm_solve_host": [P, P, P, P],
         "thm_adjoint": [P, P, P, P, P, P, P],
@@ -162,6 +164,34 @@ class Mesh:
     def from_workload(cls, mesh, order, max_block=0):
         return cls(mesh.dim, order, mesh.coords, mesh.cells, mesh.cell_sub, mesh.bfaces, mesh.btag, max_block)
 
+    def set_problems(self, sub_problem):
+        """thm_mesh_set_problems: the mesh is a batch of independent problems."""
+        sp = np.ascontiguousarray(sub_problem, np.int32)
+        self._keep.append(sp)
+        self.n_prob = int(sp.max()) + 1
+        _check(load().thm_mesh_set_problems(self.h, self.n_prob, _ptr(sp)))
+
+    @classmethod
+    def batch(cls, meshes, order, max_block=0):
+        """Disjoint union of meshes (vertices and subdomains numbered mesh by
+        mesh), declared as a batch.  Returns (mesh, offsets) with offsets the
+        per-problem starts of vertices, cells and subdomains."""
+        dim = meshes[0].dim
+        coords, cells, subs, bfaces, btag, sub_prob = [], [], [], [], [], []
+        v0 = c0 = s0 = 0
+        offs = []
+        for p, mh in enumerate(meshes):
+            offs.append((v0, c0, s0))
+            ns = int(mh.cell_sub.max()) + 1
+            coords.append(mh.coords); cells.append(mh.cells + v0); subs.append(mh.cell_sub + s0)
+            bfaces.append(mh.bfaces + v0); btag.append(mh.btag); sub_prob.append(np.full(ns, p, np.int32))
+            v0 += mh.coords.shape[0]; c0 += mh.cells.shape[0]; s0 += ns
+        offs.append((v0, c0, s0))
+        m = cls(dim, order, np.concatenate(coords), np.concatenate(cells), np.concatenate(subs),
+                np.concatenate(bfaces), np.concatenate(btag), max_block)
+        m.set_problems(np.concatenate(sub_prob))
+        return m, offs
+
     def info(self, with_dofs=False):
         lib = load()
         nd, ne, ns, dpc = I64(), I64(), C.c_int32(), C.c_int32()
@@ -180,11 +210,15 @@ class Mesh:
             self.h = None
 
 
+OUTER_GMRES, OUTER_JACOBI = 0, 1
+
+
 def _opts(mode="fp64", rtol=1e-8, inner_restart=0, inner_tol=0.0, inner_maxit=0, outer_restart=0,
-          outer_tol=0.0, outer_maxit=0, max_refine=0, relax=0):
+          outer_tol=0.0, outer_maxit=0, max_refine=0, relax=0, outer="gmres"):
     m = {"fp64": MODE_FP64, "mixed": MODE_MIXED}[mode] if isinstance(mode, str) else int(mode)
+    om = {"gmres": OUTER_GMRES, "jacobi": OUTER_JACOBI}[outer] if isinstance(outer, str) else int(outer)
     return SolveOptions(m, rtol, inner_restart, inner_tol, inner_maxit, outer_restart, outer_tol,
-                        outer_maxit, max_refine, int(relax))
+                        outer_maxit, max_refine, int(relax), om)
 
 
 class System:
@@ -201,17 +235,27 @@ class System:
         st = stream if stream is not None else torch.cuda.current_stream()
         self.stream = st
         h = P()
+        batch = np.ndim(omega) > 0
+        if batch:
+            self._omega = np.ascontiguousarray(omega, np.float64)
+
+        def assemble(mu_ptr, on_device):
+            if batch:
+                return lib.thm_assemble_batch(C.byref(h), mesh.h, mu_ptr, on_device, _ptr(self._omega),
+                                              float(kappa), _ptr(self._pol), _ptr(self._dir),
+                                              C.c_void_p(st.cuda_stream))
+            return lib.thm_assemble(C.byref(h), mesh.h, mu_ptr, on_device, float(omega), float(kappa),
+                                    _ptr(self._pol), _ptr(self._dir), C.c_void_p(st.cuda_stream))
+
         if isinstance(mu_inv, torch.Tensor):
             mu = mu_inv.to(torch.float64).contiguous()
             assert mu.is_cuda
             self._mu = mu
-            rc = lib.thm_assemble(C.byref(h), mesh.h, _dptr(mu), 1, float(omega), float(kappa), _ptr(self._pol),
-                                  _ptr(self._dir), C.c_void_p(st.cuda_stream))
+            rc = assemble(_dptr(mu), 1)
         else:
             mu = np.ascontiguousarray(mu_inv, np.float64)
             self._mu = mu
-            rc = lib.thm_assemble(C.byref(h), mesh.h, _ptr(mu), 0, float(omega), float(kappa), _ptr(self._pol),
-                                  _ptr(self._dir), C.c_void_p(st.cuda_stream))
+            rc = assemble(_ptr(mu), 0)
         _check(rc)
         self.h = h
         self.n_dof = mesh.info()["n_dof"]

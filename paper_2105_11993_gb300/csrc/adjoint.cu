@@ -173,6 +173,7 @@ int adjoint(thm_sys* s, const thm_solve_opts* opts, const double2* u, const doub
             double* grad_omega, thm_stats* stats) {
     auto t0 = std::chrono::steady_clock::now();
     const thm_mesh* m = s->m;
+    THM_REQUIRE(m->n_prob == 1, "the adjoint takes a single problem, not a batch");
     cudaStream_t st = s->st;
     SolveCfg c = make_cfg(opts);
     prepare(s, c);

@@ -149,7 +149,7 @@ __global__ void k_ref_matrices(int dim, int order, int nb, double* ref) {
 __global__ void k_assemble(int dim, int64_t n_loc, int nb, int maxc, const double* __restrict__ ref,
                            const double* __restrict__ X, const int32_t* __restrict__ cells,
                            const int8_t* __restrict__ signs, const int32_t* __restrict__ cell_loc,
-                           const double* __restrict__ mu, double w2,
+                           const double* __restrict__ mu, const double* __restrict__ w2c,
                            const int64_t* __restrict__ slice_ptr, const int32_t* __restrict__ col,
                            const uint8_t* __restrict__ pad, const int32_t* __restrict__ row_cell,
                            const int32_t* __restrict__ row_k, double* __restrict__ val64,
@@ -174,7 +174,7 @@ __global__ void k_assemble(int dim, int64_t n_loc, int nb, int maxc, const doubl
                     double hh[3];
                     cell_sides(X, dim, cells, c, hh);
                     double s = (double)(signs[(int64_t)c * nb + kr] * signs[(int64_t)c * nb + kc]);
-                    v += s * cell_entry(dim, ref, nb, mu[c], w2, hh, kr, kc);
+                    v += s * cell_entry(dim, ref, nb, mu[c], w2c[c], hh, kr, kc);
                 }
             }
         }
@@ -193,7 +193,8 @@ __global__ void k_face_terms(int dim, int64_t n_loc, int fd, const double* __res
                              const int32_t* __restrict__ face_loc, const int32_t* __restrict__ row_face,
                              const int8_t* __restrict__ row_face_a, const int8_t* __restrict__ row_face_side,
                              const int64_t* __restrict__ slice_ptr, const int32_t* __restrict__ col,
-                             const uint8_t* __restrict__ pad, double kw, double* bg64, double* bs64, float* bg32,
+                             const uint8_t* __restrict__ pad, const double* __restrict__ kwf, double* bg64,
+                             double* bs64, float* bg32,
                              float* bs32, double* bvg64, double* bvs64, float* bvg32, float* bvs32) {
     int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (r >= n_loc) return;
@@ -204,7 +205,7 @@ __global__ void k_face_terms(int dim, int64_t n_loc, int fd, const double* __res
             const int32_t f = row_face[r * RF + u];
             if (f < 0) continue;
             const int a = row_face_a[r * RF + u];
-            const double v = kw * face_mass(2, ref, X, face_v + (int64_t)f * 4, a, a);
+            const double v = kwf[f] * face_mass(2, ref, X, face_v + (int64_t)f * 4, a, a);
             if (face_kind[f] == 1) g += v; else s += v;
         }
         bg64[r] = g; bs64[r] = s; bg32[r] = (float)g; bs32[r] = (float)s;
@@ -226,7 +227,7 @@ __global__ void k_face_terms(int dim, int64_t n_loc, int fd, const double* __res
                 const int a = row_face_a[r * RF + u], side = row_face_side[r * RF + u];
                 for (int b = 0; b < fd; ++b) {
                     if (face_loc[((int64_t)f * 2 + side) * fd + b] != cc) continue;
-                    const double v = kw * face_sgn[(int64_t)f * fd + a] * face_sgn[(int64_t)f * fd + b] *
+                    const double v = kwf[f] * face_sgn[(int64_t)f * fd + a] * face_sgn[(int64_t)f * fd + b] *
                                      face_mass(3, ref, X, face_v + (int64_t)f * 4, a, b);
                     if (face_kind[f] == 1) g += v; else s += v;
                 }
@@ -236,16 +237,18 @@ __global__ void k_face_terms(int dim, int64_t n_loc, int fd, const double* __res
     }
 }
 
-// Values of the interface-entry terms: signed face mass between DOFs a and b.
+// Values of the interface-entry terms: kappa*omega times the signed face mass
+// between DOFs a and b.
 __global__ void k_iface_vals(int dim, int64_t n_terms, int fd, const double* __restrict__ ref,
                              const double* __restrict__ X, const int32_t* __restrict__ face_v,
                              const int8_t* __restrict__ face_sgn, const int32_t* __restrict__ tf,
-                             const int8_t* __restrict__ ta, const int8_t* __restrict__ tb, double* __restrict__ val) {
+                             const int8_t* __restrict__ ta, const int8_t* __restrict__ tb,
+                             const double* __restrict__ kwf, double* __restrict__ val) {
     int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (p >= n_terms) return;
     const int32_t f = tf[p];
     const int a = ta[p], b = tb[p];
-    val[p] = face_sgn[(int64_t)f * fd + a] * face_sgn[(int64_t)f * fd + b] *
+    val[p] = kwf[f] * face_sgn[(int64_t)f * fd + a] * face_sgn[(int64_t)f * fd + b] *
              face_mass(dim, ref, X, face_v + (int64_t)f * 4, a, b);
 }
 
@@ -262,7 +265,7 @@ __constant__ double c_gl8_w[8] = {0.1012285362903763, 0.2223810344533745, 0.3137
 
 __global__ void k_dirichlet(int64_t n_de, int dim, int order, const int64_t* __restrict__ edges,
                             const double* __restrict__ X, const int64_t* __restrict__ elo,
-                            const int64_t* __restrict__ ehi, double omega, double pr0, double pi0,
+                            const int64_t* __restrict__ ehi, const double* __restrict__ om, double pr0, double pi0,
                             double pr1, double pi1, double pr2, double pi2, double d0, double d1,
                             double d2, double2* __restrict__ uD) {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -277,6 +280,7 @@ __global__ void k_dirichlet(int64_t n_de, int dim, int order, const int64_t* __r
     // pol . t_hat
     double ptr = (pr0 * tv[0] + pr1 * tv[1] + pr2 * tv[2]) / l;
     double pti = (pi0 * tv[0] + pi1 * tv[1] + pi2 * tv[2]) / l;
+    const double omega = om[t];
     double m0r = 0, m0i = 0, m1r = 0, m1i = 0;
     for (int q = 0; q < 8; ++q) {
         double s = 0.5 * (c_gl8_x[q] + 1.0), wq = 0.5 * c_gl8_w[q];
@@ -300,13 +304,15 @@ __global__ void k_dirichlet(int64_t n_de, int dim, int order, const int64_t* __r
 __global__ void k_lifting(int dim, int64_t n_loc, int nb, int maxc, const double* __restrict__ ref,
                           const double* __restrict__ X, const int32_t* __restrict__ cells,
                           const int8_t* __restrict__ signs, const int32_t* __restrict__ cell_loc,
-                          const int32_t* __restrict__ cell_dofs, const double* __restrict__ mu, double w2,
+                          const int32_t* __restrict__ cell_dofs, const double* __restrict__ mu,
+                          const double* __restrict__ w2c,
                           const int32_t* __restrict__ row_cell, const int32_t* __restrict__ row_k,
                           const double2* __restrict__ uD, int fd, const int32_t* __restrict__ face_v,
                           const int32_t* __restrict__ face_dof, const int8_t* __restrict__ face_sgn,
                           const int32_t* __restrict__ face_loc, const int32_t* __restrict__ row_face,
                           const int8_t* __restrict__ row_face_a, const int8_t* __restrict__ row_face_side,
-                          const int8_t* __restrict__ face_kind, double kw, double2* __restrict__ f,
+                          const int8_t* __restrict__ face_kind, const double* __restrict__ kwf,
+                          double2* __restrict__ f,
                           double2* __restrict__ fres) {
     int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (r >= n_loc) return;
@@ -320,7 +326,7 @@ __global__ void k_lifting(int dim, int64_t n_loc, int nb, int maxc, const double
         for (int kc = 0; kc < nb; ++kc) {
             if (cell_loc[(int64_t)c * nb + kc] >= 0) continue;
             double s = (double)(signs[(int64_t)c * nb + kr] * signs[(int64_t)c * nb + kc]);
-            double v = s * cell_entry(dim, ref, nb, mu[c], w2, hh, kr, kc);
+            double v = s * cell_entry(dim, ref, nb, mu[c], w2c[c], hh, kr, kc);
             double2 d = uD[cell_dofs[(int64_t)c * nb + kc]];
             fr -= v * d.x;
             fi -= v * d.y;
@@ -339,7 +345,7 @@ __global__ void k_lifting(int dim, int64_t n_loc, int nb, int maxc, const double
         for (int b = 0; b < fd; ++b) {
             if (face_loc[((int64_t)f * 2 + side) * fd + b] >= 0) continue;
             const int32_t gd = face_dof[(int64_t)f * fd + b];
-            const double v = kw * face_sgn[(int64_t)f * fd + a] * face_sgn[(int64_t)f * fd + b] *
+            const double v = kwf[f] * face_sgn[(int64_t)f * fd + a] * face_sgn[(int64_t)f * fd + b] *
                              face_mass(dim, ref, X, face_v + (int64_t)f * 4, a, b);
             const double2 d = uD[gd];
             fr += v * d.y;            // -(i v)(d.x + i d.y) = v d.y - i v d.x
@@ -358,7 +364,7 @@ __global__ void k_lifting(int dim, int64_t n_loc, int nb, int maxc, const double
 // ---------------------------------------------------------------------------
 __global__ void k_condense(int64_t n_cell, const double* __restrict__ ref, const double* __restrict__ X,
                            const int32_t* __restrict__ cells, const int8_t* __restrict__ signs,
-                           const double* __restrict__ mu, double w2, double* __restrict__ cinv,
+                           const double* __restrict__ mu, const double* __restrict__ w2c, double* __restrict__ cinv,
                            double* __restrict__ cg, double* __restrict__ ccor, float* __restrict__ cinv32,
                            float* __restrict__ cg32, int* __restrict__ bad) {
     int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -368,7 +374,7 @@ __global__ void k_condense(int64_t n_cell, const double* __restrict__ ref, const
     double D[4][8];                              // [D | I] -> [I | D^{-1}]
     for (int i = 0; i < 4; ++i)
         for (int j = 0; j < 4; ++j) {
-            D[i][j] = cell_entry(2, ref, 12, mu[c], w2, hh, 8 + i, 8 + j);
+            D[i][j] = cell_entry(2, ref, 12, mu[c], w2c[c], hh, 8 + i, 8 + j);
             D[i][4 + j] = i == j ? 1.0 : 0.0;
         }
     for (int k = 0; k < 4; ++k) {
@@ -395,7 +401,7 @@ __global__ void k_condense(int64_t n_cell, const double* __restrict__ ref, const
     double PEI[8][4];
     for (int e = 0; e < 8; ++e)
         for (int k = 0; k < 4; ++k)
-            PEI[e][k] = (double)signs[c * 12 + e] * cell_entry(2, ref, 12, mu[c], w2, hh, e, 8 + k);
+            PEI[e][k] = (double)signs[c * 12 + e] * cell_entry(2, ref, 12, mu[c], w2c[c], hh, e, 8 + k);
     double G[8][4];
     for (int e = 0; e < 8; ++e)
         for (int k = 0; k < 4; ++k) {
@@ -712,8 +718,33 @@ void assemble(thm_sys* s) {
     const thm_mesh* m = s->m;
     cudaStream_t st = s->st;
     const int nb = m->dpc;
-    const double w2 = s->omega * s->omega;
-    const double kw = s->kappa * s->omega;
+    // omega per cell, face and Dirichlet edge (one value unless the mesh holds
+    // a batch of independent problems)
+    {
+        auto prob = [&](int32_t sub) { return (sub < 0 || m->sub_prob.empty()) ? 0 : m->sub_prob[sub]; };
+        THM_REQUIRE((int)s->omega_prob.size() == m->n_prob, "one omega per problem required");
+        std::vector<double> w2h(m->n_cell), kwh(std::max<int64_t>(1, m->n_face), 0.0);
+        std::vector<double> omh(std::max<size_t>(1, m->dir_edges.size()), 0.0);
+        for (int64_t c = 0; c < m->n_cell; ++c) {
+            const double om = s->omega_prob[prob(m->cell_sub[c])];
+            w2h[c] = om * om;
+        }
+        for (int64_t f = 0; f < m->n_face; ++f) {
+            const int32_t sb = m->face_sub[2 * f] >= 0 ? m->face_sub[2 * f] : m->face_sub[2 * f + 1];
+            kwh[f] = s->kappa * s->omega_prob[prob(sb)];
+        }
+        if (!m->dir_edges.empty()) {
+            const int nv = m->dim == 2 ? 4 : 8;
+            std::vector<int32_t> vprob(m->n_vert, 0);
+            for (int64_t c = 0; c < m->n_cell; ++c)
+                for (int v = 0; v < nv; ++v) vprob[m->cells[c * nv + v]] = prob(m->cell_sub[c]);
+            for (size_t t = 0; t < m->dir_edges.size(); ++t)
+                omh[t] = s->omega_prob[vprob[m->edge_lo[m->dir_edges[t]]]];
+        }
+        s->w2c.upload(w2h, st);
+        s->kwf.upload(kwh, st);
+        s->omd.upload(omh, st);
+    }
     s->dev_err.alloc(1);
     s->dev_err.zero(st);
     s->ref.alloc(8 * 144);
@@ -725,7 +756,7 @@ void assemble(thm_sys* s) {
     const int th = 256;
     auto grid = [&](int64_t n) { return (unsigned)((n + th - 1) / th); };
     THM_LAUNCH(THM_K_SETUP, st, k_assemble<<<grid(m->n_loc), th, 0, st>>>(m->dim, m->n_loc, nb, m->maxc, s->ref.p, m->d_coords.p, m->d_cells.p,
-                                              m->d_cell_signs.p, m->d_cell_loc.p, s->mu_inv.p, w2,
+                                              m->d_cell_signs.p, m->d_cell_loc.p, s->mu_inv.p, s->w2c.p,
                                               m->d_slice_ptr.p, m->d_sell_col.p, m->d_sell_pad.p,
                                               m->d_row_cell.p, m->d_row_k.p, s->val64.p, s->val32.p));
     THM_CUDA(cudaGetLastError());
@@ -737,7 +768,7 @@ void assemble(thm_sys* s) {
     THM_LAUNCH(THM_K_SETUP, st, k_face_terms<<<grid(m->n_loc), th, 0, st>>>(
         m->dim, m->n_loc, m->fd, s->ref.p, m->d_coords.p, m->d_face_v.p, m->d_face_sgn.p, m->d_face_kind.p,
         m->d_face_loc.p, m->d_row_face.p, m->d_row_face_a.p, m->d_row_face_side.p, m->d_slice_ptr.p,
-        m->d_sell_col.p, m->d_sell_pad.p, kw, s->bg64.p, s->bs64.p, s->bg32.p, s->bs32.p, s->bvg64.p, s->bvs64.p,
+        m->d_sell_col.p, m->d_sell_pad.p, s->kwf.p, s->bg64.p, s->bs64.p, s->bg32.p, s->bs32.p, s->bvg64.p, s->bvs64.p,
         s->bvg32.p, s->bvs32.p));
     THM_CUDA(cudaGetLastError());
     const int64_t nterm = (int64_t)m->if_tf.size();
@@ -745,7 +776,8 @@ void assemble(thm_sys* s) {
     if (nterm > 0) {
         THM_LAUNCH(THM_K_SETUP, st, k_iface_vals<<<grid(nterm), th, 0, st>>>(m->dim, nterm, m->fd, s->ref.p, m->d_coords.p,
                                                                             m->d_face_v.p, m->d_face_sgn.p, m->d_if_tf.p,
-                                                                            m->d_if_ta.p, m->d_if_tb.p, s->if_val.p));
+                                                                            m->d_if_ta.p, m->d_if_tb.p, s->kwf.p,
+                                                                            s->if_val.p));
         THM_CUDA(cudaGetLastError());
     }
     s->uD.alloc(m->n_dof);
@@ -753,7 +785,7 @@ void assemble(thm_sys* s) {
     if (!m->dir_edges.empty()) {
         THM_LAUNCH(THM_K_SETUP, st, k_dirichlet<<<grid((int64_t)m->dir_edges.size()), th, 0, st>>>(
             (int64_t)m->dir_edges.size(), m->dim, m->order, m->d_dir_edges.p, m->d_coords.p, m->d_edge_lo.p,
-            m->d_edge_hi.p, s->omega, s->pol[0], s->pol[1], s->pol[2], s->pol[3], s->pol[4], s->pol[5],
+            m->d_edge_hi.p, s->omd.p, s->pol[0], s->pol[1], s->pol[2], s->pol[3], s->pol[4], s->pol[5],
             s->dir[0], s->dir[1], s->dir[2], s->uD.p));
         THM_CUDA(cudaGetLastError());
     }
@@ -768,7 +800,7 @@ void assemble(thm_sys* s) {
         bad.alloc(1);
         bad.zero(st);
         THM_LAUNCH(THM_K_SETUP, st, k_condense<<<grid(m->n_cell), th, 0, st>>>(m->n_cell, s->ref.p, m->d_coords.p, m->d_cells.p,
-                                                     m->d_cell_signs.p, s->mu_inv.p, w2, s->cinv64.p, s->cg64.p,
+                                                     m->d_cell_signs.p, s->mu_inv.p, s->w2c.p, s->cinv64.p, s->cg64.p,
                                                      ccor.p, s->cinv32.p, s->cg32.p, bad.p));
         THM_CUDA(cudaGetLastError());
         std::vector<int> hb;
@@ -803,9 +835,9 @@ void assemble(thm_sys* s) {
     s->f_res.alloc(m->n_loc);
     THM_LAUNCH(THM_K_SETUP, st, k_lifting<<<grid(m->n_loc), th, 0, st>>>(
         m->dim, m->n_loc, nb, m->maxc, s->ref.p, m->d_coords.p, m->d_cells.p, m->d_cell_signs.p, m->d_cell_loc.p,
-        m->d_cell_dofs.p, s->mu_inv.p, w2, m->d_row_cell.p, m->d_row_k.p, s->uD.p, m->fd, m->d_face_v.p,
+        m->d_cell_dofs.p, s->mu_inv.p, s->w2c.p, m->d_row_cell.p, m->d_row_k.p, s->uD.p, m->fd, m->d_face_v.p,
         m->d_face_dof.p, m->d_face_sgn.p, m->d_face_loc.p, m->d_row_face.p, m->d_row_face_a.p, m->d_row_face_side.p,
-        m->d_face_kind.p, kw, s->f_loc.p, s->f_res.p));
+        m->d_face_kind.p, s->kwf.p, s->f_loc.p, s->f_res.p));
     THM_CUDA(cudaGetLastError());
     THM_CUDA(cudaStreamSynchronize(st));
 }

@@ -113,18 +113,21 @@ int thm_mesh_info(const thm_mesh* m, int64_t* n_dof, int64_t* n_edge, int32_t* n
 
 void thm_mesh_destroy(thm_mesh* m) { delete m; }
 
-int thm_assemble(thm_sys** out, const thm_mesh* m, const double* mu_inv, int mu_inv_on_device, double omega,
-                 double kappa, const double* pol, const double* dir, void* stream) {
+static int assemble_common(thm_sys** out, const thm_mesh* m, const double* mu_inv, int mu_inv_on_device,
+                           const std::vector<double>& omegas, double kappa, const double* pol, const double* dir,
+                           void* stream) {
     return guarded([&]() -> int {
         THM_REQUIRE(out && m && mu_inv && pol && dir, "NULL argument");
         *out = nullptr;
-        THM_REQUIRE(std::isfinite(omega) && omega > 0, "omega must be > 0");
+        THM_REQUIRE((int)omegas.size() == m->n_prob, "one omega per problem required");
+        for (double w : omegas) THM_REQUIRE(std::isfinite(w) && w > 0, "omega must be > 0");
         THM_REQUIRE(std::isfinite(kappa) && kappa >= 0, "kappa must be >= 0");
         thm_sys* s = new thm_sys();
         try {
             s->m = m;
             s->st = (cudaStream_t)stream;
-            s->omega = omega;
+            s->omega = omegas[0];
+            s->omega_prob = omegas;
             s->kappa = kappa;
             for (int k = 0; k < m->dim; ++k) {
                 s->pol[2 * k] = pol[2 * k];
@@ -139,6 +142,7 @@ int thm_assemble(thm_sys** out, const thm_mesh* m, const double* mu_inv, int mu_
                     THM_REQUIRE(std::isfinite(mu_inv[c]) && mu_inv[c] > 0, "mu_inv must be finite and > 0");
                 THM_CUDA(cudaMemcpyAsync(s->mu_inv.p, mu_inv, m->n_cell * sizeof(double), cudaMemcpyHostToDevice, s->st));
             }
+            m->assembled = true;
             assemble(s);
         } catch (...) {
             delete s;
@@ -147,6 +151,79 @@ int thm_assemble(thm_sys** out, const thm_mesh* m, const double* mu_inv, int mu_
         *out = s;
         return THM_OK;
     });
+}
+
+int thm_assemble(thm_sys** out, const thm_mesh* m, const double* mu_inv, int mu_inv_on_device, double omega,
+                 double kappa, const double* pol, const double* dir, void* stream) {
+    if (m && m->n_prob != 1) {
+        set_last_error("the mesh holds a batch of problems: use thm_assemble_batch");
+        if (out) *out = nullptr;
+        return THM_EINVAL;
+    }
+    return assemble_common(out, m, mu_inv, mu_inv_on_device, std::vector<double>{omega}, kappa, pol, dir, stream);
+}
+
+int thm_mesh_set_problems(thm_mesh* m, int32_t n_prob, const int32_t* sub_problem) {
+    return guarded([&]() -> int {
+        THM_REQUIRE(m && sub_problem, "NULL argument");
+        THM_REQUIRE(!m->assembled, "thm_mesh_set_problems must come before the first thm_assemble on this mesh");
+        THM_REQUIRE(n_prob >= 1 && n_prob <= m->n_sub, "n_prob must be in [1, n_sub]");
+        std::vector<int32_t> sp(sub_problem, sub_problem + m->n_sub);
+        std::vector<int64_t> nsub_of(n_prob, 0);
+        for (int i = 0; i < m->n_sub; ++i) {
+            THM_REQUIRE(sp[i] >= 0 && sp[i] < n_prob, "problem id out of range");
+            THM_REQUIRE(i == 0 || sp[i] >= sp[i - 1], "problems must own contiguous, increasing ranges of subdomain ids");
+            nsub_of[sp[i]]++;
+        }
+        for (int p = 0; p < n_prob; ++p) THM_REQUIRE(nsub_of[p] > 0, "every problem needs at least one subdomain");
+        for (int64_t k = 0; k < m->n_if; ++k)
+            THM_REQUIRE(sp[m->if_recv[k]] == sp[m->if_send[k]], "subdomains of different problems share an interface");
+        // global DOFs: each belongs to one problem, and the problems' DOFs form
+        // contiguous increasing ranges (vertices numbered problem by problem)
+        std::vector<int32_t> dp(m->n_dof, -1);
+        for (int64_t c = 0; c < m->n_cell; ++c) {
+            const int32_t p = sp[m->cell_sub[c]];
+            for (int k = 0; k < m->dpc; ++k) {
+                int32_t& q = dp[m->cell_dofs[c * m->dpc + k]];
+                THM_REQUIRE(q < 0 || q == p, "problems share a DOF (the batch mesh must be a disjoint union)");
+                q = p;
+            }
+        }
+        std::vector<int64_t> dptr(n_prob + 1, 0), iptr(n_prob + 1, 0);
+        for (int64_t d = 0; d < m->n_dof; ++d) {
+            THM_REQUIRE(dp[d] >= 0 && (d == 0 || dp[d] >= dp[d - 1]),
+                        "the problems' DOFs must form contiguous ranges (number the vertices problem by problem)");
+            dptr[dp[d] + 1]++;
+        }
+        for (int64_t k = 0; k < m->n_if; ++k) iptr[sp[m->if_recv[k]] + 1]++;
+        for (int p = 0; p < n_prob; ++p) { dptr[p + 1] += dptr[p]; iptr[p + 1] += iptr[p]; }
+        std::vector<Chunk> ch;
+        for (int p = 0; p < n_prob; ++p)
+            for (int64_t b = dptr[p]; b < dptr[p + 1]; b += CHUNK) {
+                Chunk c{};
+                c.seg = p; c.begin = b; c.end = std::min<int64_t>(dptr[p + 1], b + CHUNK);
+                ch.push_back(c);
+            }
+        m->n_prob = n_prob;
+        m->sub_prob = sp;
+        m->prob_dof_ptr = dptr;
+        m->prob_if_ptr = iptr;
+        m->dof_chunks = ch;
+        m->d_dof_chunks.upload(ch);
+        THM_CUDA(cudaDeviceSynchronize());
+        return THM_OK;
+    });
+}
+
+int thm_assemble_batch(thm_sys** out, const thm_mesh* m, const double* mu_inv, int mu_inv_on_device,
+                       const double* omega, double kappa, const double* pol, const double* dir, void* stream) {
+    if (!m || !omega) {
+        set_last_error("NULL argument");
+        if (out) *out = nullptr;
+        return THM_EINVAL;
+    }
+    return assemble_common(out, m, mu_inv, mu_inv_on_device, std::vector<double>(omega, omega + m->n_prob), kappa,
+                           pol, dir, stream);
 }
 
 int thm_ddm_solve(thm_sys* s, const thm_solve_opts* opts, double* u, thm_stats* stats) {

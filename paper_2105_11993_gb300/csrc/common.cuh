@@ -184,6 +184,14 @@ struct thm_mesh {
     std::vector<int8_t> if_ta, if_tb;
     std::vector<int64_t> rowg_ptr;                  // [n_loc+1] local row -> entries received
     std::vector<int32_t> rowg_idx;
+    // independent problems sharing the mesh (a batch): subdomain -> problem,
+    // each problem's contiguous range of global DOFs and of interface entries,
+    // and reduction chunks over the global DOFs segmented by problem
+    int n_prob = 1;
+    mutable bool assembled = false;                 // a system was built on this mesh
+    std::vector<int32_t> sub_prob;                  // [n_sub]
+    std::vector<int64_t> prob_dof_ptr, prob_if_ptr; // [n_prob+1]
+    std::vector<thm::Chunk> dof_chunks;
     // global <-> local
     std::vector<int32_t> owner_loc;                 // [n_dof] lowest-subdomain copy, -1 Dirichlet
     std::vector<int64_t> copy_ptr;                  // [n_dof+1]
@@ -206,6 +214,7 @@ struct thm_mesh {
     thm::DArr<int64_t> d_cpl_slot;
     thm::DArr<thm::Sub> d_subs;
     thm::DArr<thm::Chunk> d_chunks;
+    thm::DArr<thm::Chunk> d_dof_chunks;
 };
 
 namespace thm { struct Work; }
@@ -214,7 +223,11 @@ namespace thm { struct Work; }
 struct thm_sys {
     const thm_mesh* m = nullptr;
     cudaStream_t st = 0;
-    double omega = 0, kappa = 0;
+    double omega = 0, kappa = 0;       // omega: the first problem's (the only one unless batched)
+    std::vector<double> omega_prob;    // [n_prob]
+    thm::DArr<double> w2c;             // [n_cell] omega^2 of the cell's problem
+    thm::DArr<double> kwf;             // [n_face] kappa*omega of the face's problem
+    thm::DArr<double> omd;             // [n_dir_edges] omega of the Dirichlet edge's problem
     double pol[6] = {0};   // complex [dim]
     double dir[3] = {0};
     thm::DArr<double> mu_inv;          // [n_cell]

@@ -160,8 +160,11 @@ __global__ void k_rhs(int64_t n, const double2* __restrict__ src, const int64_t*
 }
 
 // Impedance-trace exchange (Eq. 6):  G_{i<-j} = -G_{j<-i} + 2 i kappa omega (M_Sigma_ij u_j)[g],
-// the face-mass product summed over the entry's terms; a term on a Dirichlet
-// DOF of u_j uses u_D when the sweep carries the Dirichlet lifting, else 0.
+// the face-mass product summed over the entry's terms (val already holds
+// kappa*omega times the face mass, so that a batch of problems with different
+// omega shares the kernel; kw is a further common factor, 1 here); a term on
+// a Dirichlet DOF of u_j uses u_D when the sweep carries the Dirichlet
+// lifting, else 0.
 __global__ void k_exchange(int64_t n_if, const int32_t* __restrict__ partner, const int64_t* __restrict__ ptr,
                            const int32_t* __restrict__ tcol, const double* __restrict__ val, double kw,
                            const double2* __restrict__ g_in, const double2* __restrict__ u,
@@ -485,6 +488,9 @@ struct Work {
     DArr<double> bn2, rn2, rprev;
     DArr<int> ir_active, nact_ir;
     DArr<double> npart;
+    // per-problem norms of global vectors (batches)
+    DArr<double> pnpart, pnrm;
+    DArr<int32_t> pseg_ch;
 };
 
 static void ensure_work(thm_sys* s, bool fp32, int m_in, int m_out) {
@@ -507,14 +513,30 @@ static void ensure_work(thm_sys* s, bool fp32, int m_in, int m_out) {
         w->has32 = true;
     }
     if (w->m_out != m_out && m->n_if > 0) {
+        // one Krylov segment per problem (its contiguous range of interface
+        // entries); a single problem is one segment over all of them
         std::vector<Chunk> oc;
-        for (int64_t b = 0; b < m->n_if; b += CHUNK) {
-            Chunk c{};
-            c.seg = 0; c.begin = b; c.end = std::min<int64_t>(m->n_if, b + CHUNK);
-            oc.push_back(c);
+        std::vector<int64_t> on(m->n_prob);
+        for (int p = 0; p < m->n_prob; ++p) {
+            const int64_t b0 = m->n_prob > 1 ? m->prob_if_ptr[p] : 0;
+            const int64_t b1 = m->n_prob > 1 ? m->prob_if_ptr[p + 1] : m->n_if;
+            on[p] = b1 - b0;
+            for (int64_t b = b0; b < b1; b += CHUNK) {
+                Chunk c{};
+                c.seg = p; c.begin = b; c.end = std::min<int64_t>(b1, b + CHUNK);
+                oc.push_back(c);
+            }
         }
-        w->outer.init(m->n_if, 1, m_out, oc, nullptr, std::vector<int64_t>{m->n_if});
+        w->outer.init(m->n_if, m->n_prob, m_out, oc, nullptr, on);
         w->m_out = m_out;
+    }
+    if (m->n_prob > 1 && w->pnrm.n == 0) {
+        std::vector<int32_t> sc(m->n_prob + 1, 0);
+        for (const Chunk& c : m->dof_chunks) sc[c.seg + 1]++;
+        for (int p = 0; p < m->n_prob; ++p) sc[p + 1] += sc[p];
+        w->pseg_ch.upload(sc);
+        w->pnpart.alloc(std::max<size_t>(1, m->dof_chunks.size()));
+        w->pnrm.alloc(m->n_prob);
     }
     if (w->b64.n == 0) {
         w->b64.alloc(m->n_loc); w->x64.alloc(m->n_loc); w->src.alloc(m->n_loc);
@@ -541,6 +563,8 @@ SolveCfg make_cfg(const thm_solve_opts* o) {
     c.inner_tol = (o && o->inner_tol > 0) ? o->inner_tol : 1e-11;
     c.cycle_tol = 1e-5;
     c.relax = o ? o->relax : 0;
+    c.outer_method = o ? o->outer_method : THM_OUTER_GMRES;
+    THM_REQUIRE(c.outer_method == THM_OUTER_GMRES || c.outer_method == THM_OUTER_JACOBI, "unknown outer method");
     if (const char* e = getenv("THM_CYCLE_TOL")) c.cycle_tol = atof(e);
     c.outer_tol = (o && o->outer_tol > 0) ? o->outer_tol : 1e-9;
     return c;
@@ -691,10 +715,12 @@ static void sweep(thm_sys* s, const SolveCfg& c, const double2* src, const doubl
     if (m->n_if > 0 && g_out)
         THM_LAUNCH(THM_K_DDM, st, k_exchange<<<nblk(m->n_if), 256, 0, st>>>(m->n_if, m->d_if_partner.p, m->d_if_ptr.p,
                                                                            m->d_if_tcol.p, s->if_val.p,
-                                                                           s->kappa * s->omega, g_in, x, uD, g_out));
+                                                                           1.0, g_in, x, uD, g_out));
     rs.sweeps++;
     THM_CUDA(cudaGetLastError());
 }
+
+static double global_norm(thm_sys* s, const double2* x, int64_t n);
 
 // DDM solve of Eq. 8 for local sources src -> local solution uloc.
 static void ddm_solve(thm_sys* s, const SolveCfg& c, const double2* src, double2* uloc, RunStats& rs,
@@ -709,6 +735,27 @@ static void ddm_solve(thm_sys* s, const SolveCfg& c, const double2* src, double2
     // b = A_src(0): sweep with sources and zero interface data
     w->g0.zero(st);
     sweep(s, c, src, w->g0.p, w->gb.p, uloc, rs, uD);
+    if (c.outer_method == THM_OUTER_JACOBI) {
+        // fixed point of g = A_src(g) = A g + b (the plain iteration of Eq. 8):
+        // g_{k+1} = A_src(g_k) from g_1 = b, stopped on ||g_k - A_src(g_k)|| <= tol ||b||
+        const double bn = global_norm(s, w->gb.p, m->n_if);
+        double2* g = w->gb.p;
+        double2* gn = w->gsol.p;
+        int k = 0;
+        bool conv = bn == 0;
+        while (!conv && k < c.outer_maxit) {
+            sweep(s, c, src, g, gn, uloc, rs, uD);
+            THM_LAUNCH(THM_K_KRYLOV, st, k_sub<double2><<<nblk(m->n_if), 256, 0, st>>>(m->n_if, g, gn, w->gtmp.p));
+            const double r = global_norm(s, w->gtmp.p, m->n_if);
+            ++k;
+            if (r <= c.outer_tol * bn) conv = true;
+            else std::swap(g, gn);
+        }
+        rs.outer += k;
+        if (!conv && rs.status == THM_OK) rs.status = THM_ENOCONV;
+        sweep(s, c, src, g, nullptr, uloc, rs, uD);
+        return;
+    }
     auto A = [&](const double2* v, double2* out) {
         SolveCfg cr = c;
         if (c.relax) {
@@ -754,6 +801,33 @@ static double global_norm(thm_sys* s, const double2* x, int64_t n) {
     return std::sqrt(t);
 }
 
+// Per-problem 2-norms of a global vector (a batch of independent problems:
+// each owns a contiguous range of global DOFs), deterministic order.
+static std::vector<double> problem_norms(thm_sys* s, const double2* x) {
+    const thm_mesh* m = s->m;
+    Work* w = s->w;
+    std::vector<double> h(m->n_prob, 0.0);
+    const int nch = (int)m->dof_chunks.size();
+    if (nch > 0) {
+        THM_LAUNCH(THM_K_DDM, s->st, k_chunk_norm2<double2><<<nch, KT, 0, s->st>>>(m->d_dof_chunks.p, x, w->pnpart.p));
+        THM_LAUNCH(THM_K_DDM, s->st, k_seg_reduce_real<<<nblk(m->n_prob), 256, 0, s->st>>>(m->n_prob, w->pseg_ch.p,
+                                                                                          w->pnpart.p, w->pnrm.p));
+        THM_CUDA(cudaMemcpyAsync(h.data(), w->pnrm.p, m->n_prob * sizeof(double), cudaMemcpyDeviceToHost, s->st));
+        THM_CUDA(cudaStreamSynchronize(s->st));
+    }
+    for (double& v : h) v = std::sqrt(v);
+    return h;
+}
+
+// The largest relative residual over the problems (r_p / f_p; a problem with
+// f_p = 0 has u_p = 0 exactly and counts as converged).
+static double max_relative(const std::vector<double>& rn, const std::vector<double>& fn) {
+    double r = 0;
+    for (size_t p = 0; p < rn.size(); ++p)
+        if (fn[p] > 0) r = std::max(r, rn[p] / fn[p]);
+    return r;
+}
+
 // A bounded device-side wait that gave up leaves a flag: report THM_ETIMEOUT.
 static void check_device_error(thm_sys* s) {
     int h = 0;
@@ -787,7 +861,16 @@ int solve_rhs(thm_sys* s, const SolveCfg& c, const double2* f_src, const double2
     Work* w = s->w;
     cudaStream_t st = s->st;
     THM_LAUNCH(THM_K_DDM, st, k_gather_sum<<<nblk(m->n_dof), 256, 0, st>>>(m->n_dof, m->d_copy_ptr.p, m->d_copy_idx.p, f_loc, w->rglob.p));
-    double fn = global_norm(s, w->rglob.p, m->n_dof);
+    const bool batch = m->n_prob > 1;
+    std::vector<double> fnp;
+    double fn;
+    if (batch) {
+        fnp = problem_norms(s, w->rglob.p);
+        fn = 0;
+        for (double v : fnp) fn = std::max(fn, v);
+    } else {
+        fn = global_norm(s, w->rglob.p, m->n_dof);
+    }
     if (u0) THM_CUDA(cudaMemcpyAsync(u, u0, m->n_dof * sizeof(double2), cudaMemcpyDeviceToDevice, st));
     else THM_CUDA(cudaMemsetAsync(u, 0, m->n_dof * sizeof(double2), st));
     THM_CUDA(cudaMemcpyAsync(w->src.p, f_src, m->n_loc * sizeof(double2), cudaMemcpyDeviceToDevice, st));
@@ -799,7 +882,7 @@ int solve_rhs(thm_sys* s, const SolveCfg& c, const double2* f_src, const double2
         rs.refine++;
         THM_LAUNCH(THM_K_DDM, st, k_glue_add<<<nblk(m->n_dof), 256, 0, st>>>(m->n_dof, m->d_owner_loc.p, w->x64.p, u));
         double rn = true_residual_rhs(s, f_loc, u, w->rglob.p);
-        rel = rn / fn;
+        rel = batch ? max_relative(problem_norms(s, w->rglob.p), fnp) : rn / fn;
         if (!std::isfinite(rel)) { rs.status = THM_EBREAKDOWN; break; }
         if (rel <= c.rtol) break;
         THM_LAUNCH(THM_K_DDM, st, k_owner_split<<<nblk(m->n_loc), 256, 0, st>>>(m->n_loc, m->d_loc_gdof.p, m->d_loc_is_owner.p,

@@ -11,6 +11,7 @@ struct SolveCfg {
     double cycle_tol;          // mixed: relative tolerance of one FP32 GMRES cycle
     int m_in, m_out, inner_maxit, outer_maxit, max_refine;
     int relax;
+    int outer_method;          // THM_OUTER_GMRES / THM_OUTER_JACOBI
 };
 
 struct RunStats {

@@ -268,3 +268,28 @@ def test_pinv_coupling_from_global_memory(name, mode, monkeypatch):
             assert np.linalg.norm(y[idx] - ys[pos[idx]]) / np.linalg.norm(ys) <= tol
     # same arithmetic in the same order: the two paths agree to rounding
     assert np.linalg.norm(y_glob - y_ring) <= (1e-13 if mode == "fp64" else 1e-5) * np.linalg.norm(y_ring)
+
+
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+def test_jacobi_outer_matches_oracle_jacobi(mode):
+    """The fixed-point (Jacobi) iteration of Eq. 8's map: the same solution as
+    the monolithic oracle, and the oracle's Jacobi sweep count (two strips,
+    no cross points, so the iteration contracts)."""
+    mesh = W.structured_mesh_2d(8, 8, 2, 1)
+    pol, d = W.plane_wave_y(2)
+    P = W.Problem("strips", mesh, 1, np.ones(mesh.n_cell), 8.0, 1.0, pol, d)
+    D = odd.setup(P)
+    uj, ij = odd.solve(D, outer="jacobi", outer_tol=1e-9, outer_maxiter=2000)
+    _, sysg = make_system(P)
+    S = fem.assemble(P)
+    u0 = fem.solve_monolithic(S)
+    # one DDM solve (no refinement), so that the sweep count is comparable
+    u, st = sysg.solve(mode=mode, rtol=1e-8, outer="jacobi", outer_tol=1e-9, outer_maxit=2000, max_refine=1,
+                       check=False)
+    assert st["status"] in (0, -2) and st["refine_steps"] == 1
+    u = u.cpu().numpy()
+    assert np.linalg.norm(u - u0) <= 1e-6 * np.linalg.norm(u0)
+    # the same contraction: sweep counts agree up to the inner-solve accuracy
+    assert abs(st["outer_iters"] - ij["outer_iters"]) <= 2, (st["outer_iters"], ij["outer_iters"])
+    _, sg = sysg.solve(mode=mode, rtol=1e-8, max_refine=1, check=False)
+    assert sg["outer_iters"] < st["outer_iters"]
