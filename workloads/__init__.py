@@ -162,7 +162,7 @@ def structured_mesh_2d(nx: int, ny: int, sx: int = 1, sy: int = 1, *,
     relabel:         random permutation of global vertex ids.
     rotate_cells:    each cell listed in a random one of its 8 tensor orders.
     """
-    assert nx % sx == 0 and ny % sy == 0
+    assert 1 <= sx <= nx and 1 <= sy <= ny
     rng = Rng(seed_key, nx, ny, sx, sy)
     I, J = np.meshgrid(np.arange(nx + 1), np.arange(ny + 1), indexing="xy")
     coords = np.stack([I.ravel() * (lx / nx), J.ravel() * (ly / ny)], 1).astype(np.float64)
@@ -170,7 +170,9 @@ def structured_mesh_2d(nx: int, ny: int, sx: int = 1, sy: int = 1, *,
     ci, cj = np.meshgrid(np.arange(nx), np.arange(ny), indexing="xy")
     ci = ci.ravel(); cj = cj.ravel()
     cells = np.stack([vid(ci, cj), vid(ci + 1, cj), vid(ci, cj + 1), vid(ci + 1, cj + 1)], 1).astype(np.int64)
-    cell_sub = ((cj // (ny // sy)) * sx + (ci // (nx // sx))).astype(np.int32)
+    # balanced blocks: cell column ci is in block floor(ci * sx / nx) (equal
+    # blocks when sx divides nx, otherwise sizes differ by at most one cell)
+    cell_sub = ((cj * sy // ny) * sx + (ci * sx // nx)).astype(np.int32)
 
     faces, tags = [], []
     def side(pairs, tag):
@@ -361,7 +363,8 @@ def config(name: str) -> Problem:
 
 def batch_problems(count: int = 512, key: str = "batch512"):
     """Independent 2D order-1 problems: side U{16..128}, omega U[2pi,32pi],
-    kappa=1, mu^{-1} lognormal(0,0.3), s=ceil(n/32) subdomains per side."""
+    kappa=1, mu^{-1} lognormal(0,0.3), s=ceil(n/32) subdomains per side
+    (balanced, possibly unequal blocks)."""
     rng = Rng(key)
     sides = rng.integers(count, 16, 128)
     omegas = rng.uniform(count, 2 * math.pi, 32 * math.pi)
@@ -369,8 +372,6 @@ def batch_problems(count: int = 512, key: str = "batch512"):
     for p in range(count):
         n = int(sides[p])
         s = int(math.ceil(n / 32))
-        while n % s:
-            s += 1
         mesh = structured_mesh_2d(n, n, s, s)
         mu = mu_inv_lognormal(mesh.n_cell, 0.3, f"{key}/{p}")
         pol, d = plane_wave_y(2)
