@@ -53,6 +53,9 @@ def parse():
     p.add_argument("--ref-subdomains", type=int, default=4, help="subdomains per reference sample")
     p.add_argument("--e2e-steps", type=int, default=1)
     p.add_argument("--relax", type=int, default=1, help="inexact-Krylov relaxation of the subdomain tolerance")
+    p.add_argument("--batch", type=int, default=0, metavar="K",
+                   help="instead of the headline workload: the first K problems of the 512-problem batch "
+                        "workload solved as one batch and, for comparison, one by one")
     p.add_argument("--ncu-sweep", action="store_true",
                    help="assemble the workload and run two DDM sweeps only (bounded case for ncu captures)")
     return p.parse_args()
@@ -263,12 +266,68 @@ def bytes_per_launch(sysg, mode, cls):
     return thm.algorithmic_bytes(sysg, mode, cls)
 
 
+def batch_arm(args):
+    """Batched solve of K independent 2-D problems (sides U{16..128}, omega
+    U[2pi,32pi], kappa=1, lognormal mu^{-1}, ceil(n/32)^2 subdomains) against
+    a loop of the plain solver over the same problems.  Both stop at rtol 1e-8
+    or at the same iteration caps (300 interface steps, 3 refinements); the
+    coarsest draws (about one cell per wavelength) may not converge, which the
+    line reports."""
+    import numpy as np
+    import torch
+    import paper_2105_11993_gb300 as thm
+    import workloads as W
+    from paper_2105_11993_gb300 import build
+    build.build()
+    probs = W.batch_problems(512)[:args.batch]
+    kw = dict(mode=args.mode, rtol=1e-8, relax=args.relax, outer_maxit=300, max_refine=3, check=False)
+    # timed: assembly, factorisation and solve (time to solution); the
+    # meshes (host-side numbering) are built beforehand for both arms
+    mesh, _ = thm.Mesh.batch([P.mesh for P in probs], 1)
+    mu = np.concatenate([P.mu_inv for P in probs])
+    om = np.array([P.omega for P in probs])
+    meshes = [thm.Mesh.from_workload(P.mesh, 1) for P in probs]
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    sb = thm.System(mesh, mu, om, 1.0, probs[0].pol, probs[0].direction)
+    _, stb = sb.solve(**kw)
+    torch.cuda.synchronize()
+    tb = time.perf_counter() - t
+    tl, dil, conv = 0.0, 0, 0
+    for P, m1 in zip(probs, meshes):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        s1 = thm.System(m1, P.mu_inv, P.omega, 1.0, P.pol, P.direction)
+        _, st1 = s1.solve(**kw)
+        torch.cuda.synchronize()
+        tl += time.perf_counter() - t
+        dil += st1["dof_iters"]
+        conv += st1["status"] == 0
+    ppw = [2 * math.pi * P.mesh.shape[0] / P.omega for P in probs]
+    line = {"metric": "batched DDM-GMRES solve of independent problems vs a loop of single solves",
+            "value": stb["dof_iters"] / tb, "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
+            "dtype": "f32 operator/preconditioner/inner Krylov + f64 refinement" if args.mode == "mixed" else "f64",
+            "data": "synthetic",
+            "config": {"workload": f"first {len(probs)} of the 512-problem batch (seed 20210525)",
+                       "n_dof": mesh.info()["n_dof"], "n_sub": mesh.info()["n_sub"],
+                       "cells_per_wavelength": [min(ppw), max(ppw)], "caps": "300 interface steps, 3 refinements"},
+            "batch": {"seconds": tb, "problems_per_s": len(probs) / tb, "status": stb["status"],
+                      "max_rel_residual": stb["rel_residual"], "outer_steps": stb["outer_iters"],
+                      "dof_iters": stb["dof_iters"]},
+            "loop": {"seconds": tl, "problems_per_s": len(probs) / tl, "converged": conv, "dof_iters": dil,
+                     "dof_iters_per_s": dil / tl},
+            "speedup_time": tl / tb}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return reference_arm(args)
     if args.ncu_sweep:
         return ncu_sweep(args)
+    if args.batch > 0:
+        return batch_arm(args)
     ws, rank, local = dist_env()
     import numpy as np
     import torch
