@@ -287,6 +287,8 @@ def batch_arm(args):
     mu = np.concatenate([P.mu_inv for P in probs])
     om = np.array([P.omega for P in probs])
     meshes = [thm.Mesh.from_workload(P.mesh, 1) for P in probs]
+    wp = W.square_problem(8, 2, 1, 5.0)              # warm-up: module loading, first launches
+    thm.System(thm.Mesh.from_workload(wp.mesh, 1), wp.mu_inv, wp.omega, 1.0, wp.pol, wp.direction).solve(**kw)
     torch.cuda.synchronize()
     t = time.perf_counter()
     sb = thm.System(mesh, mu, om, 1.0, probs[0].pol, probs[0].direction)
