@@ -445,7 +445,7 @@ struct Krylov {
             for (; checked < j && ks.status != THM_EBREAKDOWN; ++checked)
                 if (h_ring[2 * (checked % RING) + 1]) ks.status = THM_EBREAKDOWN;            THM_CUDA(cudaGetLastError());
             // x += M (V y)
-            THM_LAUNCH(THM_K_KRYLOV, st, k_backsolve<<<nblk(nseg), 64, 0, st>>>(nseg, m, Rm.p, gv.p, kused.p, y.p));
+            THM_LAUNCH(THM_K_KRYLOV, st, k_backsolve<<<nblk(nseg, 64), 64, 0, st>>>(nseg, m, Rm.p, gv.p, kused.p, y.p));
             if (flexible && M) {
                 // x += Z y: the preconditioned directions actually used by the Arnoldi process
                 THM_LAUNCH(THM_K_KRYLOV, st, k_chunk_combine<V><<<nch, KT, 0, st>>>(d_chunks, zbasis.p, n, kused.p, y.p, m, t.p));

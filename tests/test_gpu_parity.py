@@ -293,3 +293,18 @@ def test_jacobi_outer_matches_oracle_jacobi(mode):
     assert abs(st["outer_iters"] - ij["outer_iters"]) <= 2, (st["outer_iters"], ij["outer_iters"])
     _, sg = sysg.solve(mode=mode, rtol=1e-8, max_refine=1, check=False)
     assert sg["outer_iters"] < st["outer_iters"]
+
+
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+def test_more_than_64_subdomains(mode):
+    """81 subdomains: every per-segment kernel must cover segments beyond the
+    first block of threads (a launch sized for fewer segments than it has
+    leaves their solves empty)."""
+    P = W.square_problem(18, 9, 1, 9.0, mu_inv=W.mu_inv_lognormal(324, 0.3, "s81"))
+    _, sysg = make_system(P)
+    assert sysg.n_sub == 81
+    S = fem.assemble(P)
+    u0 = fem.solve_monolithic(S)
+    u, st = sysg.solve(mode=mode, rtol=1e-11 if mode == "fp64" else 1e-9)
+    u = u.cpu().numpy()
+    assert np.linalg.norm(u - u0) <= (1e-8 if mode == "fp64" else 1e-6) * np.linalg.norm(u0)
