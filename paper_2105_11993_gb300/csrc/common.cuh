@@ -260,6 +260,9 @@ struct thm_sys {
     thm::DArr<int32_t> tab_ai, tab_ci, tab_ei;
     thm::DArr<double> tab_av64, tab_cv64, tab_ev64;
     thm::DArr<float> tab_av32, tab_cv32, tab_ev32;
+    // W-tile size of the block-solve kernel picked by its autotuner ([0] FP64
+    // factors, [1] FP32), 0 until the first apply
+    mutable size_t bt_tile[2] = {0, 0};
     // solver workspace (allocated on first solve, see solve.cu)
     thm::Work* w = nullptr;
     ~thm_sys();

@@ -592,16 +592,16 @@ static void apply_T(const thm_sys* s, const F* val, const F* bg, const F* bs, in
 
 // Twisted block-tridiagonal solve, one 2-CTA cluster per subdomain.  The
 // coupling blocks get a small ring of their own; the W ring takes what the
-// rest of the layout leaves: tiles of about THM_BT_TILE_BYTES (default 48 KB;
-// fewer, larger bulk copies stream faster per SM) each, 2..16 slots.
+// rest of the layout leaves: tiles of about `target` bytes (fewer, larger bulk
+// copies stream faster per SM, more slots reach further ahead), 2..16 slots.
+struct BtCfg {
+    int rows = 0, ns = 0, cglob = 0, nvec = 0;
+    size_t slot = 0, cslot = 0, smem = 0;
+};
+
 template <class V, class F>
-static void apply_Pinv(const thm_sys* s, const F* fac, const F* cval, const int32_t* ai, const F* av,
-                       const int32_t* ci, const F* cv, const int32_t* ei, const F* ev, const V* x, V* y) {
-    const thm_mesh* m = s->m;
-    THM_REQUIRE(m->max_m <= BT_MAX_M, "level block larger than the block-solve kernel supports (" +
-                                          std::to_string(m->max_m) + " > " + std::to_string(BT_MAX_M) + ")");
-    static const size_t target = getenv("THM_BT_TILE_BYTES") ? (size_t)std::max(1024, atoi(getenv("THM_BT_TILE_BYTES")))
-                                                              : (size_t)49152;
+static BtCfg bt_config(const thm_mesh* m, size_t target) {
+    BtCfg c;
     const size_t cap = 227 * 1024 - 256;
     const size_t row_bytes = (size_t)bt_r4(m->max_m) * sizeof(F);
     const size_t cfull = bt_r16((size_t)(m->max_m + 1) * 4) + bt_r16((size_t)m->max_cnz * 4) +
@@ -609,35 +609,81 @@ static void apply_Pinv(const thm_sys* s, const F* fac, const F* cval, const int3
     // coupling blocks larger than 12 KB are read from global memory in place
     // (THM_BT_CPL_GLOBAL=1 forces that path, for tests)
     const char* force = getenv("THM_BT_CPL_GLOBAL");
-    const int cglob = (cfull > 12 * 1024 || (force && atoi(force) != 0)) ? 1 : 0;
-    const size_t cslot = cglob ? 16 : cfull;
+    c.cglob = (cfull > 12 * 1024 || (force && atoi(force) != 0)) ? 1 : 0;
+    c.cslot = c.cglob ? 16 : cfull;
     THM_REQUIRE(m->bt_nvec < INT32_MAX, "block-solve data too large");
-    const int nvec = (int)m->bt_nvec;
+    c.nvec = (int)m->bt_nvec;
     auto layout = [&](int ns, size_t slot) {
-        return bt_layout<V>(ns, (int)slot, (int)cslot, m->max_lev, nvec, m->max_m).total;
+        return bt_layout<V>(ns, (int)slot, (int)c.cslot, m->max_lev, c.nvec, m->max_m).total;
     };
     // the largest tile height (<= the target) that leaves room for at least 3 slots
-    int rows = (int)std::max<size_t>(1, target / row_bytes);
-    while (rows > 1 && layout(3, bt_r16((size_t)rows * row_bytes)) > cap) --rows;
-    const size_t slot = bt_r16((size_t)rows * row_bytes);
-    THM_REQUIRE(slot < (size_t)INT32_MAX, "block-solve tile too large");
-    int ns = 0;
-    for (int q = 16; q >= 2 && ns == 0; --q)
-        if (layout(q, slot) <= cap) ns = q;
-    THM_REQUIRE(ns >= 2, "subdomain too large for the shared-memory block solve (" +
-                             std::to_string(layout(0, 0)) + " bytes of vectors and level data, " +
-                             std::to_string(slot) + "-byte tiles)");
-    const size_t smem = layout(ns, slot);
+    c.rows = (int)std::max<size_t>(1, target / row_bytes);
+    while (c.rows > 1 && layout(3, bt_r16((size_t)c.rows * row_bytes)) > cap) --c.rows;
+    c.slot = bt_r16((size_t)c.rows * row_bytes);
+    THM_REQUIRE(c.slot < (size_t)INT32_MAX, "block-solve tile too large");
+    for (int q = 16; q >= 2 && c.ns == 0; --q)
+        if (layout(q, c.slot) <= cap) c.ns = q;
+    THM_REQUIRE(c.ns >= 2, "subdomain too large for the shared-memory block solve (" +
+                               std::to_string(layout(0, 0)) + " bytes of vectors and level data, " +
+                               std::to_string(c.slot) + "-byte tiles)");
+    c.smem = layout(c.ns, c.slot);
+    return c;
+}
+
+template <class V, class F>
+static void bt_launch(const thm_sys* s, const BtCfg& c, const F* fac, const F* cval, const int32_t* ai, const F* av,
+                      const int32_t* ci, const F* cv, const int32_t* ei, const F* ev, const V* x, V* y) {
+    const thm_mesh* m = s->m;
     static size_t attr = 0;
-    if (smem > 48 * 1024 && smem > attr) {
-        THM_CUDA(cudaFuncSetAttribute(k_bt_solve<V, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr = smem;
+    if (c.smem > 48 * 1024 && c.smem > attr) {
+        THM_CUDA(cudaFuncSetAttribute(k_bt_solve<V, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem));
+        attr = c.smem;
     }
     THM_LAUNCH(THM_K_PINV, s->st,
-               k_bt_solve<V, F><<<dim3(2, m->n_sub), BT_THREADS, smem, s->st>>>(
+               k_bt_solve<V, F><<<dim3(2, m->n_sub), BT_THREADS, c.smem, s->st>>>(
                    m->d_subs.p, m->d_levels.p, fac, m->d_cpl_ptr.p, m->d_cpl_col.p, cval, m->n_loc,
-                   m->order == 2 ? 1 : 0, ai, av, ci, cv, ei, ev, rows, ns, (int)slot, (int)cslot, cglob,
-                   m->max_lev, nvec, m->max_m, s->dev_err.p, x, y));
+                   m->order == 2 ? 1 : 0, ai, av, ci, cv, ei, ev, c.rows, c.ns, (int)c.slot, (int)c.cslot, c.cglob,
+                   m->max_lev, c.nvec, m->max_m, s->dev_err.p, x, y));
+}
+
+// The tile size is tuned once per system and factor precision: on the first
+// apply every candidate runs on the caller's vectors (the result is the same
+// each time) and the fastest of two timed launches wins.  THM_BT_TILE_BYTES
+// fixes it instead.
+template <class V, class F>
+static void apply_Pinv(const thm_sys* s, const F* fac, const F* cval, const int32_t* ai, const F* av,
+                       const int32_t* ci, const F* cv, const int32_t* ei, const F* ev, const V* x, V* y) {
+    const thm_mesh* m = s->m;
+    THM_REQUIRE(m->max_m <= BT_MAX_M, "level block larger than the block-solve kernel supports (" +
+                                          std::to_string(m->max_m) + " > " + std::to_string(BT_MAX_M) + ")");
+    size_t& tile = s->bt_tile[sizeof(F) == 4 ? 1 : 0];
+    if (tile == 0) {
+        if (const char* e = getenv("THM_BT_TILE_BYTES")) {
+            tile = (size_t)std::max(1024, atoi(e));
+        } else {
+            const size_t cand[] = {16384, 32768, 49152, 65536, 98304};
+            cudaEvent_t e0, e1;
+            THM_CUDA(cudaEventCreate(&e0));
+            THM_CUDA(cudaEventCreate(&e1));
+            float best = 1e30f;
+            int best_rows = -1;
+            for (size_t t : cand) {
+                const BtCfg c = bt_config<V, F>(m, t);
+                if (c.rows == best_rows) continue;                // same tiles as a faster-or-equal candidate
+                bt_launch<V, F>(s, c, fac, cval, ai, av, ci, cv, ei, ev, x, y);      // warm
+                THM_CUDA(cudaEventRecord(e0, s->st));
+                for (int r = 0; r < 2; ++r) bt_launch<V, F>(s, c, fac, cval, ai, av, ci, cv, ei, ev, x, y);
+                THM_CUDA(cudaEventRecord(e1, s->st));
+                THM_CUDA(cudaEventSynchronize(e1));
+                float ms = 0;
+                THM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                if (ms < best) { best = ms; tile = t; best_rows = c.rows; }
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+        }
+    }
+    bt_launch<V, F>(s, bt_config<V, F>(m, tile), fac, cval, ai, av, ci, cv, ei, ev, x, y);
 }
 
 template <class V>
