@@ -49,7 +49,7 @@ def test_adjoint_matches_oracle_adjoint(order, oblique, mode):
 
 
 def test_adjoint_vs_central_differences_and_autograd():
-    """North-star check: dL/dmu^{-1} and dL/domega against central differences
+    """Gradient check: dL/dmu^{-1} and dL/domega against central differences
     (h = 1e-4) of the GPU solve itself, to 1e-5 relative."""
     import paper_2105_11993_gb300 as thm
     from paper_2105_11993_gb300 import autograd as ag
