@@ -173,7 +173,8 @@ typedef struct thm_solve_opts {
     int    outer_method;   /* THM_OUTER_GMRES (0): GMRES on (I - A) g = b (Eq. 8);
                               THM_OUTER_JACOBI (1): the fixed-point iteration
                               g <- A g + b of the same map, stopped when
-                              ||(I - A) g - b|| <= outer_tol ||b|| */
+                              ||(I - A) g - b|| <= outer_tol ||b|| (norms over
+                              the whole interface vector, also for a batch) */
 } thm_solve_opts;
 
 #define THM_OUTER_GMRES 0
