@@ -308,3 +308,24 @@ def test_more_than_64_subdomains(mode):
     u, st = sysg.solve(mode=mode, rtol=1e-11 if mode == "fp64" else 1e-9)
     u = u.cpu().numpy()
     assert np.linalg.norm(u - u0) <= (1e-8 if mode == "fp64" else 1e-6) * np.linalg.norm(u0)
+
+
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+def test_pinv_independent_of_tile_size(mode, monkeypatch):
+    """The block-solve tile size (autotuned per system, or fixed by
+    THM_BT_TILE_BYTES) changes only how the factor streams and the order of
+    partial sums: results agree to rounding across sizes."""
+    import paper_2105_11993_gb300 as thm
+    P = CASES["p2_rot"]()
+    x = _rand_local(make_system(P)[1].n_local, 11)
+    ys = []
+    for tile in ("2048", "16384", "65536", None):
+        if tile is None:
+            monkeypatch.delenv("THM_BT_TILE_BYTES", raising=False)
+        else:
+            monkeypatch.setenv("THM_BT_TILE_BYTES", tile)
+        _, sysg = make_system(P)
+        ys.append(sysg.apply_local(thm.OP_PINV, torch.tensor(x, device="cuda"), mode=mode).cpu().numpy())
+    tol = 1e-12 if mode == "fp64" else 1e-5
+    for y in ys[1:]:
+        assert np.linalg.norm(y - ys[0]) <= tol * np.linalg.norm(ys[0])
