@@ -309,14 +309,4 @@ __global__ void k_sub(int64_t n, const V* __restrict__ a, const V* __restrict__ 
     }
 }
 
-template <class A, class B>
-__global__ void k_convert(int64_t n, const A* __restrict__ a, B* __restrict__ b) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i < n) {
-        A u = a[i];
-        b[i].x = u.x;
-        b[i].y = u.y;
-    }
-}
-
 }  // namespace thm
