@@ -296,20 +296,40 @@ k_bt_solve(const Sub* __restrict__ subs, const Level* __restrict__ levels, const
         // ---------------- consumer warps ----------------
         const int vbase = rank == 0 ? lv[0].start : lv[k].start;
         const int vend = rank == 0 ? lv[k].start + lv[k].size : lv[L - 1].start + lv[L - 1].size;
-        // (a) load r for this rank's levels; order 2: r_E <- r_E - G r_I
-        for (int e = vbase + tid; e < vend; e += BT_NT) {
-            V a = x[e];
-            Rt ar = a.x, aim = a.y;
-            if (condensed) {
+        // (a) load r for this rank's levels; order 2: r_E <- r_E - G r_I.
+        // Two rows per pass: their table loads, then their gathers, are in
+        // flight together (each row's arithmetic is unchanged).
+        for (int e0 = vbase + tid; e0 < vend; e0 += 2 * BT_NT) {
+            int64_t ix[2][8];
+            Rt gv[2][8];
+            V xr[2];
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const int e = e0 + r * BT_NT;
+                const bool ok = e < vend;
+                xr[r] = ok ? x[e] : mk<V>(0, 0);
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
-                    const Rt g = (Rt)av[u * n_loc + e];
-                    const V xb = x[ai[u * n_loc + e]];
-                    ar -= g * xb.x;
-                    aim -= g * xb.y;
+                    ix[r][u] = (ok && condensed) ? (int64_t)ai[u * n_loc + e] : -1;
+                    gv[r][u] = (ok && condensed) ? (Rt)av[u * n_loc + e] : (Rt)0;
                 }
             }
-            vec[e - vbase] = mk<V>(ar, aim);
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const int e = e0 + r * BT_NT;
+                Rt ar = xr[r].x, aim = xr[r].y;
+                V xb[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) xb[u] = ix[r][u] >= 0 ? x[ix[r][u]] : mk<V>(0, 0);
+                if (condensed) {
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        ar -= gv[r][u] * xb[u].x;
+                        aim -= gv[r][u] * xb[u].y;
+                    }
+                }
+                if (e < vend) vec[e - vbase] = mk<V>(ar, aim);
+            }
         }
         bt_bar_consumers();
         int t = 0, tc = 0;                       // W / coupling tiles consumed
@@ -507,26 +527,49 @@ k_bt_solve(const Sub* __restrict__ subs, const Level* __restrict__ levels, const
         const int64_t b0 = S.off + S.ne, nbub = S.n - S.ne;
         const int64_t half = (nbub + 1) / 2;
         const int64_t lo = b0 + (rank == 0 ? 0 : half), hi = b0 + (rank == 0 ? half : nbub);
-        for (int64_t b = lo + tid; b < hi; b += blockDim.x) {
-            Rt ar = 0, aim = 0;
+        // two rows per pass, as in (a)
+        for (int64_t b0r = lo + tid; b0r < hi; b0r += 2 * (int64_t)blockDim.x) {
+            int64_t cix[2][4], eix[2][8];
+            Rt cc[2][4], ec[2][8];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const Rt c = (Rt)cv[j * n_loc + b];
-                const V xb = x[ci[j * n_loc + b]];
-                ar += c * xb.x;
-                aim += c * xb.y;
-            }
+            for (int r = 0; r < 2; ++r) {
+                const int64_t b = b0r + r * (int64_t)blockDim.x;
+                const bool ok = b < hi;
 #pragma unroll
-            for (int a = 0; a < 8; ++a) {
-                const int64_t e = (int64_t)ei[a * n_loc + b];
-                if (e >= S.off && e < S.off + S.ne) {
-                    const Rt c = (Rt)ev[a * n_loc + b];
-                    const V xe = y[e];
-                    ar += c * xe.x;
-                    aim += c * xe.y;
+                for (int j = 0; j < 4; ++j) {
+                    cix[r][j] = ok ? (int64_t)ci[j * n_loc + b] : -1;
+                    cc[r][j] = ok ? (Rt)cv[j * n_loc + b] : (Rt)0;
+                }
+#pragma unroll
+                for (int a = 0; a < 8; ++a) {
+                    const int64_t e = ok ? (int64_t)ei[a * n_loc + b] : -1;
+                    eix[r][a] = (e >= S.off && e < S.off + S.ne) ? e : -1;
+                    ec[r][a] = eix[r][a] >= 0 ? (Rt)ev[a * n_loc + b] : (Rt)0;
                 }
             }
-            y[b] = mk<V>(ar, aim);
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const int64_t b = b0r + r * (int64_t)blockDim.x;
+                V xb[4], xe[8];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) xb[j] = cix[r][j] >= 0 ? x[cix[r][j]] : mk<V>(0, 0);
+#pragma unroll
+                for (int a = 0; a < 8; ++a) xe[a] = eix[r][a] >= 0 ? y[eix[r][a]] : mk<V>(0, 0);
+                Rt ar = 0, aim = 0;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    ar += cc[r][j] * xb[j].x;
+                    aim += cc[r][j] * xb[j].y;
+                }
+#pragma unroll
+                for (int a = 0; a < 8; ++a) {
+                    if (eix[r][a] >= 0) {
+                        ar += ec[r][a] * xe[a].x;
+                        aim += ec[r][a] * xe[a].y;
+                    }
+                }
+                if (b < hi) y[b] = mk<V>(ar, aim);
+            }
         }
     }
 }
