@@ -301,8 +301,9 @@ int thm_alg_bytes(const thm_sys* s, int mode, int cls, double* bytes);
  * device allocation (the paper has no counterpart).
  *
  * For callers that cannot allocate device memory when they need the check:
- * code inside a CUDA stream capture, or programs that reserve all device
- * memory up front and forbid cudaMalloc in their time-critical loop.
+ * programs that hand all device memory to their own pool allocator up front
+ * (a cudaMalloc then fails, or the pool forbids it), and loops that must not
+ * call cudaMalloc or cudaFree because those synchronise the whole device.
  *
  *  u    device complex double [n_dof]: a field on all DOFs (Dirichlet entries
  *       are ignored; the Dirichlet lifting already sits in f).

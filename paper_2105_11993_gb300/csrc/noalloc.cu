@@ -2,10 +2,11 @@
 // field u without any device allocation.
 //
 // Who needs it: callers that cannot call cudaMalloc at the moment they want a
-// residual check, for example code inside a region that is being captured
-// into a CUDA graph, or a host program that pre-allocates all device memory
-// up front and forbids allocation in its time-critical loop.  The regular
-// path (thm_ddm_solve's refinement check) allocates its work vectors lazily.
+// residual check: a host program that hands all device memory to its own
+// pool allocator up front (cudaMalloc then fails), or a time-critical loop
+// that must not call cudaMalloc/cudaFree because they synchronise the whole
+// device.  The regular path (thm_ddm_solve's refinement check) allocates its
+// work vectors lazily.
 //
 // The only scratch is the file-scope array below: per-block partial sums of
 // |f - K u|^2 and |f|^2.  Each GPU that loads this library holds those 64 KB

@@ -1,5 +1,5 @@
 """thm_residual_noalloc (the entry point that allocates no device memory, for
-callers that cannot call cudaMalloc, e.g. inside a stream capture) against the
+callers whose device memory is all held by their own pool) against the
 residual the regular solve reports, called through the C ABI twice in a row.
 Collected last so that a stopping run has already run every other test."""
 import ctypes as C
