@@ -476,22 +476,6 @@ __global__ void k_condensed_values(int64_t n_loc, int nb, int maxc, int condense
 // Each W_l is stored with row stride r4(m_l) (zero padding).
 // ---------------------------------------------------------------------------
 template <class F>
-__device__ void cta_gemm(F* C, int ldc, const F* A, int lda, const F* B, int ldb, int m, int k, int n,
-                         bool b_transposed, bool subtract) {
-    // C (m x n) (-)= A (m x k) * (B (k x n) or B^T with B (n x k)); row-major, no aliasing
-    for (int t = threadIdx.x; t < m * n; t += blockDim.x) {
-        int i = t / n, j = t % n;
-        F acc = 0;
-        if (b_transposed)
-            for (int q = 0; q < k; ++q) acc += A[(int64_t)i * lda + q] * B[(int64_t)j * ldb + q];
-        else
-            for (int q = 0; q < k; ++q) acc += A[(int64_t)i * lda + q] * B[(int64_t)q * ldb + j];
-        if (subtract) C[(int64_t)i * ldc + j] -= acc;
-        else C[(int64_t)i * ldc + j] = acc;
-    }
-}
-
-template <class F>
 __device__ bool cta_gauss_jordan(F* W, int m, int ld, int* perm, F* fcol, F* rv, int* ri) {
     __shared__ int s_piv;
     __shared__ int s_bad;
@@ -591,15 +575,30 @@ __device__ void extract_block(const Level& L, int64_t c0, int mc, F* dst, int ld
 
 __device__ __forceinline__ int ld4(int m) { return (m + 3) / 4 * 4; }
 
-// W (m_l rows, stride r4(m_l)) -= C W_n C^T with C = S_{l,n} (the coupling of
-// level l to the already-eliminated neighbour n).
-__device__ void schur_update(const Level& L, const Level& N, double* W, const double* Wn, double* tC, double* tT,
-                             const int64_t* slice_ptr, const int32_t* col, const uint8_t* pad,
-                             const double* sval) {
-    extract_block(L, N.start, N.size, tC, N.size, slice_ptr, col, pad, sval);              // C
-    cta_gemm(tT, N.size, tC, N.size, Wn, ld4(N.size), L.size, N.size, N.size, false, false);  // C W_n
+// W (m_l rows, stride r4(m_l)) -= C W_n C^T with C = S_{l,n}, the coupling of
+// level l to the already-eliminated neighbour n, taken from the level's sparse
+// coupling list (side 0: n = l-1, side 1: n = l+1; a few entries per row):
+//   T = C W_n  (m_l x m_n, row stride m_n),   W[i][j] -= sum_q T[i][c_q] C[j][c_q].
+__device__ void schur_update(const Level& L, const Level& N, int side, double* W, const double* Wn, double* tT,
+                             const int32_t* __restrict__ cptr, const int32_t* __restrict__ ccol,
+                             const double* __restrict__ cval) {
+    const int32_t* P = cptr + (side == 0 ? L.eptr : L.fptr);
+    const int32_t* Cc = ccol + (side == 0 ? L.eoff : L.foff);
+    const double* Cv = cval + (side == 0 ? L.eoff : L.foff);
+    const int ml = L.size, mn = N.size, ldn = ld4(mn), ldl = ld4(ml);
+    for (int64_t t = threadIdx.x; t < (int64_t)ml * mn; t += blockDim.x) {
+        const int i = (int)(t / mn), j = (int)(t % mn);
+        double acc = 0;
+        for (int p = P[i]; p < P[i + 1]; ++p) acc += Cv[p] * Wn[(int64_t)Cc[p] * ldn + j];
+        tT[t] = acc;
+    }
     __syncthreads();
-    cta_gemm(W, ld4(L.size), tT, N.size, tC, N.size, L.size, N.size, L.size, true, true);    // -= (C W_n) C^T
+    for (int64_t t = threadIdx.x; t < (int64_t)ml * ml; t += blockDim.x) {
+        const int i = (int)(t / ml), j = (int)(t % ml);
+        double acc = 0;
+        for (int q = P[j]; q < P[j + 1]; ++q) acc += tT[(int64_t)i * mn + Cc[q]] * Cv[q];
+        W[(int64_t)i * ldl + j] -= acc;
+    }
     __syncthreads();
 }
 
@@ -607,8 +606,10 @@ __device__ void schur_update(const Level& L, const Level& N, double* W, const do
 // mid == 1: grid n_sub, the middle level (after both chains).
 __global__ void k_bt_factor(int mid, const Sub* __restrict__ subs, const Level* __restrict__ levels,
                             const int64_t* __restrict__ slice_ptr, const int32_t* __restrict__ col,
-                            const uint8_t* __restrict__ pad, const double* __restrict__ sval, double* fac,
-                            double* tmp_all, int64_t tmp_stride, int* perm_all, int max_m, int* status) {
+                            const uint8_t* __restrict__ pad, const double* __restrict__ sval,
+                            const int32_t* __restrict__ cptr, const int32_t* __restrict__ ccol,
+                            const double* __restrict__ cval, double* fac, double* tmp_all, int64_t tmp_stride,
+                            int* perm_all, int max_m, int* status) {
     extern __shared__ unsigned char smem_raw[];
     double* fcol = reinterpret_cast<double*>(smem_raw);
     double* rv = fcol + max_m;
@@ -616,8 +617,7 @@ __global__ void k_bt_factor(int mid, const Sub* __restrict__ subs, const Level* 
     const int s = blockIdx.x, chain = mid ? 0 : blockIdx.y;
     const Sub S = subs[s];
     if (S.nlev == 0) return;
-    double* tC = tmp_all + ((int64_t)s * 2 + chain) * tmp_stride;
-    double* tT = tC + (int64_t)max_m * max_m;
+    double* tT = tmp_all + ((int64_t)s * 2 + chain) * tmp_stride;
     int* perm = perm_all + ((int64_t)s * 2 + chain) * max_m;
     const int k = S.kmid;
     if (mid) {
@@ -626,11 +626,11 @@ __global__ void k_bt_factor(int mid, const Sub* __restrict__ subs, const Level* 
         extract_block(L, L.start, L.size, W, ld4(L.size), slice_ptr, col, pad, sval);
         if (k > 0) {
             const Level N = levels[S.lev0 + k - 1];
-            schur_update(L, N, W, fac + N.offW, tC, tT, slice_ptr, col, pad, sval);
+            schur_update(L, N, 0, W, fac + N.offW, tT, cptr, ccol, cval);
         }
         if (k + 1 < S.nlev) {
             const Level N = levels[S.lev0 + k + 1];
-            schur_update(L, N, W, fac + N.offW, tC, tT, slice_ptr, col, pad, sval);
+            schur_update(L, N, 1, W, fac + N.offW, tT, cptr, ccol, cval);
         }
         if (!cta_gauss_jordan(W, L.size, ld4(L.size), perm, fcol, rv, ri) && threadIdx.x == 0) atomicExch(status, 1);
         return;
@@ -643,7 +643,7 @@ __global__ void k_bt_factor(int mid, const Sub* __restrict__ subs, const Level* 
         extract_block(L, L.start, L.size, W, ld4(L.size), slice_ptr, col, pad, sval);
         if (q > 0) {
             const Level N = levels[S.lev0 + (chain == 0 ? l - 1 : l + 1)];
-            schur_update(L, N, W, fac + N.offW, tC, tT, slice_ptr, col, pad, sval);
+            schur_update(L, N, chain == 0 ? 0 : 1, W, fac + N.offW, tT, cptr, ccol, cval);
         }
         if (!cta_gauss_jordan(W, L.size, ld4(L.size), perm, fcol, rv, ri)) {
             if (threadIdx.x == 0) atomicExch(status, 1);
@@ -848,7 +848,7 @@ static void factor64(thm_sys* s) {
     s->fac64.alloc(m->fac_elems);
     s->fac64.zero(st);
     DArr<double> tmp;
-    const int64_t stride = 2 * (int64_t)m->max_m * m->max_m;
+    const int64_t stride = (int64_t)m->max_m * m->max_m;      // T = C W_n of one chain
     tmp.alloc((size_t)stride * m->n_sub * 2);
     DArr<int> perm, status;
     perm.alloc((size_t)m->max_m * m->n_sub * 2);
@@ -859,11 +859,11 @@ static void factor64(thm_sys* s) {
     if (smem > 48 * 1024)
         THM_CUDA(cudaFuncSetAttribute(k_bt_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     THM_LAUNCH(THM_K_SETUP, st, k_bt_factor<<<dim3(m->n_sub, 2), threads, smem, st>>>(
-        0, m->d_subs.p, m->d_levels.p, m->d_slice_ptr.p, m->d_sell_col.p, m->d_sell_pad.p, s->sval64.p, s->fac64.p,
-        tmp.p, stride, perm.p, m->max_m, status.p));
+        0, m->d_subs.p, m->d_levels.p, m->d_slice_ptr.p, m->d_sell_col.p, m->d_sell_pad.p, s->sval64.p, m->d_cpl_ptr.p,
+        m->d_cpl_col.p, s->cpl64.p, s->fac64.p, tmp.p, stride, perm.p, m->max_m, status.p));
     THM_LAUNCH(THM_K_SETUP, st, k_bt_factor<<<m->n_sub, threads, smem, st>>>(
-        1, m->d_subs.p, m->d_levels.p, m->d_slice_ptr.p, m->d_sell_col.p, m->d_sell_pad.p, s->sval64.p, s->fac64.p,
-        tmp.p, stride, perm.p, m->max_m, status.p));
+        1, m->d_subs.p, m->d_levels.p, m->d_slice_ptr.p, m->d_sell_col.p, m->d_sell_pad.p, s->sval64.p, m->d_cpl_ptr.p,
+        m->d_cpl_col.p, s->cpl64.p, s->fac64.p, tmp.p, stride, perm.p, m->max_m, status.p));
     THM_CUDA(cudaGetLastError());
     std::vector<int> hs;
     status.download(hs, st);
