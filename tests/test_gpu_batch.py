@@ -79,3 +79,26 @@ def _union_arrays(probs):
         v0 += mh.coords.shape[0]; s0 += int(mh.cell_sub.max()) + 1
     return (np.concatenate(coords), np.concatenate(cells), np.concatenate(subs), np.concatenate(bf),
             np.concatenate(bt))
+
+
+def test_batch_3d_matches_each_problem_alone():
+    """Order-1 hexes: a batch of three cubes (1, 8 and 8 subdomains, different
+    omega) against the monolithic oracle of each cube."""
+    import paper_2105_11993_gb300 as thm
+    probs = []
+    for p, (n, s, om) in enumerate([(3, 1, 4.0), (4, 2, 6.0), (6, 2, 5.5)]):
+        mesh = W.structured_mesh_3d(n, s, relabel=(p == 1), rotate_cells=(p == 1))
+        mu = W.mu_inv_lognormal(mesh.n_cell, 0.3, f"batch3/{p}")
+        pol, d = W.plane_wave_y(3)
+        probs.append(W.Problem(f"c{p}", mesh, 1, mu, om, 1.0, pol, d))
+    mesh, _ = thm.Mesh.batch([P.mesh for P in probs], 1)
+    sysg = thm.System(mesh, np.concatenate([P.mu_inv for P in probs]), np.array([P.omega for P in probs]), 1.0,
+                      probs[0].pol, probs[0].direction)
+    u, st = sysg.solve(mode="mixed", rtol=1e-9)
+    u = u.cpu().numpy()
+    d0 = 0
+    for P in probs:
+        u0 = fem.solve_monolithic(fem.assemble(P))
+        assert np.linalg.norm(u[d0:d0 + len(u0)] - u0) <= 1e-6 * np.linalg.norm(u0), P.name
+        d0 += len(u0)
+    assert d0 == len(u)

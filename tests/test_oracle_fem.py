@@ -291,3 +291,21 @@ def test_residual_of_direct_solve():
     u = fem.solve_monolithic(S)
     assert fem.residual(S, u) < 1e-12
     assert S.dofs.n_dof == 2112
+
+
+def test_subdomain_blocks_balanced_when_side_does_not_divide():
+    """s = ceil(n/32) blocks per side of a side-n square (the batch workload):
+    block sizes differ by at most one cell, and a dividing s gives equal blocks."""
+    for n, s in [(57, 2), (100, 4), (33, 2), (64, 2), (97, 4)]:
+        mesh = W.structured_mesh_2d(n, n, s, s)
+        counts = np.bincount(mesh.cell_sub, minlength=s * s)
+        assert counts.size == s * s and counts.min() > 0
+        assert max(counts) - min(counts) <= 2 * int(np.ceil(n / s)) + 1
+        rows = np.bincount((np.arange(n) * s // n), minlength=s)
+        assert rows.max() - rows.min() <= 1
+        if n % s == 0:
+            assert counts.min() == counts.max() == (n // s) ** 2
+    probs = W.batch_problems(16)
+    for P in probs:
+        n = P.mesh.shape[0]
+        assert P.mesh.n_sub == int(np.ceil(n / 32)) ** 2
