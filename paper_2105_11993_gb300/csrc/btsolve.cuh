@@ -193,7 +193,7 @@ k_bt_solve(const Sub* __restrict__ subs, const Level* __restrict__ levels, const
            const int32_t* __restrict__ ci, const F* __restrict__ cv, const int32_t* __restrict__ ei,
            const F* __restrict__ ev, int R, int ns, int slot_bytes, int cslot_bytes, int cglob, int max_lev, int nvec,
            int max_m,
-           int* __restrict__ err, const V* __restrict__ x, V* __restrict__ y) {
+           int* __restrict__ err, const int* __restrict__ act, const V* __restrict__ x, V* __restrict__ y) {
     using Rt = typename VT<V>::R;
     namespace cg = cooperative_groups;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -220,6 +220,9 @@ k_bt_solve(const Sub* __restrict__ subs, const Level* __restrict__ levels, const
     V* pry = cluster.map_shared_rank(ry, peer);
     volatile int* abort = &s_abort;
 
+    // a subdomain whose Krylov segment has converged is skipped by both CTAs
+    // of its cluster (same flag, read before any cluster barrier)
+    if (act && !act[blockIdx.y]) return;
     const Sub S = subs[blockIdx.y];
     const int L = S.nlev, k = S.kmid;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;

@@ -27,10 +27,12 @@ __global__ void __launch_bounds__(256) k_spmv(int64_t n, const int64_t* __restri
                                               const int32_t* __restrict__ col, const F* __restrict__ val,
                                               const F* __restrict__ bg, const F* __restrict__ bs, int use_bs,
                                               const F* __restrict__ bvg, const F* __restrict__ bvs,
-                                              const V* __restrict__ x, V* __restrict__ y) {
+                                              const V* __restrict__ x, V* __restrict__ y,
+                                              const int32_t* __restrict__ row_seg, const int* __restrict__ act) {
     using R = typename VT<V>::R;
     int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (r >= n) return;
+    if (act && !act[row_seg[r]]) return;       // a converged subdomain's rows are not needed
     int64_t sl = r >> 5;
     int lane = (int)(r & 31);
     int64_t base = slice_ptr[sl];
@@ -131,10 +133,12 @@ constexpr int EPT = CHUNK / KT;               // elements per thread
 template <class V>
 __global__ void __launch_bounds__(KT) k_chunk_dots(const Chunk* __restrict__ chunks, const V* __restrict__ basis,
                                                    int64_t ld, int nk, const V* __restrict__ w,
-                                                   double2* __restrict__ partial, int ldp) {
+                                                   double2* __restrict__ partial, int ldp,
+                                                   const int* __restrict__ act) {
     using R = typename VT<V>::R;
     extern __shared__ double2 sred[];          // [nk][KT/32]
     const Chunk c = chunks[blockIdx.x];
+    if (act && !act[c.seg]) return;            // converged segment: its partials are not read
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     V wr[EPT];
 #pragma unroll
@@ -175,11 +179,13 @@ __global__ void __launch_bounds__(KT) k_chunk_dots(const Chunk* __restrict__ chu
 template <class V>
 __global__ void __launch_bounds__(KT) k_chunk_update(const Chunk* __restrict__ chunks, const V* __restrict__ basis,
                                                      int64_t ld, int nk, const double2* __restrict__ h, int ldh,
-                                                     V* __restrict__ w, double* __restrict__ nrm_part) {
+                                                     V* __restrict__ w, double* __restrict__ nrm_part,
+                                                     const int* __restrict__ act) {
     using R = typename VT<V>::R;
     extern __shared__ double2 sh[];            // [nk] coefficients of this segment
     __shared__ double sw[KT / 32];
     const Chunk c = chunks[blockIdx.x];
+    if (act && !act[c.seg]) return;            // converged segment: left as it is
     for (int k = threadIdx.x; k < nk; k += KT) sh[k] = h[(int64_t)c.seg * ldh + k];
     __syncthreads();
     const bool full = c.end - c.begin == CHUNK;
@@ -259,9 +265,10 @@ __global__ void k_seg_reduce_real(int nseg, const int32_t* __restrict__ seg_ch, 
 // scale: x[e] = (beta[seg] > 0) ? r[e] / beta[seg] : 0
 template <class V>
 __global__ void k_chunk_scale(const Chunk* __restrict__ chunks, const V* __restrict__ r,
-                              const double* __restrict__ beta, V* __restrict__ x) {
+                              const double* __restrict__ beta, V* __restrict__ x, const int* __restrict__ act) {
     using R = typename VT<V>::R;
     const Chunk c = chunks[blockIdx.x];
+    if (act && !act[c.seg]) return;
     double b = beta[c.seg];
     R inv = b > 0 ? (R)(1.0 / b) : (R)0;
     for (int64_t e = c.begin + threadIdx.x; e < c.end; e += blockDim.x) {

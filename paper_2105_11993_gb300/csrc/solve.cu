@@ -303,6 +303,7 @@ struct Krylov {
     double2* h_gring = nullptr;      // g_{j+1} of segment 0 (residual estimate)
     double h_beta0 = 0;              // ||r_0|| of segment 0 at the first cycle
     double last_rel = 1.0;           // latest residual estimate of segment 0 seen by the host, relative
+    const int* step_mask = nullptr;  // device per-segment activity while an Arnoldi step applies A and M
     cudaEvent_t ring_ev[RING] = {};
 
     ~Krylov() {
@@ -396,28 +397,32 @@ struct Krylov {
             first = false;
             if (read_nact(st) == 0) break;
             if (total >= maxit) { ks.status = THM_ENOCONV; break; }
-            THM_LAUNCH(THM_K_KRYLOV, st, k_chunk_scale<V><<<nch, 256, 0, st>>>(d_chunks, r.p, beta.p, basis.p));
+            THM_LAUNCH(THM_K_KRYLOV, st, k_chunk_scale<V><<<nch, 256, 0, st>>>(d_chunks, r.p, beta.p, basis.p, nullptr));
             int j = 0, checked = 0;
             for (; j < m && total < maxit; ++j) {
                 V* vj = basis.p + (int64_t)j * n;
                 const V* zin = vj;
                 V* zj = flexible ? zbasis.p + (int64_t)j * n : z.p;
+                // inside the Arnoldi steps the operators and the step kernels skip
+                // segments that have converged (their columns are final)
+                step_mask = active.p;
                 if (M) { M(vj, zj); zin = zj; }
                 A(zin, w.p);
+                step_mask = nullptr;
                 const int nk = j + 1;
                 size_t sm = (size_t)nk * (KT / 32) * sizeof(double2);
-                THM_LAUNCH(THM_K_DOTS, st, k_chunk_dots<V><<<nch, KT, sm, st>>>(d_chunks, basis.p, n, nk, w.p, partial.p, m + 1));
+                THM_LAUNCH(THM_K_DOTS, st, k_chunk_dots<V><<<nch, KT, sm, st>>>(d_chunks, basis.p, n, nk, w.p, partial.p, m + 1, active.p));
                 THM_LAUNCH(THM_K_KRYLOV, st, k_seg_reduce<<<nblk((int64_t)nseg * nk), 256, 0, st>>>(nseg, seg_ch.p, partial.p, m + 1, nk, h1.p, m + 1, 0));
-                THM_LAUNCH(THM_K_UPDATE, st, k_chunk_update<V><<<nch, KT, nk * sizeof(double2), st>>>(d_chunks, basis.p, n, nk, h1.p, m + 1, w.p, nullptr));
-                THM_LAUNCH(THM_K_DOTS, st, k_chunk_dots<V><<<nch, KT, sm, st>>>(d_chunks, basis.p, n, nk, w.p, partial.p, m + 1));
+                THM_LAUNCH(THM_K_UPDATE, st, k_chunk_update<V><<<nch, KT, nk * sizeof(double2), st>>>(d_chunks, basis.p, n, nk, h1.p, m + 1, w.p, nullptr, active.p));
+                THM_LAUNCH(THM_K_DOTS, st, k_chunk_dots<V><<<nch, KT, sm, st>>>(d_chunks, basis.p, n, nk, w.p, partial.p, m + 1, active.p));
                 THM_LAUNCH(THM_K_KRYLOV, st, k_seg_reduce<<<nblk((int64_t)nseg * nk), 256, 0, st>>>(nseg, seg_ch.p, partial.p, m + 1, nk, h2.p, m + 1, 0));
-                THM_LAUNCH(THM_K_UPDATE, st, k_chunk_update<V><<<nch, KT, nk * sizeof(double2), st>>>(d_chunks, basis.p, n, nk, h2.p, m + 1, w.p, nrm_part.p));
+                THM_LAUNCH(THM_K_UPDATE, st, k_chunk_update<V><<<nch, KT, nk * sizeof(double2), st>>>(d_chunks, basis.p, n, nk, h2.p, m + 1, w.p, nrm_part.p, active.p));
                 THM_LAUNCH(THM_K_KRYLOV, st, k_seg_reduce_real<<<nblk(nseg), 256, 0, st>>>(nseg, seg_ch.p, nrm_part.p, nrm.p));
                 nact.zero(st);
                 const size_t gsm = (size_t)(j + 1) * sizeof(double2) + (size_t)j * (sizeof(double2) + sizeof(double));
                 THM_LAUNCH(THM_K_KRYLOV, st, k_givens<<<nseg, 32, gsm, st>>>(nseg, j, m, h1.p, h2.p, m + 1, nrm.p, Rm.p, cs.p, sn.p, gv.p,
                                                      target.p, active.p, kused.p, beta.p, nact.p, flag.p));
-                THM_LAUNCH(THM_K_KRYLOV, st, k_chunk_scale<V><<<nch, 256, 0, st>>>(d_chunks, w.p, beta.p, basis.p + (int64_t)(j + 1) * n));
+                THM_LAUNCH(THM_K_KRYLOV, st, k_chunk_scale<V><<<nch, 256, 0, st>>>(d_chunks, w.p, beta.p, basis.p + (int64_t)(j + 1) * n, active.p));
                 ++total;
                 // monitor: copy (active count, breakdown flag) of step j into the ring
                 const int slot = j % RING;
@@ -580,14 +585,16 @@ static inline void bv_arrays(const thm_sys* s, const float*, const float** g, co
     *sg = s->m->dim == 3 ? s->bvs32.p : nullptr;
 }
 
+// act (optional): per-subdomain activity; rows of inactive subdomains are skipped.
 template <class V, class F>
-static void apply_T(const thm_sys* s, const F* val, const F* bg, const F* bs, int use_bs, const V* x, V* y) {
+static void apply_T(const thm_sys* s, const F* val, const F* bg, const F* bs, int use_bs, const V* x, V* y,
+                    const int* act = nullptr) {
     const thm_mesh* m = s->m;
     const F *bvg, *bvs;
     bv_arrays(s, val, &bvg, &bvs);
     THM_LAUNCH(THM_K_SPMV, s->st,
                k_spmv<V, F><<<nblk(m->n_loc), 256, 0, s->st>>>(m->n_loc, m->d_slice_ptr.p, m->d_sell_col.p, val, bg, bs,
-                                                                use_bs, bvg, bvs, x, y));
+                                                                use_bs, bvg, bvs, x, y, m->d_loc_sub.p, act));
 }
 
 // Twisted block-tridiagonal solve, one 2-CTA cluster per subdomain.  The
@@ -632,7 +639,8 @@ static BtCfg bt_config(const thm_mesh* m, size_t target) {
 
 template <class V, class F>
 static void bt_launch(const thm_sys* s, const BtCfg& c, const F* fac, const F* cval, const int32_t* ai, const F* av,
-                      const int32_t* ci, const F* cv, const int32_t* ei, const F* ev, const V* x, V* y) {
+                      const int32_t* ci, const F* cv, const int32_t* ei, const F* ev, const V* x, V* y,
+                      const int* act = nullptr) {
     const thm_mesh* m = s->m;
     static size_t attr = 0;
     if (c.smem > 48 * 1024 && c.smem > attr) {
@@ -643,7 +651,7 @@ static void bt_launch(const thm_sys* s, const BtCfg& c, const F* fac, const F* c
                k_bt_solve<V, F><<<dim3(2, m->n_sub), BT_THREADS, c.smem, s->st>>>(
                    m->d_subs.p, m->d_levels.p, fac, m->d_cpl_ptr.p, m->d_cpl_col.p, cval, m->n_loc,
                    m->order == 2 ? 1 : 0, ai, av, ci, cv, ei, ev, c.rows, c.ns, (int)c.slot, (int)c.cslot, c.cglob,
-                   m->max_lev, c.nvec, m->max_m, s->dev_err.p, x, y));
+                   m->max_lev, c.nvec, m->max_m, s->dev_err.p, act, x, y));
 }
 
 // The tile size is tuned once per system and factor precision: on the first
@@ -652,7 +660,8 @@ static void bt_launch(const thm_sys* s, const BtCfg& c, const F* fac, const F* c
 // fixes it instead.
 template <class V, class F>
 static void apply_Pinv(const thm_sys* s, const F* fac, const F* cval, const int32_t* ai, const F* av,
-                       const int32_t* ci, const F* cv, const int32_t* ei, const F* ev, const V* x, V* y) {
+                       const int32_t* ci, const F* cv, const int32_t* ei, const F* ev, const V* x, V* y,
+                       const int* act = nullptr) {
     const thm_mesh* m = s->m;
     THM_REQUIRE(m->max_m <= BT_MAX_M, "level block larger than the block-solve kernel supports (" +
                                           std::to_string(m->max_m) + " > " + std::to_string(BT_MAX_M) + ")");
@@ -683,17 +692,17 @@ static void apply_Pinv(const thm_sys* s, const F* fac, const F* cval, const int3
             cudaEventDestroy(e1);
         }
     }
-    bt_launch<V, F>(s, bt_config<V, F>(m, tile), fac, cval, ai, av, ci, cv, ei, ev, x, y);
+    bt_launch<V, F>(s, bt_config<V, F>(m, tile), fac, cval, ai, av, ci, cv, ei, ev, x, y, act);
 }
 
 template <class V>
-static void apply_Pinv_mode(const thm_sys* s, bool f32, const V* x, V* y) {
+static void apply_Pinv_mode(const thm_sys* s, bool f32, const V* x, V* y, const int* act = nullptr) {
     if (f32)
         apply_Pinv<V, float>(s, s->fac32.p, s->cpl32.p, s->tab_ai.p, s->tab_av32.p, s->tab_ci.p, s->tab_cv32.p,
-                             s->tab_ei.p, s->tab_ev32.p, x, y);
+                             s->tab_ei.p, s->tab_ev32.p, x, y, act);
     else
         apply_Pinv<V, double>(s, s->fac64.p, s->cpl64.p, s->tab_ai.p, s->tab_av64.p, s->tab_ci.p, s->tab_cv64.p,
-                              s->tab_ei.p, s->tab_ev64.p, x, y);
+                              s->tab_ei.p, s->tab_ev64.p, x, y, act);
 }
 
 
@@ -711,8 +720,10 @@ static void subdomain_solves(thm_sys* s, const SolveCfg& c, const double2* b, do
     Work* w = s->w;
     cudaStream_t st = s->st;
     if (!c.fp32) {
-        auto A = [&](const double2* in, double2* out) { apply_T<double2, double>(s, s->val64.p, s->bg64.p, s->bs64.p, 1, in, out); };
-        auto M = [&](const double2* in, double2* out) { apply_Pinv_mode<double2>(s, false, in, out); };
+        auto A = [&](const double2* in, double2* out) {
+            apply_T<double2, double>(s, s->val64.p, s->bg64.p, s->bs64.p, 1, in, out, w->in64.step_mask);
+        };
+        auto M = [&](const double2* in, double2* out) { apply_Pinv_mode<double2>(s, false, in, out, w->in64.step_mask); };
         add(rs, w->in64.solve(A, M, b, x, true, c.inner_tol, c.inner_maxit, st));
     } else {
         // Mixed: GMRES-IR.  Each cycle solves T d = r in FP32 (FP32 operator,
@@ -720,8 +731,10 @@ static void subdomain_solves(thm_sys* s, const SolveCfg& c, const double2* b, do
         // from the very preconditioned vectors the Arnoldi process used) to a
         // relative 1e-5; x and the true residual r = b - T x are kept in FP64,
         // so the subdomain solves reach the same tolerance as in FP64 mode.
-        auto A = [&](const float2* in, float2* out) { apply_T<float2, float>(s, s->val32.p, s->bg32.p, s->bs32.p, 1, in, out); };
-        auto M = [&](const float2* in, float2* out) { apply_Pinv_mode<float2>(s, true, in, out); };
+        auto A = [&](const float2* in, float2* out) {
+            apply_T<float2, float>(s, s->val32.p, s->bg32.p, s->bs32.p, 1, in, out, w->in32.step_mask);
+        };
+        auto M = [&](const float2* in, float2* out) { apply_Pinv_mode<float2>(s, true, in, out, w->in32.step_mask); };
         Krylov<float2>& K = w->in32;
         THM_CUDA(cudaMemsetAsync(x, 0, m->n_loc * sizeof(double2), st));
         THM_CUDA(cudaMemcpyAsync(w->r64.p, b, m->n_loc * sizeof(double2), cudaMemcpyDeviceToDevice, st));
