@@ -374,9 +374,11 @@ def main():
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(st)
     stats_all = []
+    pinv_work = 0.0          # algorithmic bytes the block solve actually processed (converged subdomains skipped)
     for _ in range(args.steps):
         sysg, u, stats = step(mode)
         stats_all.append(stats)
+        pinv_work += thm.work_bytes(sysg, mode, thm.K_PINV)
     e1.record(st)
     torch.cuda.synchronize()
     barrier(dist)
@@ -403,18 +405,21 @@ def main():
     n_launch, pinv_ms = prof["pinv"]
     per_launch_s = pinv_ms / 1e3 / max(1, n_launch)
     alg_bytes = thm.algorithmic_bytes(sysg, mode, thm.K_PINV)
-    achieved = alg_bytes / per_launch_s / 1e9 if n_launch else None
+    # inside the Arnoldi steps the kernel skips converged subdomains, so a
+    # launch moves between 0 and alg_bytes; the kernel counts the work it did
+    achieved = pinv_work / (pinv_ms / 1e3) / 1e9 if n_launch and pinv_ms > 0 else None
     spmv_n, spmv_ms = prof["spmv"]
-    spmv_bytes = thm.algorithmic_bytes(sysg, mode, thm.K_SPMV)
     roofline = {"kernel": "k_bt_solve (block-preconditioner apply, Eq. 7)", "bound": "hbm",
                 "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": (achieved / hbm_peak) if achieved else None,
                 "traffic": measured_traffic("k_bt_solve", mode),
                 "peak_source": peak_src, "launches": n_launch, "avg_launch_us": 1e6 * per_launch_s,
-                "alg_bytes_per_launch": alg_bytes,
+                "alg_bytes_full_launch": alg_bytes,
+                "alg_bytes_processed": pinv_work,
+                "achieved_definition": "algorithmic bytes of the subdomains processed (counted on the device) / "
+                                       "summed CUDA-event time of the launches in the timed steps",
                 "share_of_step": (pinv_ms / ms) if ms > 0 else None,
                 "spmv": {"launches": spmv_n, "avg_launch_us": 1e6 * spmv_ms / 1e3 / max(1, spmv_n),
-                         "achieved": spmv_bytes / (spmv_ms / 1e3 / max(1, spmv_n)) / 1e9 if spmv_n else None,
                          "share_of_step": (spmv_ms / ms) if ms > 0 else None}}
 
     # plain FP64 form, timed beside (time-to-1e-8)

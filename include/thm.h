@@ -296,6 +296,15 @@ int thm_dirichlet_values(thm_sys* s, double* u_d);
  * Other classes: THM_EINVAL. */
 int thm_alg_bytes(const thm_sys* s, int mode, int cls, double* bytes);
 
+/* Algorithmic bytes of the block-solve work (cls THM_K_PINV) that this system
+ * has actually done so far with the factors of `mode`'s precision, by the
+ * byte model of thm_alg_bytes: inside the Arnoldi steps the kernel skips the
+ * subdomains whose Krylov segment has converged, so the work per launch
+ * varies and thm_alg_bytes (every subdomain) overstates it.  The kernel sums
+ * the values and rows of the subdomains it processes on the device; this
+ * call reads the sums (synchronising the system's stream). */
+int thm_work_bytes(const thm_sys* s, int mode, int cls, double* bytes);
+
 /* ------------------------------------------------------------------------
  * thm_residual_noalloc -- the FP64 true residual of a field u without any
  * device allocation (the paper has no counterpart).

@@ -23,7 +23,7 @@ symbols = [
     "thm_ddm_solve_host", "thm_adjoint", "thm_sys_destroy", "thm_last_error", "thm_sys_info",
     "thm_local_dofs", "thm_iface_dofs", "thm_apply_local", "thm_sweep", "thm_local_sources",
     "thm_dirichlet_values", "thm_kernel_launches", "thm_profile_enable", "thm_profile_read",
-    "thm_alg_bytes", "thm_residual_noalloc", "thm_mesh_set_problems", "thm_assemble_batch",
+    "thm_alg_bytes", "thm_residual_noalloc", "thm_mesh_set_problems", "thm_assemble_batch", "thm_work_bytes",
 ]
 
 
@@ -87,6 +87,7 @@ def load():
         "thm_profile_enable": [C.c_uint],
         "thm_profile_read": [C.c_int, P, P],
         "thm_alg_bytes": [P, C.c_int, C.c_int, P],
+        "thm_work_bytes": [P, C.c_int, C.c_int, P],
         "thm_residual_noalloc": [P, P, P],
     }
     for name, args in sig.items():
@@ -121,6 +122,14 @@ def algorithmic_bytes(sysg, mode, cls) -> float:
     b = C.c_double()
     m = MODE_MIXED if mode == "mixed" else MODE_FP64
     _check(load().thm_alg_bytes(sysg.h, m, int(cls), C.byref(b)))
+    return b.value
+
+
+def work_bytes(sysg, mode, cls) -> float:
+    """thm_work_bytes: algorithmic bytes of the block-solve work done so far."""
+    b = C.c_double()
+    m = MODE_MIXED if mode == "mixed" else MODE_FP64
+    _check(load().thm_work_bytes(sysg.h, m, int(cls), C.byref(b)))
     return b.value
 
 

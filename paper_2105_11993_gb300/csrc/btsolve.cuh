@@ -193,7 +193,8 @@ k_bt_solve(const Sub* __restrict__ subs, const Level* __restrict__ levels, const
            const int32_t* __restrict__ ci, const F* __restrict__ cv, const int32_t* __restrict__ ei,
            const F* __restrict__ ev, int R, int ns, int slot_bytes, int cslot_bytes, int cglob, int max_lev, int nvec,
            int max_m,
-           int* __restrict__ err, const int* __restrict__ act, const V* __restrict__ x, V* __restrict__ y) {
+           int* __restrict__ err, const int* __restrict__ act, const int64_t* __restrict__ welem,
+           unsigned long long* __restrict__ work, const V* __restrict__ x, V* __restrict__ y) {
     using Rt = typename VT<V>::R;
     namespace cg = cooperative_groups;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -225,6 +226,10 @@ k_bt_solve(const Sub* __restrict__ subs, const Level* __restrict__ levels, const
     if (act && !act[blockIdx.y]) return;
     const Sub S = subs[blockIdx.y];
     const int L = S.nlev, k = S.kmid;
+    if (work && rank == 0 && threadIdx.x == 0) {       // instrumentation: the work this launch does
+        atomicAdd(&work[0], (unsigned long long)welem[blockIdx.y]);
+        atomicAdd(&work[1], (unsigned long long)S.n);
+    }
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     for (int l = tid; l < L; l += blockDim.x) lv[l] = levels[S.lev0 + l];
     if (tid == 0) {

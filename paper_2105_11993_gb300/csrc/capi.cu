@@ -352,6 +352,22 @@ int thm_alg_bytes(const thm_sys* s, int mode, int cls, double* bytes) {
     });
 }
 
+int thm_work_bytes(const thm_sys* s, int mode, int cls, double* bytes) {
+    return guarded([&]() -> int {
+        THM_REQUIRE(s && bytes, "NULL argument");
+        THM_REQUIRE(cls == THM_K_PINV, "work counters exist for the block-solve kernel only");
+        *bytes = 0;
+        if (!s->bt_work.p) return THM_OK;
+        std::vector<unsigned long long> h;
+        s->bt_work.download(h, s->st);
+        const bool f32 = mode == THM_MODE_MIXED;
+        const double bv = f32 ? 4.0 : 8.0, bx = 2 * bv;
+        const unsigned long long* c = h.data() + (f32 ? 2 : 0);
+        *bytes = (double)c[0] * bv + 2.0 * (double)c[1] * bx;
+        return THM_OK;
+    });
+}
+
 int64_t thm_kernel_launches(void) { return (int64_t)g_launches.load(); }
 
 int thm_profile_enable(unsigned mask) {

@@ -165,6 +165,8 @@ struct thm_mesh {
     int max_m = 0;
     int max_lev = 0;                                // most levels of a subdomain
     int64_t bt_nvec = 0;                            // longest half-chain vector of the twisted solve
+    std::vector<int64_t> bt_welem;                  // [n_sub] values one block solve reads (W, couplings, tables)
+    thm::DArr<int64_t> d_bt_welem;
     int64_t fac_elems = 0;
     // level couplings of S as compact CSR lists (columns local to the
     // neighbouring level; slot = position of the value in the SELL arrays)
@@ -263,6 +265,10 @@ struct thm_sys {
     // W-tile size of the block-solve kernel picked by its autotuner ([0] FP64
     // factors, [1] FP32), 0 until the first apply
     mutable size_t bt_tile[2] = {0, 0};
+    // block-solve work actually done, per factor precision ([0..1] FP64, [2..3]
+    // FP32): values read and local rows processed, summed by the kernel over
+    // the subdomains it did not skip
+    mutable thm::DArr<unsigned long long> bt_work;
     // solver workspace (allocated on first solve, see solve.cu)
     thm::Work* w = nullptr;
     ~thm_sys();

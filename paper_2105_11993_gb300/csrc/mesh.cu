@@ -491,6 +491,20 @@ void build_mesh(thm_mesh* m) {
     }
     pad4i(m->cpl_ptr);
     for (int k = 0; k < 8; ++k) { m->cpl_ptr.push_back(0); m->cpl_col.push_back(0); m->cpl_slot.push_back(-1); }
+    // values one block solve reads per subdomain (the byte model of the
+    // block-solve kernel): W_l in both sweeps but the middle level once, the
+    // coupling lists, and the order-2 condensation tables
+    m->bt_welem.assign(ns, 0);
+    for (int s = 0; s < ns; ++s) {
+        const auto& S = m->subs[s];
+        int64_t w = 0;
+        for (int l = 0; l < S.nlev; ++l) {
+            const Level& L = m->levels[S.lev0 + l];
+            w += (int64_t)L.size * L.size * (l == S.kmid ? 1 : 2) + L.enz + L.fnz;
+        }
+        if (m->order == 2) w += 8 * S.ne + 12 * (S.n - S.ne);
+        m->bt_welem[s] = w;
+    }
     THM_REQUIRE(m->cpl_col.size() < (size_t)INT32_MAX, "coupling lists too large");
     row_cols_all.clear();
 
@@ -727,6 +741,7 @@ void build_mesh(thm_mesh* m) {
     m->d_cpl_col.upload(m->cpl_col);
     m->d_cpl_slot.upload(m->cpl_slot);
     m->d_subs.upload(m->subs);
+    m->d_bt_welem.upload(m->bt_welem);
     m->d_chunks.upload(m->chunks);
     m->d_dir_edges.upload(m->dir_edges);
     m->d_loc_gdof.upload(m->loc_gdof);

@@ -651,7 +651,8 @@ static void bt_launch(const thm_sys* s, const BtCfg& c, const F* fac, const F* c
                k_bt_solve<V, F><<<dim3(2, m->n_sub), BT_THREADS, c.smem, s->st>>>(
                    m->d_subs.p, m->d_levels.p, fac, m->d_cpl_ptr.p, m->d_cpl_col.p, cval, m->n_loc,
                    m->order == 2 ? 1 : 0, ai, av, ci, cv, ei, ev, c.rows, c.ns, (int)c.slot, (int)c.cslot, c.cglob,
-                   m->max_lev, c.nvec, m->max_m, s->dev_err.p, act, x, y));
+                   m->max_lev, c.nvec, m->max_m, s->dev_err.p, act, m->d_bt_welem.p,
+                   s->bt_work.p ? s->bt_work.p + (sizeof(F) == 4 ? 2 : 0) : nullptr, x, y));
 }
 
 // The tile size is tuned once per system and factor precision: on the first
@@ -666,6 +667,10 @@ static void apply_Pinv(const thm_sys* s, const F* fac, const F* cval, const int3
     THM_REQUIRE(m->max_m <= BT_MAX_M, "level block larger than the block-solve kernel supports (" +
                                           std::to_string(m->max_m) + " > " + std::to_string(BT_MAX_M) + ")");
     size_t& tile = s->bt_tile[sizeof(F) == 4 ? 1 : 0];
+    if (!s->bt_work.p) {
+        s->bt_work.alloc(4);
+        s->bt_work.zero(s->st);
+    }
     if (tile == 0) {
         if (const char* e = getenv("THM_BT_TILE_BYTES")) {
             tile = (size_t)std::max(1024, atoi(e));
