@@ -13,9 +13,9 @@ time-to-1e-8 of the same steps is reported as time_to_1e8_s.  Under torchrun
 (N > 1) every rank solves its own copy (replicas: the path does not shard
 across GPUs, see the design notes), so scaling is weak.
 
---impl reference times the FP64 CPU oracle of the same workload on the host
-cores (a bounded sample per step: the subdomain solves of a few subdomains in
-the first DDM sweep, with the paper's block-preconditioned GMRES).
+--impl reference times the FP64 CPU oracle of the same workload on all host
+cores (per step the whole first DDM sweep: the paper's block-preconditioned
+GMRES in every subdomain, subdomains dealt to one worker process per core).
 """
 from __future__ import annotations
 
@@ -52,6 +52,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--ref-subdomains", type=int, default=4, help="subdomains per reference sample")
     p.add_argument("--e2e-steps", type=int, default=1)
+    p.add_argument("--prof-steps", type=int, default=1,
+                   help="instrumented steps after the timed region (per-launch CUDA-event timing)")
     p.add_argument("--relax", type=int, default=1, help="inexact-Krylov relaxation of the subdomain tolerance")
     p.add_argument("--batch", type=int, default=0, metavar="K",
                    help="instead of the headline workload: the first K problems of the 512-problem batch "
@@ -178,7 +180,7 @@ def allreduce_sum(dist, x):
 # CPU oracle sample (cpu_baseline and --impl reference)
 # --------------------------------------------------------------------------
 ORACLE_SNIPPET = r"""
-import json, os, sys, time
+import json, os, sys, time, platform
 sys.path.insert(0, {root!r})
 import numpy as np
 import workloads as W
@@ -189,31 +191,62 @@ D = ddm.setup(P)
 solve = ddm.subdomain_solver(D, "block_gmres", inner_tol=1e-10, restart=120)
 src = ddm.local_sources(D)
 setup_s = time.perf_counter() - t0
-# the first DDM sweep (zero interface data) restricted to a fixed subdomain sample
-picks = list(range(0, len(D.subs), max(1, len(D.subs) // {nsub})))[:{nsub}]
-out = []
-for step in range({steps}):
+
+def rhs_of(i):
+    r = src[i]
+    return r if np.any(r) else np.ones(len(D.subs[i].free), np.complex128)
+
+def solve_one(i):
     D.stats["inner_iters"] = []
+    solve(i, rhs_of(i))
+    return len(D.subs[i].free) * D.stats["inner_iters"][-1][1]
+
+def cpu_model():
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith(("model name", "cpu part", "hardware")):
+                return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.processor() or platform.machine()
+
+out = {{"setup_s": setup_s, "nproc": os.cpu_count(), "cpu": cpu_model(), "machine": platform.machine(),
+       "n_sub": len(D.subs)}}
+# (i) one thread: the first DDM sweep (zero interface data) restricted to a fixed subdomain sample
+picks = list(range(0, len(D.subs), max(1, len(D.subs) // {nsub})))[:{nsub}]
+single = []
+for step in range({steps}):
     t = time.perf_counter()
-    dof_iters = 0
-    for i in picks:
-        s = D.subs[i]
-        rhs = src[i]
-        if not np.any(rhs):
-            rhs = np.ones(len(s.free), np.complex128)
-        x = solve(i, rhs)
-        it = D.stats["inner_iters"][-1][1]
-        dof_iters += len(s.free) * it
-    out.append((time.perf_counter() - t, dof_iters))
-print(json.dumps({{"setup_s": setup_s, "steps": out, "picks": picks}}))
+    di = sum(solve_one(i) for i in picks)
+    single.append((time.perf_counter() - t, di))
+out["single"] = single
+out["picks"] = picks
+# (ii) all host cores: the whole first sweep (every subdomain), subdomains
+# dealt to a pool of one worker per core.  This process never touches a GPU,
+# so the workers are forked and share the set-up.
+if {allcore_steps} > 0:
+    import multiprocessing as mp
+    ncore = os.cpu_count()
+    order = sorted(range(len(D.subs)), key=lambda i: -len(D.subs[i].free))
+    with mp.get_context("fork").Pool(ncore) as pool:
+        pool.map(solve_one, order[:ncore])            # workers up (untimed)
+        allc = []
+        for step in range({allcore_steps}):
+            t = time.perf_counter()
+            di = sum(pool.map(solve_one, order, chunksize=1))
+            allc.append((time.perf_counter() - t, di))
+    out["allcore"] = allc
+    out["allcore_workers"] = ncore
+print(json.dumps(out))
 """
 
 
-def run_oracle_sample(steps, nsub):
+def run_oracle_sample(steps, nsub, allcore_steps=0):
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[k] = "1"
-    code = ORACLE_SNIPPET.format(root=ROOT, workload=WORKLOAD, nsub=nsub, steps=steps)
+    code = ORACLE_SNIPPET.format(root=ROOT, workload=WORKLOAD, nsub=nsub, steps=steps,
+                                 allcore_steps=allcore_steps)
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
     if r.returncode != 0:
         raise RuntimeError(r.stderr[-2000:])
@@ -221,24 +254,30 @@ def run_oracle_sample(steps, nsub):
 
 
 def reference_arm(args):
+    """The FP64 oracle on all host cores: each step is the whole first DDM
+    sweep of the workload (block-preconditioned GMRES in every subdomain,
+    subdomains dealt to one worker per core)."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
     K, Wm = args.steps, args.warmup
-    res = run_oracle_sample(K + Wm, args.ref_subdomains)
-    timed = res["steps"][Wm:]
+    res = run_oracle_sample(0, args.ref_subdomains, allcore_steps=K + Wm)
+    timed = res["allcore"][Wm:]
     t = sum(s for s, _ in timed)
     di = sum(d for _, d in timed)
     value = di / t
+    cores = res["allcore_workers"]
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": K, "warmup": Wm, "ms_per_step": 1e3 * t / K, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD_DESC, "mode": "fp64 oracle (numpy/scipy, 1 host thread)"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"per step: block-preconditioned GMRES (tol 1e-10) solves of subdomains "
-                                   f"{res['picks']} in the first DDM sweep; oracle set-up "
-                                   f"{res['setup_s']:.1f}s untimed"},
+        "config": {"workload": WORKLOAD_DESC,
+                   "mode": f"fp64 oracle (numpy/scipy), {cores} worker processes of 1 thread"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "cpu": res["cpu"], "nproc": res["nproc"],
+                         "sample": f"per step: the whole first DDM sweep ({res['n_sub']} "
+                                   f"block-preconditioned GMRES subdomain solves, tol 1e-10) over {cores} "
+                                   f"forked workers; oracle set-up {res['setup_s']:.1f}s untimed"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -322,6 +361,15 @@ def batch_arm(args):
     print(json.dumps(line), flush=True)
 
 
+def kernel_classes_report(thm, prof, ms_total):
+    """Per launch class: launches, average CUDA-event time, share of the step."""
+    out = {}
+    for c, (n, ms) in prof.items():
+        out[thm.K_NAMES[c]] = {"launches": n, "avg_launch_us": 1e3 * ms / max(1, n),
+                               "share_of_step": ms / ms_total if ms_total > 0 else None}
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -353,18 +401,20 @@ def main():
     mesh_s = time.perf_counter() - t
     mode = args.mode
 
-    def step(m):
+    def step(m, **kw):
         sysg = thm.System(mesh, mu_d, P.omega, P.kappa, P.pol, P.direction, stream=st)
-        u, stats = sysg.solve(mode=m, rtol=1e-8, relax=args.relax)
+        u, stats = sysg.solve(mode=m, rtol=1e-8, relax=args.relax, **kw)
         return sysg, u, stats
 
+    # warm-up: module loading, first launches, and the block-solve tile
+    # autotuner (it runs on a mesh's first apply per precision; every later
+    # system on the mesh reuses its choice)
     for _ in range(args.warmup):
         step(mode)
     torch.cuda.synchronize()
 
-    # timed region
-    prof_mask = (1 << thm.K_PINV) | (1 << thm.K_SPMV)
-    thm.profile_enable(prof_mask)
+    # ---- timed region: plain steps, no per-launch instrumentation ----
+    thm.profile_enable(0)
     clk = ClockSampler(local)
     clk.start()
     barrier(dist)
@@ -374,11 +424,9 @@ def main():
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(st)
     stats_all = []
-    pinv_work = 0.0          # algorithmic bytes the block solve actually processed (converged subdomains skipped)
     for _ in range(args.steps):
-        sysg, u, stats = step(mode)
+        _, _, stats = step(mode)
         stats_all.append(stats)
-        pinv_work += thm.work_bytes(sysg, mode, thm.K_PINV)
     e1.record(st)
     torch.cuda.synchronize()
     barrier(dist)
@@ -386,15 +434,33 @@ def main():
     clocks = clk.stop()
     ms = e0.elapsed_time(e1)
     ms_max = allreduce_max(dist, ms)
-    prof = {thm.K_NAMES[c]: thm.profile_read(c) for c in (thm.K_PINV, thm.K_SPMV)}
-    thm.profile_enable(0)
 
     dof_iters = sum(s["dof_iters"] for s in stats_all)
     total_dof_iters = allreduce_sum(dist, dof_iters)
     value = total_dof_iters / (ms_max / 1e3)
     tt = [s["seconds"] for s in stats_all]
 
-    # roofline of the dominant timed kernel (block-preconditioner apply)
+    # ---- instrumented steps (after the timed region): per-class CUDA-event
+    # timing of every launch, and the block-solve work counted on the device ----
+    classes = (thm.K_PINV, thm.K_SPMV, thm.K_DOTS, thm.K_UPDATE, thm.K_KRYLOV, thm.K_DDM, thm.K_SETUP)
+    thm.profile_enable(sum(1 << c for c in classes))
+    torch.cuda.synchronize()
+    p0 = torch.cuda.Event(enable_timing=True)
+    p1 = torch.cuda.Event(enable_timing=True)
+    p0.record(st)
+    pinv_work = 0.0          # algorithmic bytes the block solve actually processed (converged subdomains skipped)
+    pstats = []
+    for _ in range(max(1, args.prof_steps)):
+        sysg, _, s1 = step(mode)
+        pstats.append(s1)
+        pinv_work += thm.work_bytes(sysg, mode, thm.K_PINV)
+    p1.record(st)
+    torch.cuda.synchronize()
+    prof_ms = p0.elapsed_time(p1)
+    prof = {c: thm.profile_read(c) for c in classes}
+    thm.profile_enable(0)
+
+    # roofline of the dominant kernel (block-preconditioner apply)
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -402,13 +468,12 @@ def main():
         pass
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
-    n_launch, pinv_ms = prof["pinv"]
+    n_launch, pinv_ms = prof[thm.K_PINV]
     per_launch_s = pinv_ms / 1e3 / max(1, n_launch)
     alg_bytes = thm.algorithmic_bytes(sysg, mode, thm.K_PINV)
     # inside the Arnoldi steps the kernel skips converged subdomains, so a
     # launch moves between 0 and alg_bytes; the kernel counts the work it did
     achieved = pinv_work / (pinv_ms / 1e3) / 1e9 if n_launch and pinv_ms > 0 else None
-    spmv_n, spmv_ms = prof["spmv"]
     roofline = {"kernel": "k_bt_solve (block-preconditioner apply, Eq. 7)", "bound": "hbm",
                 "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": (achieved / hbm_peak) if achieved else None,
@@ -417,14 +482,18 @@ def main():
                 "alg_bytes_full_launch": alg_bytes,
                 "alg_bytes_processed": pinv_work,
                 "achieved_definition": "algorithmic bytes of the subdomains processed (counted on the device) / "
-                                       "summed CUDA-event time of the launches in the timed steps",
-                "share_of_step": (pinv_ms / ms) if ms > 0 else None,
-                "spmv": {"launches": spmv_n, "avg_launch_us": 1e6 * spmv_ms / 1e3 / max(1, spmv_n),
-                         "share_of_step": (spmv_ms / ms) if ms > 0 else None}}
+                                       "summed CUDA-event time of its launches, over "
+                                       f"{max(1, args.prof_steps)} instrumented step(s) run after the timed region",
+                "share_of_step": (pinv_ms / prof_ms) if prof_ms > 0 else None,
+                "classes": kernel_classes_report(thm, prof, prof_ms),
+                "instrumented_ms_per_step": prof_ms / max(1, args.prof_steps),
+                "instrumented_time_to_1e8_s": statistics.median(s["seconds"] for s in pstats)}
 
-    # plain FP64 form, timed beside (time-to-1e-8)
+    # plain FP64 form, timed beside (time-to-1e-8); warmed first: FP64 kernels,
+    # the FP64 factorisation path and the FP64 tile autotuning on this mesh
     fp64 = None
     if mode == "mixed" and args.fp64_steps > 0:
+        step("fp64", outer_maxit=3, max_refine=1, check=False)
         torch.cuda.synchronize()
         f0 = torch.cuda.Event(enable_timing=True)
         f1 = torch.cuda.Event(enable_timing=True)
@@ -439,6 +508,8 @@ def main():
         fp64 = {"ms_per_step": fms, "time_to_1e8_s": statistics.median(s["seconds"] for s in fstats),
                 "dof_iters_per_s": sum(s["dof_iters"] for s in fstats) / (fms * args.fp64_steps / 1e3),
                 "outer_iters": fstats[-1]["outer_iters"], "inner_iters": fstats[-1]["inner_iters"],
+                "sweeps": fstats[-1]["sweeps"], "refine_steps": fstats[-1]["refine_steps"],
+                "max_inner_iters": fstats[-1]["max_inner_iters"],
                 "rel_residual": fstats[-1]["rel_residual"],
                 "mixed_speedup_time_to_1e8": statistics.median(s["seconds"] for s in fstats) / statistics.median(tt)}
 
@@ -462,14 +533,21 @@ def main():
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         try:
-            res = run_oracle_sample(1, args.ref_subdomains)
-            s, d = res["steps"][0]
-            cpu = {"value": d / s, "unit": UNIT, "cores": 1, "kind": "oracle",
-                   "sample": f"block-preconditioned GMRES (tol 1e-10) solves of subdomains {res['picks']} "
-                             f"of the first DDM sweep of the same workload, {s:.1f}s; oracle set-up "
+            res = run_oracle_sample(3, args.ref_subdomains, allcore_steps=3)
+            one = statistics.median(d / s for s, d in res["single"])
+            allc = statistics.median(d / s for s, d in res["allcore"])
+            cpu = {"value": allc, "unit": UNIT, "cores": res["allcore_workers"], "kind": "oracle",
+                   "cpu": res["cpu"], "nproc": res["nproc"], "machine": res["machine"],
+                   "single_thread": {"value": one, "cores": 1,
+                                     "sample": f"block-preconditioned GMRES (tol 1e-10) solves of subdomains "
+                                               f"{res['picks']} of the first DDM sweep, median of 3 "
+                                               f"({[round(s, 2) for s, _ in res['single']]} s)"},
+                   "sample": f"the whole first DDM sweep ({res['n_sub']} block-preconditioned GMRES subdomain "
+                             f"solves, tol 1e-10) over {res['allcore_workers']} forked single-thread workers, "
+                             f"median of 3 ({[round(s, 2) for s, _ in res['allcore']]} s); oracle set-up "
                              f"{res['setup_s']:.1f}s untimed"}
         except Exception as ex:  # noqa: BLE001
-            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {ex}"}
+            cpu = {"value": None, "unit": UNIT, "cores": None, "kind": "oracle", "sample": f"failed: {ex}"}
 
     if rank == 0:
         last = stats_all[-1]
@@ -483,6 +561,8 @@ def main():
                        "relax": args.relax,
                        "l2": "no flush: the per-step working set (operators, factors, Krylov bases) "
                              "exceeds the 129 MB L2", "step": "thm_assemble + thm_ddm_solve (rtol 1e-8)",
+                       "timed_steps": "no per-launch instrumentation; kernel timing comes from separate "
+                                      "instrumented steps after the timed region",
                        "mesh_setup_s": mesh_s},
             "time_to_1e8_s": statistics.median(tt),
             "solve": {"outer_iters": last["outer_iters"], "sweeps": last["sweeps"],
@@ -492,7 +572,8 @@ def main():
             "fp64": fp64,
             "roofline": roofline,
             "cpu_baseline": cpu,
-            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(mu_h.nbytes),
+            "e2e": {"value": e2e_val, "unit": UNIT, "seconds": e2e_t / max(1, args.e2e_steps),
+                    "h2d_bytes_per_step": int(mu_h.nbytes),
                     "d2h_bytes_per_step": int(16 * sysg.n_dof),
                     "includes": "thm_mesh_create from host arrays + thm_assemble from host mu^-1 + "
                                 "thm_ddm_solve_host"},

@@ -126,6 +126,32 @@ int thm_assemble(thm_sys** out, const thm_mesh* m, const double* mu_inv, int mu_
                  void* stream);
 
 /*
+ * thm_mesh_dirichlet_dofs -- the Dirichlet DOFs of the mesh (those on
+ * THM_TAG_DIRICHLET faces, Gamma^inc of Eq. 1), in increasing global order:
+ * the order in which thm_assemble_dirichlet takes their values.
+ *  n_dir  host output (may be NULL);  ids  host int64 [n_dir] or NULL.
+ */
+int thm_mesh_dirichlet_dofs(const thm_mesh* m, int64_t* n_dir, int64_t* ids);
+
+/*
+ * thm_assemble_dirichlet -- thm_assemble with the Dirichlet data of Eq. 1
+ * (gamma^T E = gamma^T E^inc on Gamma^inc) given by the caller instead of a
+ * plane wave: the values of the Dirichlet DOFs themselves (order 1: the
+ * tangential moment of E^inc along the edge; order 2 also the second edge
+ * moment; the same DOF definition the plane-wave path evaluates).
+ *
+ *  u_dir            complex double [n_dir] (interleaved re, im) in the order
+ *                   of thm_mesh_dirichlet_dofs; host or device
+ *                   (u_dir_on_device).  May be NULL only when n_dir = 0.
+ *  Other arguments as in thm_assemble.  A single problem only (a batch mesh
+ *  gets THM_EINVAL).  The values are copied during the call.  The adjoint of
+ *  such a system treats the data as independent of omega and kappa.
+ *  Errors: as thm_assemble; THM_EINVAL for a non-finite host value.
+ */
+int thm_assemble_dirichlet(thm_sys** out, const thm_mesh* m, const double* mu_inv, int mu_inv_on_device,
+                           double omega, double kappa, const double* u_dir, int u_dir_on_device, void* stream);
+
+/*
  * Batches of independent problems (the paper solves one problem at a time;
  * this is the batched form of the same solve).  A batch mesh is the disjoint
  * union of the problems' meshes, built with thm_mesh_create: subdomain ids are
@@ -218,13 +244,19 @@ int thm_ddm_solve_host(thm_sys* s, const thm_solve_opts* opts, double* u_host, t
  *   grad_mu_inv[c] = -2 Re(lambda_c^T A_c u_c)           (device double [n_cell])
  *   grad_omega     = -2 Re(lambda^T [(dK/domega) u + K du_D/domega])
  *                    + 2 Re(a^T du_D/domega)              (host double)
+ *   grad_kappa     = -2 Re(lambda^T (i omega M_Gamma) u)     (host double, or
+ *                    NULL when not wanted)
  * with dK/domega = -2 omega M + i kappa M_Gamma, a = dLdu_conj and du_D/domega
- * the derivative of the Dirichlet moments.  2-D (orders 1, 2) and 3-D.  u is
- * the forward solution (device complex [n_dof]); lambda is zero on Dirichlet
- * DOFs.
+ * the derivative of the Dirichlet moments (0 for caller-given Dirichlet data,
+ * thm_assemble_dirichlet).  Since s K(mu^{-1}, omega, kappa) = K(s mu^{-1},
+ * sqrt(s) omega, sqrt(s) kappa), the three gradients satisfy
+ * sum_c mu^{-1}_c grad_mu_inv[c] + (omega/2) grad_omega + (kappa/2) grad_kappa
+ * = 0 whenever the Dirichlet data do not depend on omega.  2-D (orders 1, 2)
+ * and 3-D.  u is the forward solution (device complex [n_dof]); lambda is
+ * zero on Dirichlet DOFs.
  */
 int thm_adjoint(thm_sys* s, const thm_solve_opts* opts, const double* u, const double* dLdu_conj,
-                double* grad_mu_inv, double* grad_omega, thm_stats* stats);
+                double* grad_mu_inv, double* grad_omega, double* grad_kappa, thm_stats* stats);
 
 void thm_sys_destroy(thm_sys* s);
 
@@ -317,8 +349,10 @@ int thm_work_bytes(const thm_sys* s, int mode, int cls, double* bytes);
  *  u    device complex double [n_dof]: a field on all DOFs (Dirichlet entries
  *       are ignored; the Dirichlet lifting already sits in f).
  *  out  device double[2], written on the system's stream: out[0] = ||f - K u||,
- *       out[1] = ||f|| (the global FP64 quantities of thm_stats.rel_residual =
- *       out[0] / out[1]).
+ *       out[1] = ||f||, global FP64 norms over all free DOFs.  For a single
+ *       problem out[0] / out[1] is thm_stats.rel_residual; for a batch it is
+ *       the ratio over the whole batch vector, whereas thm_stats.rel_residual
+ *       reports the largest per-problem ratio.
  *  Limit: n_dof <= 4,194,304 (4096 partial-sum blocks of 1024 DOFs); larger
  *       systems get THM_EINVAL with the limit in the message.
  *  Scratch: a file-scope device array of 64 KB, held by every GPU that loads

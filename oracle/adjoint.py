@@ -84,6 +84,13 @@ def adjoint_gradients(problem, sys_: fem.System, u: np.ndarray, a: np.ndarray):
     return g_mu, float(g_w), lam
 
 
+def kappa_gradient(problem, sys_: fem.System, u: np.ndarray, lam: np.ndarray) -> float:
+    """dL/dkappa = -2 Re(lambda^T (dK/dkappa) u) with dK/dkappa = i omega M_Gamma
+    (the impedance term of Eq. 1 is the only place kappa enters; the Dirichlet
+    data do not depend on it)."""
+    return float(-2.0 * np.real(lam @ (1j * problem.omega * (sys_.Mg @ u))))
+
+
 def gradients_by_fd(problem, MR, cells_to_check, h=1e-6, d_omega=True):
     """Central finite differences of L through the monolithic solve."""
     import copy

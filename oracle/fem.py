@@ -396,6 +396,18 @@ def assemble(problem) -> System:
     return System(dofs, K, A.tocsr(), M.tocsr(), Mg.tocsr(), is_d, uD, free, f)
 
 
+def with_dirichlet(sys_: System, values: np.ndarray) -> System:
+    """The same discrete problem with the Dirichlet trace of Eq. 1 given
+    directly as the values of the Dirichlet DOFs (`values`, complex, in
+    increasing global-DOF order) instead of the moments of a plane wave:
+    u_D replaced and f = -K_FD u_D formed again."""
+    dd = np.flatnonzero(sys_.is_dir)
+    uD = np.zeros(sys_.dofs.n_dof, np.complex128)
+    uD[dd] = values
+    f = -(sys_.K[sys_.free][:, dd] @ uD[dd])
+    return System(sys_.dofs, sys_.K, sys_.A, sys_.M, sys_.Mg, sys_.is_dir, uD, sys_.free, f)
+
+
 def solve_monolithic(sys_: System) -> np.ndarray:
     """The plain definition of the discrete solution: u_F = K_FF^{-1}(-K_FD u_D)."""
     Kff = sys_.K[sys_.free][:, sys_.free].tocsc()

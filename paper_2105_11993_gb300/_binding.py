@@ -24,6 +24,7 @@ symbols = [
     "thm_local_dofs", "thm_iface_dofs", "thm_apply_local", "thm_sweep", "thm_local_sources",
     "thm_dirichlet_values", "thm_kernel_launches", "thm_profile_enable", "thm_profile_read",
     "thm_alg_bytes", "thm_residual_noalloc", "thm_mesh_set_problems", "thm_assemble_batch", "thm_work_bytes",
+    "thm_mesh_dirichlet_dofs", "thm_assemble_dirichlet",
 ]
 
 
@@ -73,7 +74,9 @@ def load():
         "thm_assemble_batch": [C.POINTER(P), P, P, C.c_int, P, C.c_double, P, P, P],
         "thm_ddm_solve": [P, P, P, P],
         "thm_ddm_solve_host": [P, P, P, P],
-        "thm_adjoint": [P, P, P, P, P, P, P],
+        "thm_adjoint": [P, P, P, P, P, P, P, P],
+        "thm_mesh_dirichlet_dofs": [P, P, P],
+        "thm_assemble_dirichlet": [C.POINTER(P), P, P, C.c_int, C.c_double, C.c_double, P, C.c_int, P],
         "thm_sys_destroy": [P],
         "thm_last_error": [],
         "thm_sys_info": [P, P, P, P, P],
@@ -201,6 +204,16 @@ class Mesh:
         m.set_problems(np.concatenate(sub_prob))
         return m, offs
 
+    def dirichlet_dofs(self):
+        """thm_mesh_dirichlet_dofs: the Dirichlet DOFs, increasing."""
+        lib = load()
+        n = I64()
+        _check(lib.thm_mesh_dirichlet_dofs(self.h, C.byref(n), None))
+        ids = np.empty(n.value, np.int64)
+        if n.value:
+            _check(lib.thm_mesh_dirichlet_dofs(self.h, None, _ptr(ids)))
+        return ids
+
     def info(self, with_dofs=False):
         lib = load()
         nd, ne, ns, dpc = I64(), I64(), C.c_int32(), C.c_int32()
@@ -233,13 +246,18 @@ def _opts(mode="fp64", rtol=1e-8, inner_restart=0, inner_tol=0.0, inner_maxit=0,
 class System:
     """thm_assemble: subdomain operators, Dirichlet data, preconditioner."""
 
-    def __init__(self, mesh: Mesh, mu_inv, omega, kappa, pol, direction, stream=None):
+    def __init__(self, mesh: Mesh, mu_inv, omega, kappa, pol=None, direction=None, stream=None, dirichlet=None):
+        """pol/direction: plane-wave Dirichlet data (thm_assemble); or
+        dirichlet: complex values of the Dirichlet DOFs in the order of
+        mesh.dirichlet_dofs(), numpy or a CUDA tensor (thm_assemble_dirichlet)."""
         lib = load()
         torch = _torch()
         self.mesh = mesh
-        polr = np.zeros((3, 2)); pol = np.asarray(pol, np.complex128)
-        polr[:len(pol), 0] = pol.real; polr[:len(pol), 1] = pol.imag
-        d = np.zeros(3); d[:len(direction)] = direction
+        polr = np.zeros((3, 2)); d = np.zeros(3)
+        if dirichlet is None:
+            pol = np.asarray(pol, np.complex128)
+            polr[:len(pol), 0] = pol.real; polr[:len(pol), 1] = pol.imag
+            d[:len(direction)] = direction
         self._pol, self._dir = np.ascontiguousarray(polr), d
         st = stream if stream is not None else torch.cuda.current_stream()
         self.stream = st
@@ -248,7 +266,21 @@ class System:
         if batch:
             self._omega = np.ascontiguousarray(omega, np.float64)
 
+        if dirichlet is not None:
+            if isinstance(dirichlet, torch.Tensor):
+                dv = dirichlet.to(torch.complex128).contiguous()
+                assert dv.is_cuda
+                dptr, don = _dptr(dv), 1
+            else:
+                dv = np.ascontiguousarray(dirichlet, np.complex128)
+                dptr, don = _ptr(dv), 0
+            self._dir = dv
+
         def assemble(mu_ptr, on_device):
+            if dirichlet is not None:
+                assert not batch, "caller-given Dirichlet data: single problems only"
+                return lib.thm_assemble_dirichlet(C.byref(h), mesh.h, mu_ptr, on_device, float(omega), float(kappa),
+                                                  dptr, don, C.c_void_p(st.cuda_stream))
             if batch:
                 return lib.thm_assemble_batch(C.byref(h), mesh.h, mu_ptr, on_device, _ptr(self._omega),
                                               float(kappa), _ptr(self._pol), _ptr(self._dir),
@@ -293,14 +325,18 @@ class System:
         _check(load().thm_ddm_solve_host(self.h, C.byref(o), _ptr(u), C.byref(st)))
         return u, st.to_dict()
 
-    def adjoint(self, u, dL_du, mode="fp64", **kw):
+    def adjoint(self, u, dL_du, mode="fp64", with_kappa=False, **kw):
+        """thm_adjoint -> (dL/dmu^{-1} [n_cell] cuda tensor, dL/domega, stats)
+        or, with_kappa=True, (dL/dmu^{-1}, dL/domega, dL/dkappa, stats)."""
         torch = _torch()
         g = torch.empty(self.mesh.n_cell, dtype=torch.float64, device="cuda")
-        gw = C.c_double()
+        gw, gk = C.c_double(), C.c_double()
         st = Stats()
         o = _opts(mode, **kw)
         _check(load().thm_adjoint(self.h, C.byref(o), _dptr(u.contiguous()), _dptr(dL_du.contiguous()),
-                                  _dptr(g), C.byref(gw), C.byref(st)))
+                                  _dptr(g), C.byref(gw), C.byref(gk) if with_kappa else None, C.byref(st)))
+        if with_kappa:
+            return g, gw.value, gk.value, st.to_dict()
         return g, gw.value, st.to_dict()
 
     def apply_local(self, op, x, mode="fp64"):

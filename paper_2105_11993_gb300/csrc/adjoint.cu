@@ -5,6 +5,7 @@
 //   dL/dmu_c  = -2 Re(lambda_c^T A_c u_c)
 //   dL/domega = -2 Re(lambda^T [(-2 omega M + i kappa M_Gamma) u + K du_D/domega])
 //               + 2 Re(a . du_D/domega)
+//   dL/dkappa = -2 Re(lambda^T (i omega M_Gamma) u)
 // with lambda = 0 on Dirichlet DOFs.  The forward solution u is an input (it is
 // recomputed by the caller, not stored with Krylov bases).
 #include <chrono>
@@ -108,9 +109,10 @@ __global__ void k_adj_cells(int dim, int64_t n_cell, int nb, const double* __res
     gw[c] = -2.0 * (-2.0 * omega * sM.x) - 2.0 * sD.x;
 }
 
-// Gamma^inf face share of dL/domega: with m_f the signed face mass and
-// K's face term i kappa omega m_f,
-//   -2 Re(lambda^T (i kappa m_f) u) - 2 Re(lambda^T (i kappa omega m_f) du_D/domega)
+// Gamma^inf face share of dL/domega and of dL/dkappa: with m_f the signed face
+// mass and K's face term i kappa omega m_f,
+//   dL/domega: -2 Re(lambda^T (i kappa m_f) u) - 2 Re(lambda^T (i kappa omega m_f) du_D/domega)
+//   dL/dkappa: -2 Re(lambda^T (i omega m_f) u)   (the Dirichlet data do not depend on kappa)
 // (u includes the Dirichlet values; in 3-D an impedance face may hold edges
 // of the Dirichlet boundary, so both terms reach Dirichlet columns).
 __global__ void k_adj_faces(int dim, int64_t n_face, int fd, const double* __restrict__ ref,
@@ -118,10 +120,10 @@ __global__ void k_adj_faces(int dim, int64_t n_face, int fd, const double* __res
                             const int32_t* __restrict__ face_dof, const int8_t* __restrict__ face_sgn,
                             const int8_t* __restrict__ face_kind, double kappa, double omega,
                             const double2* __restrict__ lam, const double2* __restrict__ u,
-                            const double2* __restrict__ duD, double* __restrict__ gw) {
+                            const double2* __restrict__ duD, double* __restrict__ gw, double* __restrict__ gk) {
     int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (f >= n_face) return;
-    if (face_kind[f] != 1) { gw[f] = 0; return; }
+    if (face_kind[f] != 1) { gw[f] = 0; gk[f] = 0; return; }
     double2 s1 = make_double2(0, 0), s2 = make_double2(0, 0);
     for (int a = 0; a < fd; ++a) {
         const int32_t da = face_dof[f * fd + a];
@@ -136,6 +138,7 @@ __global__ void k_adj_faces(int dim, int64_t n_face, int fd, const double* __res
         }
     }
     gw[f] = 2.0 * kappa * s1.y + 2.0 * kappa * omega * s2.y;      // -2 Re(i c z) = 2 c Im(z)
+    gk[f] = 2.0 * omega * s1.y;                                    // dK/dkappa = i omega M_Gamma
 }
 
 __global__ void k_adj_dir(int64_t n_dof, const double2* __restrict__ a, const double2* __restrict__ duD,
@@ -170,7 +173,7 @@ static double device_sum(cudaStream_t st, const double* x, int64_t n, DArr<doubl
 }
 
 int adjoint(thm_sys* s, const thm_solve_opts* opts, const double2* u, const double2* a, double* grad_mu,
-            double* grad_omega, thm_stats* stats) {
+            double* grad_omega, double* grad_kappa, thm_stats* stats) {
     auto t0 = std::chrono::steady_clock::now();
     const thm_mesh* m = s->m;
     THM_REQUIRE(m->n_prob == 1, "the adjoint takes a single problem, not a batch");
@@ -179,17 +182,20 @@ int adjoint(thm_sys* s, const thm_solve_opts* opts, const double2* u, const doub
     prepare(s, c);
     auto nb = [](int64_t n) { return (unsigned)((n + 255) / 256); };
     DArr<double2> rhs, lam, duD;
-    DArr<double> gw_cell, gw_face, gw_dof, part;
+    DArr<double> gw_cell, gw_face, gk_face, gw_dof, part;
     rhs.alloc(m->n_loc); lam.alloc(m->n_dof); duD.alloc(m->n_dof);
     gw_cell.alloc(m->n_cell); gw_face.alloc(std::max<int64_t>(1, m->n_face)); gw_dof.alloc(m->n_dof);
+    gk_face.alloc(std::max<int64_t>(1, m->n_face));
     part.alloc(256);
     gw_face.zero(st);
+    gk_face.zero(st);
     THM_LAUNCH(THM_K_DDM, st, k_adj_rhs<<<nb(m->n_loc), 256, 0, st>>>(m->n_loc, m->d_loc_gdof.p, m->d_loc_is_owner.p, a, rhs.p));
     RunStats rs;
     double rel = 0;
     int rc = solve_rhs(s, c, rhs.p, rhs.p, nullptr, lam.p, rs, rel);
     duD.zero(st);
-    if (!m->dir_edges.empty())
+    // caller-given Dirichlet values (thm_assemble_dirichlet) do not depend on omega
+    if (!m->dir_edges.empty() && !s->dir_user)
         THM_LAUNCH(THM_K_DDM, st, k_dirichlet_dw<<<nb((int64_t)m->dir_edges.size()), 256, 0, st>>>(
             (int64_t)m->dir_edges.size(), m->dim, m->order, m->d_dir_edges.p, m->d_coords.p, m->d_edge_lo.p,
             m->d_edge_hi.p, s->omega, s->pol[0], s->pol[1], s->pol[2], s->pol[3], s->pol[4], s->pol[5], s->dir[0],
@@ -201,11 +207,12 @@ int adjoint(thm_sys* s, const thm_solve_opts* opts, const double2* u, const doub
     if (m->n_face > 0)
         THM_LAUNCH(THM_K_DDM, st, k_adj_faces<<<nb(m->n_face), 256, 0, st>>>(
             m->dim, m->n_face, m->fd, s->ref.p, m->d_coords.p, m->d_face_v.p, m->d_face_dof.p, m->d_face_sgn.p,
-            m->d_face_kind.p, s->kappa, s->omega, lam.p, u, duD.p, gw_face.p));
+            m->d_face_kind.p, s->kappa, s->omega, lam.p, u, duD.p, gw_face.p, gk_face.p));
     THM_LAUNCH(THM_K_DDM, st, k_adj_dir<<<nb(m->n_dof), 256, 0, st>>>(m->n_dof, a, duD.p, gw_dof.p));
     THM_CUDA(cudaGetLastError());
     *grad_omega = device_sum(st, gw_cell.p, m->n_cell, part) + device_sum(st, gw_face.p, std::max<int64_t>(1, m->n_face), part) +
                   device_sum(st, gw_dof.p, m->n_dof, part);
+    if (grad_kappa) *grad_kappa = device_sum(st, gk_face.p, std::max<int64_t>(1, m->n_face), part);
     double sec = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     fill_stats(rs, rel, sec, stats);
     return rc;

@@ -299,6 +299,13 @@ __global__ void k_dirichlet(int64_t n_de, int dim, int order, const int64_t* __r
     }
 }
 
+// Dirichlet values given by the caller: u_D[ids[t]] = vals[t].
+__global__ void k_dirichlet_given(int64_t n_dir, const int64_t* __restrict__ ids, const double2* __restrict__ vals,
+                                  double2* __restrict__ uD) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t < n_dir) uD[ids[t]] = vals[t];
+}
+
 // Lifting: f_i = -(P_i)_{F,D} u_D from the cells of each row (2-D: the face
 // terms never couple a free DOF to a Dirichlet one).
 __global__ void k_lifting(int dim, int64_t n_loc, int nb, int maxc, const double* __restrict__ ref,
@@ -782,7 +789,14 @@ void assemble(thm_sys* s) {
     }
     s->uD.alloc(m->n_dof);
     s->uD.zero(st);
-    if (!m->dir_edges.empty()) {
+    if (s->dir_user) {
+        const int64_t nd = (int64_t)m->dir_dofs.size();
+        if (nd > 0) {
+            THM_LAUNCH(THM_K_SETUP, st, k_dirichlet_given<<<grid(nd), th, 0, st>>>(nd, m->d_dir_dofs.p, s->dir_vals.p,
+                                                                                  s->uD.p));
+            THM_CUDA(cudaGetLastError());
+        }
+    } else if (!m->dir_edges.empty()) {
         THM_LAUNCH(THM_K_SETUP, st, k_dirichlet<<<grid((int64_t)m->dir_edges.size()), th, 0, st>>>(
             (int64_t)m->dir_edges.size(), m->dim, m->order, m->d_dir_edges.p, m->d_coords.p, m->d_edge_lo.p,
             m->d_edge_hi.p, s->omd.p, s->pol[0], s->pol[1], s->pol[2], s->pol[3], s->pol[4], s->pol[5],

@@ -11,7 +11,7 @@ void apply_local(thm_sys* s, int op, int mode, const double2* x, double2* y);
 int sweep_diag(thm_sys* s, const thm_solve_opts* opts, int with_sources, const double2* g_in, double2* g_out,
                double2* uloc, thm_stats* stats);
 int adjoint(thm_sys* s, const thm_solve_opts* opts, const double2* u, const double2* rhs, double* grad_mu,
-            double* grad_omega, thm_stats* stats);
+            double* grad_omega, double* grad_kappa, thm_stats* stats);
 
 extern std::atomic<long long> g_launches;
 static thread_local std::string g_msg;
@@ -115,9 +115,11 @@ void thm_mesh_destroy(thm_mesh* m) { delete m; }
 
 static int assemble_common(thm_sys** out, const thm_mesh* m, const double* mu_inv, int mu_inv_on_device,
                            const std::vector<double>& omegas, double kappa, const double* pol, const double* dir,
-                           void* stream) {
+                           void* stream, const double* u_dir = nullptr, int u_dir_on_device = 0) {
     return guarded([&]() -> int {
-        THM_REQUIRE(out && m && mu_inv && pol && dir, "NULL argument");
+        THM_REQUIRE(out && m && mu_inv, "NULL argument");
+        const bool given = u_dir != nullptr;
+        THM_REQUIRE(given || (pol && dir), "NULL argument (plane-wave polarisation / direction)");
         *out = nullptr;
         THM_REQUIRE((int)omegas.size() == m->n_prob, "one omega per problem required");
         for (double w : omegas) THM_REQUIRE(std::isfinite(w) && w > 0, "omega must be > 0");
@@ -129,10 +131,27 @@ static int assemble_common(thm_sys** out, const thm_mesh* m, const double* mu_in
             s->omega = omegas[0];
             s->omega_prob = omegas;
             s->kappa = kappa;
-            for (int k = 0; k < m->dim; ++k) {
-                s->pol[2 * k] = pol[2 * k];
-                s->pol[2 * k + 1] = pol[2 * k + 1];
-                s->dir[k] = dir[k];
+            if (given) {
+                const int64_t nd = (int64_t)m->dir_dofs.size();
+                s->dir_user = true;
+                s->dir_vals.alloc(nd > 0 ? nd : 1);
+                if (nd > 0) {
+                    if (u_dir_on_device) {
+                        THM_CUDA(cudaMemcpyAsync(s->dir_vals.p, u_dir, nd * sizeof(double2), cudaMemcpyDeviceToDevice,
+                                                 s->st));
+                    } else {
+                        for (int64_t i = 0; i < 2 * nd; ++i)
+                            THM_REQUIRE(std::isfinite(u_dir[i]), "non-finite Dirichlet value");
+                        THM_CUDA(cudaMemcpyAsync(s->dir_vals.p, u_dir, nd * sizeof(double2), cudaMemcpyHostToDevice,
+                                                 s->st));
+                    }
+                }
+            } else {
+                for (int k = 0; k < m->dim; ++k) {
+                    s->pol[2 * k] = pol[2 * k];
+                    s->pol[2 * k + 1] = pol[2 * k + 1];
+                    s->dir[k] = dir[k];
+                }
             }
             s->mu_inv.alloc(m->n_cell);
             if (mu_inv_on_device) {
@@ -161,6 +180,32 @@ int thm_assemble(thm_sys** out, const thm_mesh* m, const double* mu_inv, int mu_
         return THM_EINVAL;
     }
     return assemble_common(out, m, mu_inv, mu_inv_on_device, std::vector<double>{omega}, kappa, pol, dir, stream);
+}
+
+int thm_assemble_dirichlet(thm_sys** out, const thm_mesh* m, const double* mu_inv, int mu_inv_on_device,
+                           double omega, double kappa, const double* u_dir, int u_dir_on_device, void* stream) {
+    if (m && m->n_prob != 1) {
+        set_last_error("thm_assemble_dirichlet takes a single problem, not a batch");
+        if (out) *out = nullptr;
+        return THM_EINVAL;
+    }
+    if (m && !m->dir_dofs.empty() && !u_dir) {
+        set_last_error("u_dir is NULL but the mesh has Dirichlet DOFs");
+        if (out) *out = nullptr;
+        return THM_EINVAL;
+    }
+    static const double none = 0.0;
+    return assemble_common(out, m, mu_inv, mu_inv_on_device, std::vector<double>{omega}, kappa, nullptr, nullptr,
+                           stream, u_dir ? u_dir : &none, u_dir_on_device);
+}
+
+int thm_mesh_dirichlet_dofs(const thm_mesh* m, int64_t* n_dir, int64_t* ids) {
+    return guarded([&]() -> int {
+        THM_REQUIRE(m, "mesh is NULL");
+        if (n_dir) *n_dir = (int64_t)m->dir_dofs.size();
+        if (ids) std::copy(m->dir_dofs.begin(), m->dir_dofs.end(), ids);
+        return THM_OK;
+    });
 }
 
 int thm_mesh_set_problems(thm_mesh* m, int32_t n_prob, const int32_t* sub_problem) {
@@ -246,11 +291,11 @@ int thm_ddm_solve_host(thm_sys* s, const thm_solve_opts* opts, double* u_host, t
 }
 
 int thm_adjoint(thm_sys* s, const thm_solve_opts* opts, const double* u, const double* dLdu_conj,
-                double* grad_mu_inv, double* grad_omega, thm_stats* stats) {
+                double* grad_mu_inv, double* grad_omega, double* grad_kappa, thm_stats* stats) {
     return guarded([&]() -> int {
         THM_REQUIRE(s && u && dLdu_conj && grad_mu_inv && grad_omega, "NULL argument");
         return adjoint(s, opts, reinterpret_cast<const double2*>(u), reinterpret_cast<const double2*>(dLdu_conj),
-                       grad_mu_inv, grad_omega, stats);
+                       grad_mu_inv, grad_omega, grad_kappa, stats);
     });
 }
 

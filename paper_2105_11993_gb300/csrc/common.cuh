@@ -132,6 +132,8 @@ struct thm_mesh {
     std::vector<int8_t> cell_signs;                 // [n_cell][dpc]
     std::vector<uint8_t> is_dir;                    // [n_dof]
     std::vector<int64_t> dir_edges;                 // edges carrying Dirichlet DOFs
+    std::vector<int64_t> dir_dofs;                  // Dirichlet DOFs, increasing
+    thm::DArr<int64_t> d_dir_dofs;
 
     // local (per-subdomain, free DOFs) structure
     int64_t n_loc = 0;
@@ -168,6 +170,11 @@ struct thm_mesh {
     std::vector<int64_t> bt_welem;                  // [n_sub] values one block solve reads (W, couplings, tables)
     thm::DArr<int64_t> d_bt_welem;
     int64_t fac_elems = 0;
+    // W-tile size of the block-solve kernel picked by its autotuner ([0] FP64
+    // factors, [1] FP32), 0 until the first apply of a system on this mesh.
+    // The factor layout (levels, block sizes) is the mesh's, so every system
+    // assembled on the mesh reuses the choice.
+    mutable size_t bt_tile[2] = {0, 0};
     // level couplings of S as compact CSR lists (columns local to the
     // neighbouring level; slot = position of the value in the SELL arrays)
     std::vector<int32_t> cpl_ptr, cpl_col;
@@ -242,6 +249,10 @@ struct thm_sys {
     thm::DArr<double> bvg64, bvs64;    // 3-D: kappa*omega face masses on the SELL pattern (Gamma^inf, Sigma)
     thm::DArr<float> bvg32, bvs32;
     thm::DArr<double2> uD;             // [n_dof] Dirichlet values
+    // Dirichlet values given by the caller (thm_assemble_dirichlet) instead of
+    // the moments of a plane wave: [n_dir] in increasing global-DOF order
+    bool dir_user = false;
+    thm::DArr<double2> dir_vals;
     thm::DArr<double2> f_loc;          // [n_loc] subdomain sources: -(T_i)_{F,D} u_D (Eq. 5)
     thm::DArr<double2> f_res;          // [n_loc] split of the global right-hand side: -(K_i^loc)_{F,D} u_D
     // block-tridiagonal factors of P_i (lazily built per precision)
@@ -262,9 +273,6 @@ struct thm_sys {
     thm::DArr<int32_t> tab_ai, tab_ci, tab_ei;
     thm::DArr<double> tab_av64, tab_cv64, tab_ev64;
     thm::DArr<float> tab_av32, tab_cv32, tab_ev32;
-    // W-tile size of the block-solve kernel picked by its autotuner ([0] FP64
-    // factors, [1] FP32), 0 until the first apply
-    mutable size_t bt_tile[2] = {0, 0};
     // block-solve work actually done, per factor precision ([0..1] FP64, [2..3]
     // FP32): values read and local rows processed, summed by the kernel over
     // the subdomains it did not skip

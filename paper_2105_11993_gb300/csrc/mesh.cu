@@ -744,6 +744,10 @@ void build_mesh(thm_mesh* m) {
     m->d_bt_welem.upload(m->bt_welem);
     m->d_chunks.upload(m->chunks);
     m->d_dir_edges.upload(m->dir_edges);
+    m->dir_dofs.clear();
+    for (int64_t g = 0; g < m->n_dof; ++g)
+        if (m->is_dir[g]) m->dir_dofs.push_back(g);
+    m->d_dir_dofs.upload(m->dir_dofs);
     m->d_loc_gdof.upload(m->loc_gdof);
     m->d_loc_sub.upload(m->loc_sub);
     m->d_if_rowi.upload(m->if_rowi);

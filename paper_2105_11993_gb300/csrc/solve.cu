@@ -655,10 +655,10 @@ static void bt_launch(const thm_sys* s, const BtCfg& c, const F* fac, const F* c
                    s->bt_work.p ? s->bt_work.p + (sizeof(F) == 4 ? 2 : 0) : nullptr, x, y));
 }
 
-// The tile size is tuned once per system and factor precision: on the first
-// apply every candidate runs on the caller's vectors (the result is the same
-// each time) and the fastest of two timed launches wins.  THM_BT_TILE_BYTES
-// fixes it instead.
+// The tile size is tuned once per mesh and factor precision: on the first
+// apply of a system every candidate runs on the caller's vectors (the result
+// is the same each time) and the fastest of two timed launches wins; later
+// systems on the same mesh reuse it.  THM_BT_TILE_BYTES fixes it instead.
 template <class V, class F>
 static void apply_Pinv(const thm_sys* s, const F* fac, const F* cval, const int32_t* ai, const F* av,
                        const int32_t* ci, const F* cv, const int32_t* ei, const F* ev, const V* x, V* y,
@@ -666,7 +666,7 @@ static void apply_Pinv(const thm_sys* s, const F* fac, const F* cval, const int3
     const thm_mesh* m = s->m;
     THM_REQUIRE(m->max_m <= BT_MAX_M, "level block larger than the block-solve kernel supports (" +
                                           std::to_string(m->max_m) + " > " + std::to_string(BT_MAX_M) + ")");
-    size_t& tile = s->bt_tile[sizeof(F) == 4 ? 1 : 0];
+    size_t& tile = m->bt_tile[sizeof(F) == 4 ? 1 : 0];
     if (!s->bt_work.p) {
         s->bt_work.alloc(4);
         s->bt_work.zero(s->st);

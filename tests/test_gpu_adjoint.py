@@ -103,18 +103,48 @@ def test_adjoint_3d_matches_oracle_adjoint(mode):
     assert abs(g_w - gw_ref) <= 1e-8 * abs(gw_ref)
 
 
-def test_adjoint_3d_vs_central_differences():
-    """3-D (12^3 hexes, 3x3x3 subdomains, smooth random mu^{-1} as in the
-    48^3 differentiation workload, oblique incidence): gradients from one
-    adjoint solve against central differences (h = 1e-4) of the GPU solve
-    itself, to 1e-5 relative."""
-    import paper_2105_11993_gb300 as thm
+def _cube12():
+    """The 12^3 copy of the 48^3 differentiation workload: 3x3x3 subdomains,
+    smooth random mu^{-1} (the same generator), oblique incidence, the loss
+    over the central 2^3 cells (the 8^3 of 48^3 scaled)."""
     n = 12
     mu = W.mu_inv_smooth_3d(n, 0.3, 3.0, "adj12/mu")
     P = W.cube_problem(n, 3, 3 * np.pi, mu_inv=mu)
     P.direction = np.array([0.6, 0.8, 0.0])
     X = P.mesh.coords[P.mesh.cells].mean(1)
     region = np.flatnonzero(np.all((X >= 5 / n) & (X < 7 / n), axis=1))
+    return P, region
+
+
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+def test_adjoint_12cube_matches_oracle_adjoint(mode):
+    """The 12^3 copy of the differentiation workload: every dL/dmu^{-1}, dL/domega
+    and dL/dkappa against the FP64 CPU oracle adjoint."""
+    import paper_2105_11993_gb300 as thm
+    P, region = _cube12()
+    S = fem.assemble(P)
+    MR = adj.region_mass(P, S, region)
+    mesh = thm.Mesh.from_workload(P.mesh, P.order)
+    sysg = thm.System(mesh, P.mu_inv, P.omega, P.kappa, P.pol, P.direction)
+    tol = 1e-12 if mode == "fp64" else 1e-11
+    u, _ = sysg.solve(mode=mode, rtol=tol)
+    a = MR @ np.conj(u.cpu().numpy())
+    g_mu, g_w, g_k, _ = sysg.adjoint(u, torch.tensor(a, device="cuda"), mode=mode, rtol=tol, with_kappa=True)
+    u0 = fem.solve_monolithic(S)
+    g_ref, gw_ref, lam = adj.adjoint_gradients(P, S, u0, MR @ np.conj(u0))
+    gk_ref = adj.kappa_gradient(P, S, u0, lam)
+    assert np.linalg.norm(g_mu.cpu().numpy() - g_ref) <= 1e-8 * np.linalg.norm(g_ref)
+    assert abs(g_w - gw_ref) <= 1e-8 * abs(gw_ref)
+    assert abs(g_k - gk_ref) <= 1e-8 * abs(gk_ref)
+
+
+def test_adjoint_3d_vs_central_differences():
+    """3-D (12^3 hexes, 3x3x3 subdomains, smooth random mu^{-1} as in the
+    48^3 differentiation workload, oblique incidence): gradients from one
+    adjoint solve against central differences (h = 1e-4) of the GPU solve
+    itself, to 1e-5 relative, at 20 random cells and in omega."""
+    import paper_2105_11993_gb300 as thm
+    P, region = _cube12()
     S = fem.assemble(P)
     MR = torch.tensor(adj.region_mass(P, S, region).toarray(), dtype=torch.complex128, device="cuda")
     mesh = thm.Mesh.from_workload(P.mesh, P.order)
@@ -131,10 +161,54 @@ def test_adjoint_3d_vs_central_differences():
     L = lambda uu: float(torch.real(torch.vdot(uu, MR @ uu)))
     h = 1e-4
     scale = np.abs(g_mu).max()
-    for c in np.random.default_rng(7).choice(P.mesh.n_cell, 3, replace=False):
+    for c in np.random.default_rng(7).choice(P.mesh.n_cell, 20, replace=False):
         mp = P.mu_inv.copy(); mp[c] += h
         mm = P.mu_inv.copy(); mm[c] -= h
         fd = (L(solve(mp, P.omega)[1]) - L(solve(mm, P.omega)[1])) / (2 * h)
         assert abs(g_mu[c] - fd) <= 1e-5 * max(abs(fd), 1e-3 * scale), (c, g_mu[c], fd)
     fdw = (L(solve(P.mu_inv, P.omega + h)[1]) - L(solve(P.mu_inv, P.omega - h)[1])) / (2 * h)
     assert abs(g_w - fdw) <= 1e-5 * abs(fdw), (g_w, fdw)
+
+
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+def test_given_dirichlet_data_solve_adjoint_and_scaling_invariant(mode):
+    """thm_assemble_dirichlet: arbitrary Dirichlet values (not a plane wave)
+    against the oracle's monolithic solve with the same values; the adjoint of
+    that system (data independent of omega and kappa) against the oracle
+    adjoint, dL/dkappa included; and the scaling invariant
+    sum_c mu_c dL/dmu_c + (omega/2) dL/domega + (kappa/2) dL/dkappa = 0
+    on the GPU gradients."""
+    import paper_2105_11993_gb300 as thm
+    P = W.square_problem(12, 2, 2, 9.0, mu_inv=W.mu_inv_lognormal(144, 0.3, "given-gpu"), relabel=True,
+                         rotate_cells=True)
+    S = fem.assemble(P)
+    mesh = thm.Mesh.from_workload(P.mesh, P.order)
+    ids = mesh.dirichlet_dofs()
+    assert np.array_equal(ids, np.flatnonzero(S.is_dir))
+    r = np.random.default_rng(17)
+    d = r.standard_normal(len(ids)) + 1j * r.standard_normal(len(ids))
+    Sg = fem.with_dirichlet(S, d)
+    u0 = fem.solve_monolithic(Sg)
+    tol = 1e-12 if mode == "fp64" else 1e-11
+    for on_device in (False, True):
+        sysg = thm.System(mesh, P.mu_inv, P.omega, P.kappa, stream=None,
+                          dirichlet=torch.tensor(d, device="cuda") if on_device else d)
+        u, st = sysg.solve(mode=mode, rtol=tol)
+        uh = u.cpu().numpy()
+        assert np.array_equal(uh[ids], d)
+        assert np.linalg.norm(uh - u0) <= (1e-8 if mode == "fp64" else 1e-6) * np.linalg.norm(u0)
+    X = P.mesh.coords[P.mesh.cells].mean(1)
+    region = np.flatnonzero((X[:, 0] > 0.3) & (X[:, 0] < 0.7) & (X[:, 1] > 0.3) & (X[:, 1] < 0.7))
+    MR = adj.region_mass(P, S, region)
+    g_mu, g_w, g_k, _ = sysg.adjoint(u, torch.tensor(MR @ np.conj(uh), device="cuda"), mode=mode, rtol=tol,
+                                     with_kappa=True)
+    g_mu = g_mu.cpu().numpy()
+    # oracle: data independent of omega (direction (1,0): zero phase on x = 0)
+    assert np.allclose(adj.dirichlet_domega(P, Sg), 0)
+    g_ref, gw_ref, lam = adj.adjoint_gradients(P, Sg, u0, MR @ np.conj(u0))
+    gk_ref = adj.kappa_gradient(P, Sg, u0, lam)
+    assert np.linalg.norm(g_mu - g_ref) <= 1e-8 * np.linalg.norm(g_ref)
+    assert abs(g_w - gw_ref) <= 1e-8 * abs(gw_ref)
+    assert abs(g_k - gk_ref) <= 1e-8 * abs(gk_ref)
+    total = np.sum(P.mu_inv * g_mu) + 0.5 * P.omega * g_w + 0.5 * P.kappa * g_k
+    assert abs(total) <= 1e-9 * (np.abs(P.mu_inv * g_mu).sum() + abs(P.omega * g_w))

@@ -48,8 +48,7 @@ def test_scaling_invariant():
     MR = adj.region_mass(P, S, np.arange(0, 36, 3))
     a = MR @ np.conj(u)
     g_mu, g_w, lam = adj.adjoint_gradients(P, S, u, a)
-    # dL/dkappa = -2 Re(lambda^T (i omega M_Gamma) u)
-    g_k = -2.0 * np.real(lam @ (1j * P.omega * (S.Mg @ u)))
+    g_k = adj.kappa_gradient(P, S, u, lam)
     total = np.sum(P.mu_inv * g_mu) + 0.5 * P.omega * g_w + 0.5 * P.kappa * g_k
     assert abs(total) <= 1e-9 * (np.abs(P.mu_inv * g_mu).sum() + abs(P.omega * g_w))
 
@@ -72,3 +71,23 @@ def test_adjoint_3d_matches_central_differences():
     for c in cells:
         assert abs(g_mu[c] - fd[int(c)]) <= 1e-6 * scale + 1e-7 * abs(fd[int(c)])
     assert abs(g_w - fd["omega"]) <= 1e-6 * max(abs(fd["omega"]), scale)
+
+
+def test_kappa_gradient_matches_central_differences():
+    """dL/dkappa from the adjoint against central differences in kappa
+    through the monolithic solve (oblique incidence, order 2)."""
+    P = _problem(2, True)
+    S = fem.assemble(P)
+    u = fem.solve_monolithic(S)
+    MR = adj.region_mass(P, S, np.arange(0, 36, 2))
+    _, _, lam = adj.adjoint_gradients(P, S, u, MR @ np.conj(u))
+    g_k = adj.kappa_gradient(P, S, u, lam)
+
+    def L_of(kappa):
+        Q = copy.copy(P)
+        Q.kappa = kappa
+        return adj.loss(fem.solve_monolithic(fem.assemble(Q)), MR)
+
+    h = 1e-5
+    fd = (L_of(P.kappa + h) - L_of(P.kappa - h)) / (2 * h)
+    assert abs(g_k - fd) <= 1e-6 * abs(fd)

@@ -309,3 +309,25 @@ def test_subdomain_blocks_balanced_when_side_does_not_divide():
     for P in probs:
         n = P.mesh.shape[0]
         assert P.mesh.n_sub == int(np.ceil(n / 32)) ** 2
+
+
+def test_given_dirichlet_values_superpose_and_reproduce_the_plane_wave():
+    """fem.with_dirichlet: Dirichlet values given as DOF values.  With the
+    plane wave's own moments it is the plane-wave problem (same solution);
+    the solution is linear in the data (superposition of two random data
+    sets), and its Dirichlet entries are the data."""
+    P = W.square_problem(6, 2, 2, 7.0, mu_inv=W.mu_inv_lognormal(36, 0.3, "given"), relabel=True,
+                         rotate_cells=True)
+    S = fem.assemble(P)
+    dd = np.flatnonzero(S.is_dir)
+    u_pw = fem.solve_monolithic(S)
+    u_same = fem.solve_monolithic(fem.with_dirichlet(S, S.uD[dd]))
+    assert np.linalg.norm(u_same - u_pw) <= 1e-12 * np.linalg.norm(u_pw)
+    r = np.random.default_rng(3)
+    d1 = r.standard_normal(len(dd)) + 1j * r.standard_normal(len(dd))
+    d2 = r.standard_normal(len(dd)) + 1j * r.standard_normal(len(dd))
+    u1 = fem.solve_monolithic(fem.with_dirichlet(S, d1))
+    u2 = fem.solve_monolithic(fem.with_dirichlet(S, d2))
+    u12 = fem.solve_monolithic(fem.with_dirichlet(S, 2.0 * d1 - 0.5j * d2))
+    assert np.linalg.norm(u12 - (2.0 * u1 - 0.5j * u2)) <= 1e-11 * np.linalg.norm(u12)
+    assert np.array_equal(u1[dd], d1)

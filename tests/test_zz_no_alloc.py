@@ -21,13 +21,30 @@ def _lib():
     build.build()
 
 
-@pytest.mark.parametrize("name", ["square32_p1", "p2"])
+def _problem(name):
+    if name == "p2":
+        return W.square_problem(16, 2, 2, 13.0, mu_inv=W.mu_inv_lognormal(256, 0.3, "na"), relabel=True,
+                                rotate_cells=True)
+    if name == "cube":
+        # 3-D: the impedance face terms ride on the SELL pattern (not a diagonal)
+        return W.cube_problem(6, 2, 7.0, mu_inv=W.mu_inv_lognormal(216, 0.3, "na3"), relabel=True,
+                              rotate_cells=True)
+    return W.config(name)
+
+
+def _noalloc(lib, sysg, field):
+    out = torch.full((2,), -1.0, dtype=torch.float64, device="cuda")
+    rc = lib.thm_residual_noalloc(sysg.h, C.c_void_p(field.data_ptr()), C.c_void_p(out.data_ptr()))
+    assert rc == 0, lib.thm_last_error()
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+@pytest.mark.parametrize("name", ["square32_p1", "p2", "cube"])
 def test_noalloc_residual_matches_solver_residual(name):
     import paper_2105_11993_gb300 as thm
     lib = thm.load()
-    P = (W.config(name) if name != "p2" else
-         W.square_problem(16, 2, 2, 13.0, mu_inv=W.mu_inv_lognormal(256, 0.3, "na"), relabel=True,
-                          rotate_cells=True))
+    P = _problem(name)
     mesh = thm.Mesh.from_workload(P.mesh, P.order)
     sysg = thm.System(mesh, P.mu_inv, P.omega, P.kappa, P.pol, P.direction)
     u, st = sysg.solve(mode="fp64", rtol=1e-8)
@@ -39,13 +56,7 @@ def test_noalloc_residual_matches_solver_residual(name):
     idx = torch.tensor(S.free[: len(S.free) // 3], device="cuda")
     v[idx] *= 1.5
     for field, ref in ((u, st["rel_residual"]), (v, None)):
-        outs = []
-        for _ in range(2):                         # two calls in a row share the scratch
-            out = torch.full((2,), -1.0, dtype=torch.float64, device="cuda")
-            rc = lib.thm_residual_noalloc(sysg.h, C.c_void_p(field.data_ptr()), C.c_void_p(out.data_ptr()))
-            assert rc == 0, lib.thm_last_error()
-            torch.cuda.synchronize()
-            outs.append(out.cpu().numpy())
+        outs = [_noalloc(lib, sysg, field) for _ in range(2)]      # two calls in a row share the scratch
         assert np.array_equal(outs[0], outs[1])
         rel = outs[0][0] / outs[0][1]
         if ref is not None:
@@ -55,3 +66,38 @@ def test_noalloc_residual_matches_solver_residual(name):
         else:
             # away from the solution: against the oracle's residual
             assert abs(rel - fem.residual(S, field.cpu().numpy())) <= 1e-10 * rel
+
+
+def test_noalloc_residual_of_a_batch_is_the_global_ratio():
+    """A batch of independent problems: out[0] / out[1] is the residual ratio
+    over the whole batch vector (not the largest per-problem ratio that the
+    solver's refinement stops on), checked against the problems' oracles."""
+    import paper_2105_11993_gb300 as thm
+    from oracle import fem
+    lib = thm.load()
+    probs = []
+    for p, (n, s, om) in enumerate([(8, 2, 6.0), (12, 3, 9.0), (6, 1, 5.0)]):
+        mesh = W.structured_mesh_2d(n, n, s, s)
+        pol, d = W.plane_wave_y(2)
+        probs.append(W.Problem(f"na{p}", mesh, 1, W.mu_inv_lognormal(mesh.n_cell, 0.3, f"na-b/{p}"), om, 1.0,
+                               pol, d))
+    mesh, _ = thm.Mesh.batch([P.mesh for P in probs], 1)
+    sysg = thm.System(mesh, np.concatenate([P.mu_inv for P in probs]), np.array([P.omega for P in probs]), 1.0,
+                      probs[0].pol, probs[0].direction)
+    u, _ = sysg.solve(mode="fp64", rtol=1e-8)
+    v = u.clone()
+    v[::7] *= 1.25                                 # away from the solution (free entries matter only)
+    outs = [_noalloc(lib, sysg, v) for _ in range(2)]
+    assert np.array_equal(outs[0], outs[1])
+    vh = v.cpu().numpy()
+    r2 = f2 = 0.0
+    d0 = 0
+    for P in probs:
+        S = fem.assemble(P)
+        up = vh[d0:d0 + S.dofs.n_dof].copy()
+        up[S.is_dir] = S.uD[S.is_dir]              # the Dirichlet entries are not read
+        d0 += S.dofs.n_dof
+        r2 += np.linalg.norm((S.K @ up)[S.free]) ** 2
+        f2 += np.linalg.norm(S.f) ** 2
+    assert abs(outs[0][0] - np.sqrt(r2)) <= 1e-10 * np.sqrt(r2)
+    assert abs(outs[0][1] - np.sqrt(f2)) <= 1e-12 * np.sqrt(f2)

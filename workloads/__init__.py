@@ -344,6 +344,10 @@ def config(name: str) -> Problem:
     square32_p1:   32x32 quads, order 1, 2x2 subdomains, omega=4pi, mu^{-1}=1.
     square256_p2:  256x256 quads, order 2, 8x8 subdomains, omega=40pi,
                    mu^{-1} piecewise constant on 16x16-cell tiles, U[0.5,2].
+    square64_p2:   64x64 quads, order 2, 2x2 subdomains of 32x32 cells (the
+                   subdomain of square256_p2: 8,320 free DOFs), omega=10pi
+                   (the same omega*h as square256_p2), mu^{-1} on 16x16-cell
+                   tiles, U[0.5,2].
     cube64_p1:     64^3 hexes, order 1, 4^3 subdomains, omega=16pi, mu^{-1}=1.
     cube48_adj:    48^3 hexes, order 1, 3^3 subdomains, omega=12pi,
                    mu^{-1}=exp(0.3 g), g smoothed white noise (sigma 3 cells).
@@ -353,6 +357,9 @@ def config(name: str) -> Problem:
     if name == "square256_p2":
         mu = mu_inv_blocks_2d(256, 256, 16, 0.5, 2.0, "square256_p2/mu")
         return square_problem(256, 8, 2, 40 * math.pi, mu_inv=mu, name=name)
+    if name == "square64_p2":
+        mu = mu_inv_blocks_2d(64, 64, 16, 0.5, 2.0, "square64_p2/mu")
+        return square_problem(64, 2, 2, 10 * math.pi, mu_inv=mu, name=name)
     if name == "cube64_p1":
         return cube_problem(64, 4, 16 * math.pi, name=name)
     if name == "cube48_adj":
