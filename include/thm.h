@@ -152,6 +152,48 @@ int thm_assemble_dirichlet(thm_sys** out, const thm_mesh* m, const double* mu_in
                            double omega, double kappa, const double* u_dir, int u_dir_on_device, void* stream);
 
 /*
+ * thm_assemble_ex -- thm_assemble / thm_assemble_batch / thm_assemble_dirichlet
+ * with the options below (opts may be NULL: all defaults).
+ *
+ *  omega   host double [n_prob] (one value unless the mesh is a batch).
+ *  pol, dir  the plane wave, as in thm_assemble; ignored when opts->u_dir is set.
+ *
+ *  eps     relative permittivity per cell (double [n_cell], > 0, host or
+ *          device per eps_on_device): the mass term becomes omega^2 M_eps,
+ *          M_eps = sum_c eps_c M_c, i.e. curl(mu^{-1} curl E) - omega^2 eps E = 0.
+ *          Eq. 1 is printed with eps = 1 (NULL); the paper's Example 1 (Section 4)
+ *          describes its block by a refractive index n, eps = n^2.  The Gamma^inf
+ *          and Sigma coefficients stay kappa omega; the adjoint differentiates
+ *          the weighted mass term.
+ *  trans_re, trans_im
+ *          transmission coefficient on Sigma_ij in units of kappa omega; both 0
+ *          means (0, 1): i kappa omega, the impedance condition of Eq. 5 with
+ *          S = 1 (Section 3.1).  Subdomain i then solves
+ *          (K_i + c kappa omega M_Sigma) u_i = s_i + G and the exchange is
+ *          G_{i<-j} = -G_{j<-i} + 2 c kappa omega M_Sigma u_j, c = trans_re + i trans_im;
+ *          the fixed point is the monolithic solution for every c != 0.  A large
+ *          real c is the penalty form of the Dirichlet-like classical Schwarz
+ *          interface condition that Section 3.1 says cannot be expected to
+ *          converge for large omega.  The block preconditioner of Eq. 7
+ *          factorises P_i = Re(T_i), which then includes trans_re kappa omega M_Sigma.
+ *  u_dir, u_dir_on_device
+ *          caller-given Dirichlet values as in thm_assemble_dirichlet (single
+ *          problems only), or NULL for the plane wave (pol, dir).
+ *  Errors: as thm_assemble.
+ */
+typedef struct thm_assemble_opts {
+    const double* eps;
+    int eps_on_device;
+    double trans_re, trans_im;
+    const double* u_dir;
+    int u_dir_on_device;
+} thm_assemble_opts;
+
+int thm_assemble_ex(thm_sys** out, const thm_mesh* m, const double* mu_inv, int mu_inv_on_device,
+                    const double* omega, double kappa, const double* pol, const double* dir,
+                    const thm_assemble_opts* opts, void* stream);
+
+/*
  * Batches of independent problems (the paper solves one problem at a time;
  * this is the batched form of the same solve).  A batch mesh is the disjoint
  * union of the problems' meshes, built with thm_mesh_create: subdomain ids are

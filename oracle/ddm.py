@@ -17,6 +17,9 @@ G_{i<-j} standing for -int g_{i<-j} . phi on Sigma_ij:
   subdomain i:  (K_i + i k sum_j M_ij) u_i = s_i + sum_j G_{i<-j}
   update:       G_{i<-j}  <-  -G_{j<-i} + 2 i k M_ij u_j
 
+(i k is the impedance coefficient; `setup(..., transmission=c)` puts c k in
+its place to study other interface conditions.)
+
 where K_i is the part of the global matrix assembled from the cells of
 Omega_i (volume terms and the Gamma^inf impedance terms of its boundary).  At a
 fixed point, adding and subtracting the two updates of a pair gives
@@ -69,8 +72,9 @@ class DDM:
     sys: fem.System
     subs: list
     pairs: list               # directed (i <- j), sorted by (i, j)
-    kw: complex               # i * kappa * omega
+    kw: complex               # i * kappa * omega (the Gamma^inf impedance coefficient)
     offsets: np.ndarray       # start of each pair's block in the interface vector
+    kt: complex = None        # transmission coefficient on Sigma_ij (default kw)
     stats: dict = field(default_factory=dict)
 
     @property
@@ -78,12 +82,19 @@ class DDM:
         return int(self.offsets[-1])
 
 
-def setup(problem, sys_: fem.System | None = None) -> DDM:
+def setup(problem, sys_: fem.System | None = None, transmission: complex = 1j) -> DDM:
+    """transmission: the interface coefficient in units of kappa*omega.  1j is
+    the impedance condition of Eq. 5 (S = 1); a real value replaces it by a
+    Robin condition with a real coefficient, and a large real value is the
+    penalty form of the Dirichlet-like classical interface condition of
+    Section 3.1.  The fixed point is the monolithic solution for any nonzero
+    coefficient (the argument above does not use its value)."""
     mesh = problem.mesh
     if sys_ is None:
         sys_ = fem.assemble(problem)
     dofs = sys_.dofs
     kw = 1j * problem.kappa * problem.omega
+    kt = complex(transmission) * problem.kappa * problem.omega
     fverts, fcells = fem.cell_faces(mesh)
     sub_of = mesh.cell_sub
     # interface faces: two cells in different subdomains
@@ -109,18 +120,19 @@ def setup(problem, sys_: fem.System | None = None) -> DDM:
     for i in range(nsub):
         cells = np.flatnonzero(sub_of == i)
         gd = np.unique(dofs.cell_dofs[cells])
-        A, M = fem.assemble_volume(mesh, dofs, problem.mu_inv, problem.omega, cells)
+        A, M = fem.assemble_volume(mesh, dofs, problem.mu_inv, problem.omega, cells, eps=problem.eps)
         Mg = fem.assemble_faces(mesh, dofs, imp_by_sub[i])
         Kg = (A - problem.omega ** 2 * M).astype(np.complex128) + kw * Mg
         Tg = Kg.copy()
         for (a, b), Mp in pair_M.items():
             if i in (a, b):
-                Tg = Tg + kw * Mp
+                Tg = Tg + kt * Mp
         T = Tg.tocsr()[gd][:, gd].tocsr()
         Kl = Kg.tocsr()[gd][:, gd].tocsr()
         isd = sys_.is_dir[gd]
         s = Sub(i, cells, gd, np.flatnonzero(~isd), np.flatnonzero(isd), T, Kl)
         s.Tff = T[s.free][:, s.free].tocsc()
+        # P = Re(T_ff): A_i - omega^2 M_i (plus the real part of the transmission term, if any)
         Pm = s.Tff.copy()
         s.P = sp.csc_matrix((np.ascontiguousarray(Pm.data.real), Pm.indices.copy(), Pm.indptr.copy()), shape=Pm.shape)
         subs.append(s)
@@ -134,7 +146,7 @@ def setup(problem, sys_: fem.System | None = None) -> DDM:
         pairs.append(Pair(b, a, d_all, d_free, Ml))
     pairs.sort(key=lambda p: (p.i, p.j))
     offsets = np.concatenate([[0], np.cumsum([len(p.free) for p in pairs])])
-    return DDM(sys_, subs, pairs, kw, offsets)
+    return DDM(sys_, subs, pairs, kw, offsets, kt=kt)
 
 
 def local_sources(ddm: DDM) -> list:
@@ -203,7 +215,7 @@ def sweep(ddm: DDM, g: np.ndarray, sources, with_dirichlet: bool, solve):
         uj = us[p.j][np.searchsorted(sj.dofs, p.dofs)]
         Mu = p.M @ uj
         sel = np.searchsorted(p.dofs, p.free)
-        g_new[lo:hi] = -g[plo:phi] + 2.0 * ddm.kw * Mu[sel]
+        g_new[lo:hi] = -g[plo:phi] + 2.0 * ddm.kt * Mu[sel]
     return g_new, us
 
 

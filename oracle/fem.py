@@ -19,6 +19,9 @@ Definitions used here (stated once, pinned by tests/test_oracle_fem.py):
   as in the Zaglmayr reference cited in Section 2.)
 * Reference functions map by the covariant Piola map phi = J^{-T} phi_hat,
   curl by the contravariant one (1/det J) J curl_hat (a scalar 1/det J in 2-D).
+* An optional relative permittivity eps per cell weights the mass term,
+  sum_c eps_c M_c (Eq. 1 is printed with eps = 1; the paper's Example 1
+  describes its centre block by a refractive index n, eps = n^2).
 * K = mu^{-1} A - omega^2 M + i kappa omega M_Gamma_inf, i.e. Eq. 3's
   K = A - w^2 M + iB with B = kappa*omega*M_Gamma_inf: the coefficient of the
   boundary integral is taken from the strong form's impedance condition
@@ -337,8 +340,9 @@ def cell_matrices(mesh, order):
     return A, M
 
 
-def assemble_volume(mesh, dofs: Dofs, mu_inv, omega, cells=None):
-    """Signed global (mu^{-1} A, M) from the given cells (default all)."""
+def assemble_volume(mesh, dofs: Dofs, mu_inv, omega, cells=None, eps=None):
+    """Signed global (mu^{-1} A, M) from the given cells (default all); with
+    eps (relative permittivity per cell) the mass is sum_c eps_c M_c."""
     A, M = cell_matrices(mesh, dofs.order)
     if cells is None:
         cells = np.arange(mesh.n_cell)
@@ -347,6 +351,8 @@ def assemble_volume(mesh, dofs: Dofs, mu_inv, omega, cells=None):
     ss = cs[:, :, None] * cs[:, None, :]
     Av = (mu_inv[cells][:, None, None] * A[cells]) * ss
     Mv = M[cells] * ss
+    if eps is not None:
+        Mv = eps[cells][:, None, None] * Mv
     rows = np.repeat(cd, cd.shape[1], axis=1).ravel()
     cols = np.tile(cd, (1, cd.shape[1])).ravel()
     n = dofs.n_dof
@@ -373,7 +379,7 @@ class System:
     dofs: Dofs
     K: sp.csr_matrix          # complex, all DOFs
     A: sp.csr_matrix          # mu^{-1}-weighted curl-curl
-    M: sp.csr_matrix          # mass
+    M: sp.csr_matrix          # mass (eps-weighted when the problem has a permittivity field)
     Mg: sp.csr_matrix         # impedance boundary mass (Gamma^inf)
     is_dir: np.ndarray
     uD: np.ndarray
@@ -384,7 +390,7 @@ class System:
 def assemble(problem) -> System:
     mesh = problem.mesh
     dofs = number_dofs(mesh.cells, mesh.dim, problem.order)
-    A, M = assemble_volume(mesh, dofs, problem.mu_inv, problem.omega)
+    A, M = assemble_volume(mesh, dofs, problem.mu_inv, problem.omega, eps=problem.eps)
     imp = [f for f, t in zip(mesh.bfaces, mesh.btag) if t == 0]
     Mg = assemble_faces(mesh, dofs, imp)
     K = (A - problem.omega ** 2 * M).astype(np.complex128) + 1j * problem.kappa * problem.omega * Mg

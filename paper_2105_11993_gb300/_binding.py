@@ -24,7 +24,7 @@ symbols = [
     "thm_local_dofs", "thm_iface_dofs", "thm_apply_local", "thm_sweep", "thm_local_sources",
     "thm_dirichlet_values", "thm_kernel_launches", "thm_profile_enable", "thm_profile_read",
     "thm_alg_bytes", "thm_residual_noalloc", "thm_mesh_set_problems", "thm_assemble_batch", "thm_work_bytes",
-    "thm_mesh_dirichlet_dofs", "thm_assemble_dirichlet",
+    "thm_mesh_dirichlet_dofs", "thm_assemble_dirichlet", "thm_assemble_ex",
 ]
 
 
@@ -39,6 +39,11 @@ class SolveOptions(C.Structure):
                 ("inner_tol", C.c_double), ("inner_maxit", C.c_int), ("outer_restart", C.c_int),
                 ("outer_tol", C.c_double), ("outer_maxit", C.c_int), ("max_refine", C.c_int),
                 ("relax", C.c_int), ("outer_method", C.c_int)]
+
+
+class AssembleOptions(C.Structure):
+    _fields_ = [("eps", C.c_void_p), ("eps_on_device", C.c_int), ("trans_re", C.c_double),
+                ("trans_im", C.c_double), ("u_dir", C.c_void_p), ("u_dir_on_device", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -77,6 +82,7 @@ def load():
         "thm_adjoint": [P, P, P, P, P, P, P, P],
         "thm_mesh_dirichlet_dofs": [P, P, P],
         "thm_assemble_dirichlet": [C.POINTER(P), P, P, C.c_int, C.c_double, C.c_double, P, C.c_int, P],
+        "thm_assemble_ex": [C.POINTER(P), P, P, C.c_int, P, C.c_double, P, P, P, P],
         "thm_sys_destroy": [P],
         "thm_last_error": [],
         "thm_sys_info": [P, P, P, P, P],
@@ -246,10 +252,14 @@ def _opts(mode="fp64", rtol=1e-8, inner_restart=0, inner_tol=0.0, inner_maxit=0,
 class System:
     """thm_assemble: subdomain operators, Dirichlet data, preconditioner."""
 
-    def __init__(self, mesh: Mesh, mu_inv, omega, kappa, pol=None, direction=None, stream=None, dirichlet=None):
+    def __init__(self, mesh: Mesh, mu_inv, omega, kappa, pol=None, direction=None, stream=None, dirichlet=None,
+                 eps=None, transmission=None):
         """pol/direction: plane-wave Dirichlet data (thm_assemble); or
         dirichlet: complex values of the Dirichlet DOFs in the order of
-        mesh.dirichlet_dofs(), numpy or a CUDA tensor (thm_assemble_dirichlet)."""
+        mesh.dirichlet_dofs(), numpy or a CUDA tensor (thm_assemble_dirichlet).
+        eps: relative permittivity per cell; transmission: complex coefficient
+        on the interfaces in units of kappa*omega (default 1j, the impedance
+        condition); either one goes through thm_assemble_ex."""
         lib = load()
         torch = _torch()
         self.mesh = mesh
@@ -276,7 +286,30 @@ class System:
                 dptr, don = _ptr(dv), 0
             self._dir = dv
 
+        use_ex = eps is not None or transmission is not None
+        if use_ex:
+            ao = AssembleOptions()
+            if eps is not None:
+                if isinstance(eps, torch.Tensor):
+                    ev = eps.to(torch.float64).contiguous()
+                    ao.eps, ao.eps_on_device = ev.data_ptr(), 1
+                else:
+                    ev = np.ascontiguousarray(eps, np.float64)
+                    ao.eps, ao.eps_on_device = ev.ctypes.data, 0
+                self._eps = ev
+            if transmission is not None:
+                t = complex(transmission)
+                ao.trans_re, ao.trans_im = t.real, t.imag
+            if dirichlet is not None:
+                ao.u_dir, ao.u_dir_on_device = dptr.value, don
+            self._om_ex = np.ascontiguousarray(np.atleast_1d(omega), np.float64)
+            self._ao = ao
+
         def assemble(mu_ptr, on_device):
+            if use_ex:
+                return lib.thm_assemble_ex(C.byref(h), mesh.h, mu_ptr, on_device, _ptr(self._om_ex), float(kappa),
+                                           _ptr(self._pol), _ptr(self._dir), C.byref(self._ao),
+                                           C.c_void_p(st.cuda_stream))
             if dirichlet is not None:
                 assert not batch, "caller-given Dirichlet data: single problems only"
                 return lib.thm_assemble_dirichlet(C.byref(h), mesh.h, mu_ptr, on_device, float(omega), float(kappa),

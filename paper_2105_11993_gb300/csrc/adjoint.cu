@@ -69,11 +69,13 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
     return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-// Per cell: dL/dmu_c and the cell's share of dL/domega (volume terms).
+// Per cell: dL/dmu_c and the cell's share of dL/domega (volume terms;
+// K_c = mu_c A_c - omega^2 eps_c M_c).
 __global__ void k_adj_cells(int dim, int64_t n_cell, int nb, const double* __restrict__ ref,
                             const double* __restrict__ X, const int32_t* __restrict__ cells,
                             const int32_t* __restrict__ cdofs, const int8_t* __restrict__ signs,
-                            const double* __restrict__ mu, double omega, const double2* __restrict__ lam,
+                            const double* __restrict__ mu, const double* __restrict__ w2c, double omega,
+                            const double2* __restrict__ lam,
                             const double2* __restrict__ u, const double2* __restrict__ duD,
                             double* __restrict__ gmu, double* __restrict__ gw) {
     int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -89,7 +91,7 @@ __global__ void k_adj_cells(int dim, int64_t n_cell, int nb, const double* __res
         dc[i] = make_double2(s * duD[d].x, s * duD[d].y);
     }
     double2 sA = make_double2(0, 0), sM = make_double2(0, 0), sD = make_double2(0, 0);
-    const double w2 = omega * omega;
+    const double w2 = w2c[c];                   // omega^2 eps_c: the cell's mass-term weight
     for (int i = 0; i < nb; ++i) {
         double2 tA = make_double2(0, 0), tM = make_double2(0, 0), tD = make_double2(0, 0);
         for (int j = 0; j < nb; ++j) {
@@ -106,7 +108,7 @@ __global__ void k_adj_cells(int dim, int64_t n_cell, int nb, const double* __res
         sD.x += r.x; sD.y += r.y;
     }
     gmu[c] = -2.0 * sA.x;
-    gw[c] = -2.0 * (-2.0 * omega * sM.x) - 2.0 * sD.x;
+    gw[c] = -2.0 * (-2.0 * (w2 / omega) * sM.x) - 2.0 * sD.x;      // dK_c/domega = -2 omega eps_c M_c
 }
 
 // Gamma^inf face share of dL/domega and of dL/dkappa: with m_f the signed face
@@ -202,7 +204,7 @@ int adjoint(thm_sys* s, const thm_solve_opts* opts, const double2* u, const doub
             s->dir[1], s->dir[2], duD.p));
     THM_LAUNCH(THM_K_DDM, st, k_adj_cells<<<nb(m->n_cell), 256, 0, st>>>(m->dim, m->n_cell, m->dpc, s->ref.p, m->d_coords.p,
                                                                         m->d_cells.p, m->d_cell_dofs.p, m->d_cell_signs.p,
-                                                                        s->mu_inv.p, s->omega, lam.p, u, duD.p, grad_mu,
+                                                                        s->mu_inv.p, s->w2c.p, s->omega, lam.p, u, duD.p, grad_mu,
                                                                         gw_cell.p));
     if (m->n_face > 0)
         THM_LAUNCH(THM_K_DDM, st, k_adj_faces<<<nb(m->n_face), 256, 0, st>>>(

@@ -193,9 +193,12 @@ __global__ void k_face_terms(int dim, int64_t n_loc, int fd, const double* __res
                              const int32_t* __restrict__ face_loc, const int32_t* __restrict__ row_face,
                              const int8_t* __restrict__ row_face_a, const int8_t* __restrict__ row_face_side,
                              const int64_t* __restrict__ slice_ptr, const int32_t* __restrict__ col,
-                             const uint8_t* __restrict__ pad, const double* __restrict__ kwf, double* bg64,
+                             const uint8_t* __restrict__ pad, const double* __restrict__ kwf, double tre,
+                             double tim, double* val64, float* val32, double* bg64,
                              double* bs64, float* bg32,
                              float* bs32, double* bvg64, double* bvs64, float* bvg32, float* bvs32) {
+    // Sigma terms: (tre + i tim) kappa omega M_Sigma; the imaginary part goes to
+    // the face-term arrays, a real part (tre != 0) into the values of P_i
     int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (r >= n_loc) return;
     constexpr int RF = thm_mesh::RF;
@@ -208,7 +211,20 @@ __global__ void k_face_terms(int dim, int64_t n_loc, int fd, const double* __res
             const double v = kwf[f] * face_mass(2, ref, X, face_v + (int64_t)f * 4, a, a);
             if (face_kind[f] == 1) g += v; else s += v;
         }
-        bg64[r] = g; bs64[r] = s; bg32[r] = (float)g; bs32[r] = (float)s;
+        bg64[r] = g; bs64[r] = tim * s; bg32[r] = (float)g; bs32[r] = (float)(tim * s);
+        if (tre != 0.0 && s != 0.0) {
+            const int64_t sl = r / SELL_C;
+            const int lane = (int)(r % SELL_C);
+            const int64_t base = slice_ptr[sl];
+            const int w = (int)((slice_ptr[sl + 1] - base) / SELL_C);
+            for (int t = 0; t < w; ++t) {
+                const int64_t idx = base + (int64_t)t * SELL_C + lane;
+                if (!pad[idx] && col[idx] == r) {
+                    val64[idx] += tre * s;
+                    val32[idx] = (float)val64[idx];
+                }
+            }
+        }
         return;
     }
     bg64[r] = 0; bs64[r] = 0; bg32[r] = 0; bs32[r] = 0;
@@ -233,7 +249,11 @@ __global__ void k_face_terms(int dim, int64_t n_loc, int fd, const double* __res
                 }
             }
         }
-        bvg64[idx] = g; bvs64[idx] = s; bvg32[idx] = (float)g; bvs32[idx] = (float)s;
+        bvg64[idx] = g; bvs64[idx] = tim * s; bvg32[idx] = (float)g; bvs32[idx] = (float)(tim * s);
+        if (tre != 0.0 && s != 0.0) {
+            val64[idx] += tre * s;
+            val32[idx] = (float)val64[idx];
+        }
     }
 }
 
@@ -318,8 +338,8 @@ __global__ void k_lifting(int dim, int64_t n_loc, int nb, int maxc, const double
                           const int32_t* __restrict__ face_dof, const int8_t* __restrict__ face_sgn,
                           const int32_t* __restrict__ face_loc, const int32_t* __restrict__ row_face,
                           const int8_t* __restrict__ row_face_a, const int8_t* __restrict__ row_face_side,
-                          const int8_t* __restrict__ face_kind, const double* __restrict__ kwf,
-                          double2* __restrict__ f,
+                          const int8_t* __restrict__ face_kind, const double* __restrict__ kwf, double tre,
+                          double tim, double2* __restrict__ f,
                           double2* __restrict__ fres) {
     int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (r >= n_loc) return;
@@ -341,8 +361,9 @@ __global__ void k_lifting(int dim, int64_t n_loc, int nb, int maxc, const double
     }
     // face terms coupling the row to Dirichlet DOFs: -(i kappa omega M_f) u_D.
     // The global system holds only the Gamma^inf faces; the subdomain operator
-    // T_i also the transmission faces of Sigma (3-D only: in 2-D no Dirichlet
-    // DOF lies on an interface edge).
+    // T_i also the transmission faces of Sigma, with the coefficient
+    // (tre + i tim) kappa omega (3-D only: in 2-D no Dirichlet DOF lies on an
+    // interface edge).
     double gr = fr, gi = fi;
     constexpr int RF = thm_mesh::RF;
     for (int u = 0; u < RF; ++u) {
@@ -355,9 +376,15 @@ __global__ void k_lifting(int dim, int64_t n_loc, int nb, int maxc, const double
             const double v = kwf[f] * face_sgn[(int64_t)f * fd + a] * face_sgn[(int64_t)f * fd + b] *
                              face_mass(dim, ref, X, face_v + (int64_t)f * 4, a, b);
             const double2 d = uD[gd];
-            fr += v * d.y;            // -(i v)(d.x + i d.y) = v d.y - i v d.x
-            fi -= v * d.x;
-            if (face_kind[f] == 1) { gr += v * d.y; gi -= v * d.x; }
+            if (face_kind[f] == 1) {
+                fr += v * d.y;            // -(i v)(d.x + i d.y) = v d.y - i v d.x
+                fi -= v * d.x;
+                gr += v * d.y;
+                gi -= v * d.x;
+            } else {                      // -((tre + i tim) v) d
+                fr -= v * (tre * d.x - tim * d.y);
+                fi -= v * (tre * d.y + tim * d.x);
+            }
         }
     }
     f[r] = make_double2(fr, fi);
@@ -732,9 +759,11 @@ void assemble(thm_sys* s) {
         THM_REQUIRE((int)s->omega_prob.size() == m->n_prob, "one omega per problem required");
         std::vector<double> w2h(m->n_cell), kwh(std::max<int64_t>(1, m->n_face), 0.0);
         std::vector<double> omh(std::max<size_t>(1, m->dir_edges.size()), 0.0);
+        std::vector<double> eps;
+        if (s->eps.p) s->eps.download(eps, st);
         for (int64_t c = 0; c < m->n_cell; ++c) {
             const double om = s->omega_prob[prob(m->cell_sub[c])];
-            w2h[c] = om * om;
+            w2h[c] = om * om * (eps.empty() ? 1.0 : eps[c]);      // the mass term omega^2 eps_c M_c
         }
         for (int64_t f = 0; f < m->n_face; ++f) {
             const int32_t sb = m->face_sub[2 * f] >= 0 ? m->face_sub[2 * f] : m->face_sub[2 * f + 1];
@@ -767,6 +796,13 @@ void assemble(thm_sys* s) {
                                               m->d_slice_ptr.p, m->d_sell_col.p, m->d_sell_pad.p,
                                               m->d_row_cell.p, m->d_row_k.p, s->val64.p, s->val32.p));
     THM_CUDA(cudaGetLastError());
+    if (s->trans_re != 0.0) {
+        // K_i^loc (no Sigma terms) keeps the values before the real Sigma part is added
+        s->valK64.alloc(m->n_slots);
+        s->valK32.alloc(m->n_slots);
+        THM_CUDA(cudaMemcpyAsync(s->valK64.p, s->val64.p, m->n_slots * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        THM_CUDA(cudaMemcpyAsync(s->valK32.p, s->val32.p, m->n_slots * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    }
     s->bg64.alloc(m->n_loc); s->bs64.alloc(m->n_loc);
     s->bg32.alloc(m->n_loc); s->bs32.alloc(m->n_loc);
     const bool sellb = m->dim == 3;
@@ -775,8 +811,8 @@ void assemble(thm_sys* s) {
     THM_LAUNCH(THM_K_SETUP, st, k_face_terms<<<grid(m->n_loc), th, 0, st>>>(
         m->dim, m->n_loc, m->fd, s->ref.p, m->d_coords.p, m->d_face_v.p, m->d_face_sgn.p, m->d_face_kind.p,
         m->d_face_loc.p, m->d_row_face.p, m->d_row_face_a.p, m->d_row_face_side.p, m->d_slice_ptr.p,
-        m->d_sell_col.p, m->d_sell_pad.p, s->kwf.p, s->bg64.p, s->bs64.p, s->bg32.p, s->bs32.p, s->bvg64.p, s->bvs64.p,
-        s->bvg32.p, s->bvs32.p));
+        m->d_sell_col.p, m->d_sell_pad.p, s->kwf.p, s->trans_re, s->trans_im, s->val64.p, s->val32.p, s->bg64.p,
+        s->bs64.p, s->bg32.p, s->bs32.p, s->bvg64.p, s->bvs64.p, s->bvg32.p, s->bvs32.p));
     THM_CUDA(cudaGetLastError());
     const int64_t nterm = (int64_t)m->if_tf.size();
     s->if_val.alloc(nterm > 0 ? nterm : 1);
@@ -851,7 +887,7 @@ void assemble(thm_sys* s) {
         m->dim, m->n_loc, nb, m->maxc, s->ref.p, m->d_coords.p, m->d_cells.p, m->d_cell_signs.p, m->d_cell_loc.p,
         m->d_cell_dofs.p, s->mu_inv.p, s->w2c.p, m->d_row_cell.p, m->d_row_k.p, s->uD.p, m->fd, m->d_face_v.p,
         m->d_face_dof.p, m->d_face_sgn.p, m->d_face_loc.p, m->d_row_face.p, m->d_row_face_a.p, m->d_row_face_side.p,
-        m->d_face_kind.p, s->kwf.p, s->f_loc.p, s->f_res.p));
+        m->d_face_kind.p, s->kwf.p, s->trans_re, s->trans_im, s->f_loc.p, s->f_res.p));
     THM_CUDA(cudaGetLastError());
     THM_CUDA(cudaStreamSynchronize(st));
 }

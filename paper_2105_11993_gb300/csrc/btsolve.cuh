@@ -45,9 +45,9 @@ namespace thm {
 constexpr int BT_NT = 384;                  // consumer threads
 constexpr int BT_NW = BT_NT / 32;           // consumer warps
 constexpr int BT_THREADS = BT_NT + 32;      // + one producer warp
-constexpr int BT_MAXG = 8;                  // row groups of a block GEMV
-constexpr int BT_QMAX = 2;                  // output quads per thread: m_l <= 4 * BT_QMAX * BT_NT
-constexpr int BT_MAX_M = 4 * BT_QMAX * BT_NT;
+constexpr int BT_GQ = 8;                    // output quads per quad group (one group per warp pass)
+constexpr int BT_GMAX = 4;                  // quad groups per warp: m_l <= 4 * BT_GQ * BT_GMAX * BT_NW
+constexpr int BT_MAX_M = 4 * BT_GQ * BT_GMAX * BT_NW;
 constexpr int BT_NC = 4;                    // slots of the coupling ring
 
 __host__ __device__ constexpr int bt_r4(int v) { return (v + 3) / 4 * 4; }
@@ -162,7 +162,7 @@ __device__ __forceinline__ void bt_load4<double, float>(const double* p, float* 
 
 // Shared-memory layout of k_bt_solve (host and device agree through this).
 struct BtLayout {
-    size_t bars, lv, slots, cslots, vec, su, tx, rx, ry, part, total;
+    size_t bars, lv, slots, cslots, vec, su, tx, rx, ry, total;
 };
 template <class V>
 __host__ __device__ inline BtLayout bt_layout(int ns, int slot_bytes, int cslot_bytes, int max_lev, int nvec,
@@ -179,8 +179,6 @@ __host__ __device__ inline BtLayout bt_layout(int ns, int slot_bytes, int cslot_
     L.tx = o; o += vm;
     L.rx = o; o += vm;
     L.ry = o; o += vm;
-    const int np = 4 * BT_NT > bt_r4(max_m) ? 4 * BT_NT : bt_r4(max_m);
-    L.part = o; o += bt_r16((size_t)np * sizeof(V));
     L.total = o;
     return L;
 }
@@ -216,7 +214,6 @@ k_bt_solve(const Sub* __restrict__ subs, const Level* __restrict__ levels, const
     V* tx = reinterpret_cast<V*>(smem + lay.tx);
     V* rx = reinterpret_cast<V*>(smem + lay.rx);
     V* ry = reinterpret_cast<V*>(smem + lay.ry);
-    V* part = reinterpret_cast<V*>(smem + lay.part);
     V* prx = cluster.map_shared_rank(rx, peer);
     V* pry = cluster.map_shared_rank(ry, peer);
     volatile int* abort = &s_abort;
@@ -423,14 +420,19 @@ k_bt_solve(const Sub* __restrict__ subs, const Level* __restrict__ levels, const
                 }
             }
             bt_bar_consumers();
-            // (b2) y = W_l^T s over the rows [ra, rb) this rank streams
+            // (b2) y = W_l^T s over the rows [ra, rb) this rank streams.  Warp w
+            // owns the quad groups g = w, w + NW, ... (8 output quads = 32
+            // outputs each); inside a warp, lane = (row subset rs, quad qq):
+            // the 8 lanes of a subset read 128 contiguous bytes of one W row
+            // (no bank conflicts whatever the row stride) and the 4 subsets
+            // take every 4th row.  The subsets are summed with shuffles, so
+            // each output is complete inside one warp: no cross-warp combine.
             const int nq = ldm / 4;
-            const int tq = min(nq, BT_NT);
-            const int ng = min(BT_MAXG, BT_NT / tq);
-            const int g = tid / tq, i0 = tid % tq;
-            Rt acc[BT_QMAX][4][2];
+            const int ngr = (nq + BT_GQ - 1) / BT_GQ;
+            const int rs = lane >> 3, qq = lane & 7;
+            Rt acc[BT_GMAX][4][2];
 #pragma unroll
-            for (int u = 0; u < BT_QMAX; ++u)
+            for (int u = 0; u < BT_GMAX; ++u)
 #pragma unroll
                 for (int c = 0; c < 4; ++c) acc[u][c][0] = acc[u][c][1] = 0;
             for (int r0 = st.ra; r0 < st.rb; r0 += R) {
@@ -438,45 +440,37 @@ k_bt_solve(const Sub* __restrict__ subs, const Level* __restrict__ levels, const
                 bt_wait<false>(&full[q], (unsigned)((t / ns) & 1), abort, err);
                 const F* Wt = reinterpret_cast<const F*>(slots + (size_t)q * slot_bytes);
                 const int nr = min(R, st.rb - r0);
-                if (g < ng) {
-                    int jj = g;
-                    // four rows per pass: their loads are independent
-                    for (; jj + 3 * ng < nr; jj += 4 * ng) {
-                        V sj[4];
 #pragma unroll
-                        for (int r = 0; r < 4; ++r) sj[r] = su[r0 + jj + r * ng];
+                for (int u = 0; u < BT_GMAX; ++u) {
+                    const int quad = (warp + u * BT_NW) * BT_GQ + qq;
+                    if (warp + u * BT_NW < ngr && quad < nq) {
+                        const F* wc = Wt + 4 * quad;
+                        int jj = rs;
+                        // four rows per pass: their loads are independent
+                        for (; jj + 12 < nr; jj += 16) {
+                            V sj[4];
+                            Rt w[4][4];
 #pragma unroll
-                        for (int u = 0; u < BT_QMAX; ++u) {
-                            const int qq = i0 + u * tq;
-                            if (qq < nq) {
-                                Rt w[4][4];
-#pragma unroll
-                                for (int r = 0; r < 4; ++r)
-                                    bt_load4<F, Rt>(Wt + (size_t)(jj + r * ng) * ldm + 4 * qq, w[r]);
-#pragma unroll
-                                for (int r = 0; r < 4; ++r)
-#pragma unroll
-                                    for (int c = 0; c < 4; ++c) {
-                                        acc[u][c][0] += w[r][c] * sj[r].x;
-                                        acc[u][c][1] += w[r][c] * sj[r].y;
-                                    }
+                            for (int r = 0; r < 4; ++r) {
+                                sj[r] = su[r0 + jj + 4 * r];
+                                bt_load4<F, Rt>(wc + (size_t)(jj + 4 * r) * ldm, w[r]);
                             }
-                        }
-                    }
-                    for (; jj < nr; jj += ng) {
-                        const V sj = su[r0 + jj];
-                        const F* wr = Wt + (size_t)jj * ldm;
 #pragma unroll
-                        for (int u = 0; u < BT_QMAX; ++u) {
-                            const int qq = i0 + u * tq;
-                            if (qq < nq) {
-                                Rt w[4];
-                                bt_load4<F, Rt>(wr + 4 * qq, w);
+                            for (int r = 0; r < 4; ++r)
 #pragma unroll
                                 for (int c = 0; c < 4; ++c) {
-                                    acc[u][c][0] += w[c] * sj.x;
-                                    acc[u][c][1] += w[c] * sj.y;
+                                    acc[u][c][0] += w[r][c] * sj[r].x;
+                                    acc[u][c][1] += w[r][c] * sj[r].y;
                                 }
+                        }
+                        for (; jj < nr; jj += 4) {
+                            const V sj = su[r0 + jj];
+                            Rt w[4];
+                            bt_load4<F, Rt>(wc + (size_t)jj * ldm, w);
+#pragma unroll
+                            for (int c = 0; c < 4; ++c) {
+                                acc[u][c][0] += w[c] * sj.x;
+                                acc[u][c][1] += w[c] * sj.y;
                             }
                         }
                     }
@@ -485,39 +479,43 @@ k_bt_solve(const Sub* __restrict__ subs, const Level* __restrict__ levels, const
                 if (lane == 0) mbar_arrive_local(&empty[q]);
                 ++t;
             }
-            // (b3) combine the row groups
-            if (g < ng) {
+            // (b3) sum the 4 row subsets and write each output from the lane of subset 0
 #pragma unroll
-                for (int u = 0; u < BT_QMAX; ++u) {
-                    const int qq = i0 + u * tq;
-                    if (qq < nq)
+            for (int u = 0; u < BT_GMAX; ++u) {
+                if (warp + u * BT_NW >= ngr) break;              // uniform across the warp
 #pragma unroll
-                        for (int c = 0; c < 4; ++c) part[g * ldm + 4 * qq + c] = mk<V>(acc[u][c][0], acc[u][c][1]);
-                }
-            }
-            bt_bar_consumers();
-            for (int i = tid; i < m; i += BT_NT) {
-                Rt yr = 0, yi = 0;
-                for (int gg = 0; gg < ng; ++gg) {
-                    const V pv = part[gg * ldm + i];
-                    yr += pv.x;
-                    yi += pv.y;
-                }
-                if (st.kind == 0) {
-                    vec[o + i] = mk<V>(yr, yi);
-                } else if (st.kind == 1) {
-                    tx[i] = mk<V>(yr, yi);
-                    pry[i] = mk<V>(yr, yi);
-                } else {
-                    const V z = vec[o + i];
-                    vec[o + i] = mk<V>(z.x - yr, z.y - yi);
+                for (int c = 0; c < 4; ++c)
+#pragma unroll
+                    for (int z = 0; z < 2; ++z) {
+                        acc[u][c][z] += __shfl_xor_sync(0xffffffffu, acc[u][c][z], 8);
+                        acc[u][c][z] += __shfl_xor_sync(0xffffffffu, acc[u][c][z], 16);
+                    }
+                const int quad = (warp + u * BT_NW) * BT_GQ + qq;
+                if (rs == 0 && quad < nq) {
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const int i = 4 * quad + c;
+                        if (i >= m) break;
+                        const V yv = mk<V>(acc[u][c][0], acc[u][c][1]);
+                        if (st.kind == 0) {
+                            vec[o + i] = yv;
+                        } else if (st.kind == 1) {
+                            tx[i] = yv;
+                            pry[i] = yv;
+                        } else {
+                            const V z = vec[o + i];
+                            vec[o + i] = mk<V>(z.x - yv.x, z.y - yv.y);
+                        }
+                    }
                 }
             }
             if (st.kind == 1) {
-                // x_k = own half + the peer's half
+                // x_k = own half + the peer's half (both complete once every
+                // warp of both CTAs has written its outputs)
                 __syncwarp();
                 if (lane == 0) mbar_arrive_remote(mapa_u32(&xbar[1], (unsigned)peer));
                 bt_wait<true>(&xbar[1], 0u, abort, err);
+                bt_bar_consumers();
                 for (int i = tid; i < m; i += BT_NT) {
                     const V a = tx[i], b = ry[i];
                     vec[o + i] = mk<V>(a.x + b.x, a.y + b.y);

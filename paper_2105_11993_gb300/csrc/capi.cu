@@ -115,10 +115,13 @@ void thm_mesh_destroy(thm_mesh* m) { delete m; }
 
 static int assemble_common(thm_sys** out, const thm_mesh* m, const double* mu_inv, int mu_inv_on_device,
                            const std::vector<double>& omegas, double kappa, const double* pol, const double* dir,
-                           void* stream, const double* u_dir = nullptr, int u_dir_on_device = 0) {
+                           void* stream, const thm_assemble_opts* ao = nullptr) {
     return guarded([&]() -> int {
         THM_REQUIRE(out && m && mu_inv, "NULL argument");
+        const double* u_dir = ao ? ao->u_dir : nullptr;
+        const int u_dir_on_device = ao ? ao->u_dir_on_device : 0;
         const bool given = u_dir != nullptr;
+        THM_REQUIRE(!given || m->n_prob == 1, "caller-given Dirichlet values: single problems only");
         THM_REQUIRE(given || (pol && dir), "NULL argument (plane-wave polarisation / direction)");
         *out = nullptr;
         THM_REQUIRE((int)omegas.size() == m->n_prob, "one omega per problem required");
@@ -152,6 +155,25 @@ static int assemble_common(thm_sys** out, const thm_mesh* m, const double* mu_in
                     s->pol[2 * k + 1] = pol[2 * k + 1];
                     s->dir[k] = dir[k];
                 }
+            }
+            if (ao && (ao->trans_re != 0.0 || ao->trans_im != 0.0)) {
+                THM_REQUIRE(std::isfinite(ao->trans_re) && std::isfinite(ao->trans_im),
+                            "non-finite transmission coefficient");
+                s->trans_re = ao->trans_re;
+                s->trans_im = ao->trans_im;
+            }
+            if (ao && ao->eps) {
+                s->eps.alloc(m->n_cell);
+                std::vector<double> e(m->n_cell);
+                if (ao->eps_on_device)
+                    THM_CUDA(cudaMemcpyAsync(e.data(), ao->eps, m->n_cell * sizeof(double), cudaMemcpyDeviceToHost,
+                                             s->st));
+                else
+                    std::copy(ao->eps, ao->eps + m->n_cell, e.begin());
+                THM_CUDA(cudaStreamSynchronize(s->st));
+                for (double v : e) THM_REQUIRE(std::isfinite(v) && v > 0, "eps must be finite and > 0");
+                THM_CUDA(cudaMemcpyAsync(s->eps.p, e.data(), m->n_cell * sizeof(double), cudaMemcpyHostToDevice, s->st));
+                THM_CUDA(cudaStreamSynchronize(s->st));
             }
             s->mu_inv.alloc(m->n_cell);
             if (mu_inv_on_device) {
@@ -195,8 +217,25 @@ int thm_assemble_dirichlet(thm_sys** out, const thm_mesh* m, const double* mu_in
         return THM_EINVAL;
     }
     static const double none = 0.0;
+    thm_assemble_opts ao{};
+    ao.u_dir = u_dir ? u_dir : &none;
+    ao.u_dir_on_device = u_dir_on_device;
     return assemble_common(out, m, mu_inv, mu_inv_on_device, std::vector<double>{omega}, kappa, nullptr, nullptr,
-                           stream, u_dir ? u_dir : &none, u_dir_on_device);
+                           stream, &ao);
+}
+
+int thm_assemble_ex(thm_sys** out, const thm_mesh* m, const double* mu_inv, int mu_inv_on_device,
+                    const double* omega, double kappa, const double* pol, const double* dir,
+                    const thm_assemble_opts* opts, void* stream) {
+    if (!m || !omega) {
+        set_last_error("NULL argument");
+        if (out) *out = nullptr;
+        return THM_EINVAL;
+    }
+    thm_assemble_opts ao{};
+    if (opts) ao = *opts;
+    return assemble_common(out, m, mu_inv, mu_inv_on_device, std::vector<double>(omega, omega + m->n_prob), kappa,
+                           pol, dir, stream, &ao);
 }
 
 int thm_mesh_dirichlet_dofs(const thm_mesh* m, int64_t* n_dir, int64_t* ids) {

@@ -241,8 +241,18 @@ struct thm_sys {
     double dir[3] = {0};
     thm::DArr<double> mu_inv;          // [n_cell]
     thm::DArr<double> ref;             // reference matrices (see assemble.cu)
-    thm::DArr<double> val64;           // SELL values of P_i, FP64
+    thm::DArr<double> val64;           // SELL values of P_i = Re(T_i), FP64
     thm::DArr<float> val32;            // same, FP32
+    // transmission coefficient on Sigma_ij in units of kappa*omega: (0, 1) is
+    // i kappa omega, the impedance condition of Eq. 5; a real part adds
+    // trans_re * kappa omega M_Sigma to Re(T_i) (and then K_i^loc, which has no
+    // Sigma terms, gets value arrays of its own)
+    double trans_re = 0.0, trans_im = 1.0;
+    thm::DArr<double> valK64;          // SELL values of Re(K_i^loc) when trans_re != 0
+    thm::DArr<float> valK32;
+    const double* kloc_val64() const { return valK64.p ? valK64.p : val64.p; }
+    const float* kloc_val32() const { return valK32.p ? valK32.p : val32.p; }
+    thm::DArr<double> eps;             // [n_cell] relative permittivity (mass-term weight), 1 if not given
     thm::DArr<double> bg64, bs64;      // kappa*omega * diagonal face masses: Gamma^inf, Sigma
     thm::DArr<float> bg32, bs32;
     thm::DArr<double> if_val;          // values of the interface-entry terms (face masses)

@@ -160,12 +160,15 @@ __global__ void __launch_bounds__(KT) k_chunk_dots(const Chunk* __restrict__ chu
                 ai += v.x * wr[q].y - v.y * wr[q].x;
             }
         }
+        // each thread sums its EPT products in the vector precision; from the
+        // warp reduction on every sum is FP64
+        double dr = (double)ar, di = (double)ai;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            ar += __shfl_down_sync(0xffffffffu, ar, o);
-            ai += __shfl_down_sync(0xffffffffu, ai, o);
+            dr += __shfl_down_sync(0xffffffffu, dr, o);
+            di += __shfl_down_sync(0xffffffffu, di, o);
         }
-        if (lane == 0) sred[k * (KT / 32) + warp] = make_double2((double)ar, (double)ai);
+        if (lane == 0) sred[k * (KT / 32) + warp] = make_double2(dr, di);
     }
     __syncthreads();
     for (int kk = threadIdx.x; kk < nk; kk += KT) {

@@ -134,7 +134,7 @@ extern "C" int thm_residual_noalloc(const thm_sys* s, const double* u, double* o
             THM_LAUNCH(THM_K_DDM, s->st,
                        k_na_residual<<<(unsigned)nb, NA_THREADS, 0, s->st>>>(
                            m->n_dof, m->d_copy_ptr.p, m->d_copy_idx.p, m->d_loc_gdof.p, m->d_slice_ptr.p,
-                           m->d_sell_col.p, s->val64.p, s->bg64.p, m->dim == 3 ? s->bvg64.p : nullptr, s->f_res.p,
+                           m->d_sell_col.p, s->kloc_val64(), s->bg64.p, m->dim == 3 ? s->bvg64.p : nullptr, s->f_res.p,
                            reinterpret_cast<const double2*>(u), scratch));
         }
         THM_LAUNCH(THM_K_DDM, s->st, k_na_finish<<<1, 256, 0, s->st>>>((int)nb, scratch, out));

@@ -35,18 +35,25 @@ __global__ void k_seg_reduce_real(int nseg, const int32_t* __restrict__ seg_ch, 
 }
 
 // Start of a cycle: beta = ||r||, activity, g = (beta, 0, ...).  On the first
-// cycle the per-segment target is tol * ||b_s|| (x = 0 there, so r = b).
+// cycle the per-segment target is tol * ||b_s|| (x = 0 there, so r = b), or
+// an absolute floor when that is larger: floor_fac * ||f_s|| with f_s the
+// segment's original right-hand side (fnrm2, optional), so that a refinement
+// cycle stops once the solve it refines is accurate enough.
 // A segment whose true residual did not fall below half of its value at the
 // previous cycle start has reached the accuracy its arithmetic allows
 // (FP32 iterates: about cond(T_i) * 6e-8) and stops as well.
 __global__ void k_cycle_start(int nseg, int m, const double* __restrict__ nrm2, double tol, int first,
+                              const double* __restrict__ fnrm2, double floor_fac,
                               double* __restrict__ target, double* __restrict__ beta, int* __restrict__ active,
                               int* __restrict__ kused, double2* __restrict__ gv, int* __restrict__ nact,
                               double* __restrict__ prev) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= nseg) return;
     double b = sqrt(nrm2[s]);
-    if (first) { target[s] = tol * b; prev[s] = INFINITY; }
+    if (first) {
+        target[s] = fnrm2 ? fmax(tol * b, floor_fac * sqrt(fnrm2[s])) : tol * b;
+        prev[s] = INFINITY;
+    }
     int a = b > target[s] && b > 0 && b < 0.5 * prev[s];
     prev[s] = b;
     active[s] = a;
@@ -162,11 +169,12 @@ __global__ void k_rhs(int64_t n, const double2* __restrict__ src, const int64_t*
 // Impedance-trace exchange (Eq. 6):  G_{i<-j} = -G_{j<-i} + 2 i kappa omega (M_Sigma_ij u_j)[g],
 // the face-mass product summed over the entry's terms (val already holds
 // kappa*omega times the face mass, so that a batch of problems with different
-// omega shares the kernel; kw is a further common factor, 1 here); a term on
-// a Dirichlet DOF of u_j uses u_D when the sweep carries the Dirichlet
-// lifting, else 0.
+// omega shares the kernel); (cr, ci) is the transmission coefficient in units
+// of kappa*omega, (0, 1) for the impedance condition (i kappa omega), so the
+// update is G = -G_partner + 2 (cr + i ci) (val . u_j).  A term on a Dirichlet
+// DOF of u_j uses u_D when the sweep carries the Dirichlet lifting, else 0.
 __global__ void k_exchange(int64_t n_if, const int32_t* __restrict__ partner, const int64_t* __restrict__ ptr,
-                           const int32_t* __restrict__ tcol, const double* __restrict__ val, double kw,
+                           const int32_t* __restrict__ tcol, const double* __restrict__ val, double cr, double ci,
                            const double2* __restrict__ g_in, const double2* __restrict__ u,
                            const double2* __restrict__ uD, double2* __restrict__ g_out) {
     int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -179,7 +187,7 @@ __global__ void k_exchange(int64_t n_if, const int32_t* __restrict__ partner, co
         ai += val[p] * x.y;
     }
     double2 gp = g_in ? g_in[partner[k]] : make_double2(0, 0);
-    g_out[k] = make_double2(-gp.x - 2.0 * kw * ai, -gp.y + 2.0 * kw * ar);
+    g_out[k] = make_double2(-gp.x + 2.0 * (cr * ar - ci * ai), -gp.y + 2.0 * (cr * ai + ci * ar));
 }
 
 // u[d] += u_loc[owner(d)] on free DOFs
@@ -369,7 +377,8 @@ struct Krylov {
 
     // Solve A x = b for all segments (x in/out).  A(in, out); M(in, out) or empty.
     KStats solve(const std::function<void(const V*, V*)>& A, const std::function<void(const V*, V*)>& M,
-                 const V* b, V* x, bool x_zero, double tol, int maxit, cudaStream_t st, bool single_cycle = false) {
+                 const V* b, V* x, bool x_zero, double tol, int maxit, cudaStream_t st, bool single_cycle = false,
+                 const double* fnrm2 = nullptr, double floor_fac = 0.0) {
         KStats ks;
         std::vector<int64_t> per_seg(nseg, 0);
         int total = 0;
@@ -385,8 +394,9 @@ struct Krylov {
         while (true) {
             seg_norm2(r.p, st);
             nact.zero(st);
-            THM_LAUNCH(THM_K_KRYLOV, st, k_cycle_start<<<nblk(nseg), 256, 0, st>>>(nseg, m, nrm.p, tol, first ? 1 : 0, target.p, beta.p,
-                                                      active.p, kused.p, gv.p, nact.p, prev.p));
+            THM_LAUNCH(THM_K_KRYLOV, st, k_cycle_start<<<nblk(nseg), 256, 0, st>>>(nseg, m, nrm.p, tol, first ? 1 : 0, fnrm2,
+                                                      floor_fac, target.p, beta.p, active.p, kused.p, gv.p,
+                                                      nact.p, prev.p));
             if (first && nseg == 1) {
                 double b0 = 0;
                 THM_CUDA(cudaMemcpyAsync(&b0, beta.p, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -757,7 +767,11 @@ static void subdomain_solves(thm_sys* s, const SolveCfg& c, const double2* b, do
             std::vector<int> na;
             w->nact_ir.download(na, st);
             if (na[0] == 0) break;
-            KStats ks = K.solve(A, M, w->b32.p, w->x32.p, true, c.cycle_tol, c.m_in, st, true);
+            // the cycle stops at cycle_tol (the FP32 limit) relative to its own
+            // right-hand side, or once the refined solve meets a quarter of
+            // the subdomain tolerance, whichever comes first
+            KStats ks = K.solve(A, M, w->b32.p, w->x32.p, true, c.cycle_tol, c.m_in, st, true, w->bn2.p,
+                                0.25 * c.inner_tol);
             ks.status = THM_OK;      // the refinement loop owns convergence
             add(rs, ks);
             THM_LAUNCH(THM_K_DDM, st, k_ir_update<<<nblk(m->n_loc), 256, 0, st>>>(m->n_loc, w->x32.p, x));
@@ -779,7 +793,8 @@ static void sweep(thm_sys* s, const SolveCfg& c, const double2* src, const doubl
     if (m->n_if > 0 && g_out)
         THM_LAUNCH(THM_K_DDM, st, k_exchange<<<nblk(m->n_if), 256, 0, st>>>(m->n_if, m->d_if_partner.p, m->d_if_ptr.p,
                                                                            m->d_if_tcol.p, s->if_val.p,
-                                                                           1.0, g_in, x, uD, g_out));
+                                                                           s->trans_re, s->trans_im, g_in, x, uD,
+                                                                           g_out));
     rs.sweeps++;
     THM_CUDA(cudaGetLastError());
 }
@@ -909,7 +924,7 @@ static double true_residual_rhs(thm_sys* s, const double2* f_loc, const double2*
     Work* w = s->w;
     cudaStream_t st = s->st;
     THM_LAUNCH(THM_K_DDM, st, k_scatter_loc<<<nblk(m->n_loc), 256, 0, st>>>(m->n_loc, m->d_loc_gdof.p, u, w->uloc.p));
-    apply_T<double2, double>(s, s->val64.p, s->bg64.p, s->bs64.p, 0, w->uloc.p, w->ytmp.p);   // K^loc
+    apply_T<double2, double>(s, s->kloc_val64(), s->bg64.p, s->bs64.p, 0, w->uloc.p, w->ytmp.p);   // K^loc
     THM_LAUNCH(THM_K_DDM, st, k_sub<double2><<<nblk(m->n_loc), 256, 0, st>>>(m->n_loc, f_loc, w->ytmp.p, w->rloc.p));
     THM_LAUNCH(THM_K_DDM, st, k_gather_sum<<<nblk(m->n_dof), 256, 0, st>>>(m->n_dof, m->d_copy_ptr.p, m->d_copy_idx.p, w->rloc.p, rglob));
     return global_norm(s, rglob, m->n_dof);
@@ -1000,8 +1015,8 @@ void apply_local(thm_sys* s, int op, int mode, const double2* x, double2* y) {
         check_device_error(s);
     } else {
         int use_bs = op == THM_OP_T;
-        if (f32) apply_T<double2, float>(s, s->val32.p, s->bg32.p, s->bs32.p, use_bs, x, y);
-        else apply_T<double2, double>(s, s->val64.p, s->bg64.p, s->bs64.p, use_bs, x, y);
+        if (f32) apply_T<double2, float>(s, use_bs ? s->val32.p : s->kloc_val32(), s->bg32.p, s->bs32.p, use_bs, x, y);
+        else apply_T<double2, double>(s, use_bs ? s->val64.p : s->kloc_val64(), s->bg64.p, s->bs64.p, use_bs, x, y);
     }
     THM_CUDA(cudaGetLastError());
     THM_CUDA(cudaStreamSynchronize(s->st));

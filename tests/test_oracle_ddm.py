@@ -104,3 +104,51 @@ def test_interface_sizes_small_config():
     D = ddm.setup(W.config("square32_p1"))
     assert D.n_iface == 128                           # 4 interfaces x 2 directions x 16 edges
     assert [len(s.dofs) for s in D.subs] == [544] * 4
+
+
+def _jacobi_map(D):
+    """The sweep map g -> A g of Eq. 8 (zero sources) as a dense matrix."""
+    n = D.n_iface
+    sv = ddm.subdomain_solver(D, "direct")
+    A = np.zeros((n, n), np.complex128)
+    for k in range(n):
+        e = np.zeros(n, np.complex128)
+        e[k] = 1.0
+        A[:, k] = ddm.sweep(D, e, None, False, sv)[0]
+    return A
+
+
+def test_fixed_point_is_monolithic_for_other_interface_coefficients():
+    """The argument that the DDM fixed point is the monolithic solution does
+    not use the value of the interface coefficient: real Robin and a
+    Dirichlet-like penalty give the same answer (solved by GMRES on Eq. 8)."""
+    P = W.square_problem(8, 2, 1, 9.0, mu_inv=W.mu_inv_lognormal(64, 0.3, "tr"))
+    u0 = fem.solve_monolithic(fem.assemble(P))
+    for c in (1.0, 50.0, 2.0 + 1.0j):
+        D = ddm.setup(P, transmission=c)
+        u, _ = ddm.solve(D, inner="direct", outer_tol=1e-13, outer_restart=400, outer_maxiter=400)
+        assert np.linalg.norm(u - u0) <= 1e-9 * np.linalg.norm(u0), c
+
+
+def test_dirichlet_like_interface_conditions_do_not_converge_for_large_omega():
+    """Section 3.1: the classical Schwarz decomposition with Dirichlet-like
+    interface conditions cannot be expected to converge for large omega,
+    while the impedance condition (S = 1) can.  Two strips (no cross points),
+    many wavelengths along the interface: the Jacobi map of Eq. 8 contracts
+    with the impedance coefficient i kappa omega and has spectral radius >= 1
+    with a real coefficient (Robin with a real parameter, or a large real
+    penalty: the Dirichlet-like limit)."""
+    mesh = W.structured_mesh_2d(16, 8, 2, 1)
+    pol, d = W.plane_wave_y(2)
+    P = W.Problem("strips", mesh, 1, np.ones(mesh.n_cell), 20.0, 1.0, pol, d)
+    rho = {}
+    for c in (1j, 1.0, 100.0):
+        lam = np.linalg.eigvals(_jacobi_map(ddm.setup(P, transmission=c)))
+        rho[c] = np.abs(lam).max()
+    assert rho[1j] < 1.0
+    assert rho[1.0] >= 1.0 - 1e-9 and rho[100.0] >= 1.0 - 1e-9
+    # and the plain fixed-point iteration: converges with impedance, not with the penalty
+    _, ij = ddm.solve(ddm.setup(P, transmission=1j), outer="jacobi", outer_tol=1e-8, outer_maxiter=3000)
+    _, idl = ddm.solve(ddm.setup(P, transmission=100.0), outer="jacobi", outer_tol=1e-8, outer_maxiter=300)
+    assert ij["hist"][-1] < 1e-8
+    assert idl["hist"][-1] > 1e-2

@@ -331,3 +331,67 @@ def test_given_dirichlet_values_superpose_and_reproduce_the_plane_wave():
     u12 = fem.solve_monolithic(fem.with_dirichlet(S, 2.0 * d1 - 0.5j * d2))
     assert np.linalg.norm(u12 - (2.0 * u1 - 0.5j * u2)) <= 1e-11 * np.linalg.norm(u12)
     assert np.array_equal(u1[dd], d1)
+
+
+# --------------------------------------------------------------------------
+# permittivity per cell (eps weights the mass term)
+# --------------------------------------------------------------------------
+def _robin_1d_p2_layered(n, omega, eps_e, kappa=1.0):
+    """Textbook 1-D quadratic Lagrange FE for v'' + w^2 eps(x) v = 0 with eps
+    constant per element, v(0) = 1, v'(1) = -i k w v(1) (dense solve)."""
+    h = 1.0 / n
+    N = 2 * n + 1
+    K = np.zeros((N, N), np.complex128)
+    Ke = np.array([[7, -8, 1], [-8, 16, -8], [1, -8, 7]]) / (3 * h)
+    Me = np.array([[4, 2, -1], [2, 16, 2], [-1, 2, 4]]) * h / 30
+    for e in range(n):
+        idx = [2 * e, 2 * e + 1, 2 * e + 2]
+        K[np.ix_(idx, idx)] += Ke - omega ** 2 * eps_e[e] * Me
+    K[N - 1, N - 1] += 1j * kappa * omega
+    v = np.zeros(N, np.complex128)
+    v[0] = 1.0
+    v[1:] = np.linalg.solve(K[1:, 1:], -K[1:, 0])
+
+    def ev(x):
+        j = np.minimum(np.floor(x / h).astype(int), n - 1)
+        t = x / h - j
+        return (v[2 * j] * 2 * (t - 0.5) * (t - 1) + v[2 * j + 1] * (-4) * t * (t - 1)
+                + v[2 * j + 2] * 2 * t * (t - 0.5))
+    return ev
+
+
+def _max_plane_wave_error(P, S, u, v, seed):
+    rng = np.random.default_rng(seed)
+    worst = 0.0
+    for c in range(P.mesh.n_cell):
+        xi = rng.random((3, 2))
+        E = fem.evaluate_field(P.mesh, S.dofs, u, c, xi)
+        X = fem.physical_point(P.mesh, c, xi)
+        worst = max(worst, np.abs(E[:, 1] - v(X[:, 0])).max(), np.abs(E[:, 0]).max())
+    return worst
+
+
+def test_constant_eps_is_the_closed_form_with_scaled_wavenumber():
+    """eps = n^2 everywhere: omega^2 eps M is the mass term of wavenumber
+    omega n, while the impedance row keeps i kappa omega = i (kappa/n)(omega n):
+    the 1-D closed form with (omega n, kappa / n)."""
+    n, omega, ref = 8, 4.0, 1.5
+    P = W.square_problem(n, 1, 1, omega, bc="planewave", relabel=True, rotate_cells=True)
+    P.eps = np.full(P.mesh.n_cell, ref ** 2)
+    S = fem.assemble(P)
+    u = fem.solve_monolithic(S)
+    assert _max_plane_wave_error(P, S, u, _robin_1d_p1(n, omega * ref, kappa=1.0 / ref), 5) < 1e-12
+
+
+def test_layered_eps_matches_a_1d_solve():
+    """eps constant on each column of cells (layers across the propagation
+    direction, refractive index 1.516 in some): the 2-D order-2 solution is
+    the 1-D quadratic FE solution with per-element eps."""
+    n, omega = 8, 6.0
+    P = W.square_problem(n, 1, 2, omega, bc="planewave", relabel=True, rotate_cells=True)
+    col_eps = np.where(np.arange(n) % 3 == 1, 1.516 ** 2, 1.0)
+    X = P.mesh.coords[P.mesh.cells].mean(1)
+    P.eps = col_eps[np.floor(X[:, 0] * n).astype(int)]
+    S = fem.assemble(P)
+    u = fem.solve_monolithic(S)
+    assert _max_plane_wave_error(P, S, u, _robin_1d_p2_layered(n, omega, col_eps), 6) < 1e-12

@@ -311,6 +311,7 @@ class Problem:
     kappa: float
     pol: np.ndarray       # complex [dim]: E_inc(x) = pol * exp(-i omega dir.x)
     direction: np.ndarray  # real unit [dim]
+    eps: np.ndarray | None = None   # relative permittivity per cell (None: 1 everywhere)
 
 
 def plane_wave_y(dim: int):
@@ -336,6 +337,21 @@ def cube_problem(n: int, s: int, omega: float, *, kappa: float = 1.0, mu_inv=Non
         mu_inv = np.ones(mesh.n_cell)
     pol, d = plane_wave_y(3)
     return Problem(name, mesh, 1, np.asarray(mu_inv, np.float64), float(omega), float(kappa), pol, d)
+
+
+def block_benchmark(n: int, s: int, order: int, omega: float, *, n_core: float = 1.516,
+                    name: str = "block") -> Problem:
+    """The block benchmark of the paper's Example 1 (Section 4) as far as it is
+    described: the unit square with a centre block of refractive index
+    n_core = 1.516 in air (n = 1).  The block's size is not given; here it is
+    the centre square [0.25, 0.75]^2.  eps = n^2 per cell, mu^{-1} = 1,
+    Dirichlet x = 0 with E_inc = (0, exp(-i omega x)), impedance elsewhere,
+    n x n quads in s x s subdomains."""
+    P = square_problem(n, s, order, omega, name=name)
+    X = P.mesh.coords[P.mesh.cells].mean(1)
+    inside = np.all((X > 0.25) & (X < 0.75), axis=1)
+    P.eps = np.where(inside, n_core ** 2, 1.0).astype(np.float64)
+    return P
 
 
 def config(name: str) -> Problem:
