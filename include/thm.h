@@ -243,10 +243,20 @@ typedef struct thm_solve_opts {
                               g <- A g + b of the same map, stopped when
                               ||(I - A) g - b|| <= outer_tol ||b|| (norms over
                               the whole interface vector, also for a batch) */
+    int    precond;        /* preconditioner of the subdomain GMRES (Section 3.2):
+                              THM_PRECOND_BLOCKDIAG (0): blockdiag(P_i, P_i)^{-1} of
+                              Eq. 7 on the real/imaginary splitting (default);
+                              THM_PRECOND_FULL (1): the exact inverse of the full
+                              2x2 block operator [[P_i, -B_i], [B_i, P_i]] (the real
+                              form of T_i, Eq. 3), i.e. T_i^{-1} from complex
+                              factors: GMRES then needs one step per solve (FP64)
+                              for twice the factor memory.  2-D meshes only. */
 } thm_solve_opts;
 
 #define THM_OUTER_GMRES 0
 #define THM_OUTER_JACOBI 1
+#define THM_PRECOND_BLOCKDIAG 0
+#define THM_PRECOND_FULL 1
 
 typedef struct thm_stats {
     int    outer_iters;        /* interface GMRES iterations, summed over refinement */
@@ -325,10 +335,12 @@ int thm_iface_dofs(const thm_sys* s, int32_t* recv, int32_t* send, int64_t* gdof
  *   THM_OP_T     y = T_i x   for all i (Eq. 5's subdomain operator)
  *   THM_OP_PINV  y = P_i^{-1} x  (Eq. 7: the same real P_i^{-1} on Re and Im)
  *   THM_OP_KLOC  y = (T_i - i kappa omega sum_j M_Sigma_ij) x  (no transmission term)
+ *   THM_OP_TINV  y = T_i^{-1} x  (the full 2x2 block preconditioner; 2-D only)
  * mode selects FP64 or FP32 storage of the operator (vectors stay FP64 here). */
 #define THM_OP_T    0
 #define THM_OP_PINV 1
 #define THM_OP_KLOC 2
+#define THM_OP_TINV 3
 int thm_apply_local(thm_sys* s, int op, int mode, const double* x, double* y);
 
 /* One DDM sweep (Eqs. 5-6) on interface data g_in (device complex [n_iface]):
@@ -408,6 +420,12 @@ int thm_work_bytes(const thm_sys* s, int mode, int cls, double* bytes);
  *  No cudaMalloc, cudaFree or allocating library call is made.
  * ------------------------------------------------------------------------ */
 int thm_residual_noalloc(const thm_sys* s, const double* u, double* out);
+
+/* Bytes of the stored preconditioner factors (the dense inverse blocks W_l of
+ * the twisted block factorisation) for precond THM_PRECOND_* in mode
+ * THM_MODE_*: real values for Eq. 7, complex ones for the full 2x2 block
+ * operator.  From the sizes alone (nothing is factorised by this call). */
+int thm_factor_bytes(const thm_sys* s, int precond, int mode, double* bytes);
 
 /* Kernel launches issued by this library since the process started. */
 int64_t thm_kernel_launches(void);

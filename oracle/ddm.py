@@ -29,7 +29,9 @@ fixed point is the monolithic discrete solution (pinned by a test).
 
 Subdomain solves are either direct (sparse LU) or, as in Section 3.2, GMRES
 right-preconditioned with the block-diagonal operator of Eq. 7, i.e. the real
-matrix P_i = A_i - omega^2 M_i applied to real and imaginary parts alike.
+matrix P_i = A_i - omega^2 M_i applied to real and imaginary parts alike, or
+with the full 2x2 block operator that Section 3.2 describes as the
+alternative (its exact inverse; with the sign of Eq. 3 it is T_ff^{-1}).
 """
 from __future__ import annotations
 
@@ -167,6 +169,43 @@ def subdomain_solver(ddm: DDM, kind: str = "direct", inner_tol: float = 1e-12,
             if s.lu_T is None:
                 s.lu_T = spla.splu(s.Tff)
         return lambda i, rhs: ddm.subs[i].lu_T.solve(rhs)
+    if kind == "full_block":
+        # the full 2x2 block operator of Section 3.2 with the sign of Eq. 3,
+        # [[P, -B], [B, P]], is the real form of T_ff itself: its exact inverse
+        # is T_ff^{-1}, so right-preconditioned GMRES stops after one step
+        for s in ddm.subs:
+            if s.lu_T is None:
+                s.lu_T = spla.splu(s.Tff)
+
+        def solve_full(i, rhs):
+            s = ddm.subs[i]
+            x, it, _ = gmres(lambda v: s.Tff @ v, rhs, precond=s.lu_T.solve, tol=inner_tol, restart=restart,
+                             maxiter=maxiter)
+            ddm.stats["inner_iters"].append((i, it))
+            return x
+        return solve_full
+    if kind == "full_block_printed":
+        # the same block operator with the off-diagonal signs as printed in
+        # Section 3.2, [[P, -B], [-B, P]] (a real symmetric matrix), applied
+        # to the real/imaginary splitting of the residual
+        lus = {}
+
+        def solve_printed(i, rhs):
+            s = ddm.subs[i]
+            if i not in lus:
+                Bm = sp.csc_matrix((np.ascontiguousarray(s.Tff.data.imag), s.Tff.indices.copy(),
+                                    s.Tff.indptr.copy()), shape=s.Tff.shape)
+                lus[i] = spla.splu(sp.bmat([[s.P, -Bm], [-Bm, s.P]], format="csc"))
+            nf = s.Tff.shape[0]
+
+            def prec(v):
+                y = lus[i].solve(np.concatenate([v.real, v.imag]))
+                return y[:nf] + 1j * y[nf:]
+            x, it, _ = gmres(lambda v: s.Tff @ v, rhs, precond=prec, tol=inner_tol, restart=restart,
+                             maxiter=maxiter)
+            ddm.stats["inner_iters"].append((i, it))
+            return x
+        return solve_printed
     if kind == "block_gmres":
         for s in ddm.subs:
             if s.lu_P is None:

@@ -13,7 +13,7 @@ from __future__ import annotations
 
 from ._binding import (  # noqa: F401
     K_DDM, K_DOTS, K_KRYLOV, K_NAMES, K_PINV, K_SETUP, K_SPMV, K_UPDATE, LIB_PATH, MODE_FP64,
-    MODE_MIXED, OP_KLOC, OP_PINV, OP_T, TAG_DIRICHLET, TAG_IMPEDANCE, TAG_NATURAL, Mesh,
-    SolveOptions, System, ThmError, algorithmic_bytes, kernel_launches, load, profile_enable,
-    profile_read, symbols, work_bytes,
+    MODE_MIXED, OP_KLOC, OP_PINV, OP_T, OP_TINV, PRECOND_BLOCKDIAG, PRECOND_FULL, TAG_DIRICHLET,
+    TAG_IMPEDANCE, TAG_NATURAL, AssembleOptions, Mesh, SolveOptions, System, ThmError, algorithmic_bytes,
+    factor_bytes, kernel_launches, load, profile_enable, profile_read, symbols, work_bytes,
 )

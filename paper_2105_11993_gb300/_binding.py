@@ -11,7 +11,8 @@ LIB_PATH = os.path.join(HERE, "_build", "libthm.so")
 
 THM_OK = 0
 MODE_FP64, MODE_MIXED = 0, 1
-OP_T, OP_PINV, OP_KLOC = 0, 1, 2
+OP_T, OP_PINV, OP_KLOC, OP_TINV = 0, 1, 2, 3
+PRECOND_BLOCKDIAG, PRECOND_FULL = 0, 1
 TAG_IMPEDANCE, TAG_DIRICHLET, TAG_NATURAL = 0, 1, 2
 
 ERRORS = {-1: "EINVAL", -2: "ENOCONV", -3: "EBREAKDOWN", -4: "ESINGULAR", -5: "ETIMEOUT",
@@ -24,7 +25,7 @@ symbols = [
     "thm_local_dofs", "thm_iface_dofs", "thm_apply_local", "thm_sweep", "thm_local_sources",
     "thm_dirichlet_values", "thm_kernel_launches", "thm_profile_enable", "thm_profile_read",
     "thm_alg_bytes", "thm_residual_noalloc", "thm_mesh_set_problems", "thm_assemble_batch", "thm_work_bytes",
-    "thm_mesh_dirichlet_dofs", "thm_assemble_dirichlet", "thm_assemble_ex",
+    "thm_mesh_dirichlet_dofs", "thm_assemble_dirichlet", "thm_assemble_ex", "thm_factor_bytes",
 ]
 
 
@@ -38,7 +39,7 @@ class SolveOptions(C.Structure):
     _fields_ = [("mode", C.c_int), ("rtol", C.c_double), ("inner_restart", C.c_int),
                 ("inner_tol", C.c_double), ("inner_maxit", C.c_int), ("outer_restart", C.c_int),
                 ("outer_tol", C.c_double), ("outer_maxit", C.c_int), ("max_refine", C.c_int),
-                ("relax", C.c_int), ("outer_method", C.c_int)]
+                ("relax", C.c_int), ("outer_method", C.c_int), ("precond", C.c_int)]
 
 
 class AssembleOptions(C.Structure):
@@ -96,6 +97,7 @@ def load():
         "thm_profile_enable": [C.c_uint],
         "thm_profile_read": [C.c_int, P, P],
         "thm_alg_bytes": [P, C.c_int, C.c_int, P],
+        "thm_factor_bytes": [P, C.c_int, C.c_int, P],
         "thm_work_bytes": [P, C.c_int, C.c_int, P],
         "thm_residual_noalloc": [P, P, P],
     }
@@ -131,6 +133,15 @@ def algorithmic_bytes(sysg, mode, cls) -> float:
     b = C.c_double()
     m = MODE_MIXED if mode == "mixed" else MODE_FP64
     _check(load().thm_alg_bytes(sysg.h, m, int(cls), C.byref(b)))
+    return b.value
+
+
+def factor_bytes(sysg, precond="blockdiag", mode="mixed") -> float:
+    """thm_factor_bytes: bytes of the stored preconditioner factors."""
+    b = C.c_double()
+    pc = PRECOND_FULL if precond == "full" else PRECOND_BLOCKDIAG
+    m = MODE_MIXED if mode == "mixed" else MODE_FP64
+    _check(load().thm_factor_bytes(sysg.h, pc, m, C.byref(b)))
     return b.value
 
 
@@ -242,11 +253,12 @@ OUTER_GMRES, OUTER_JACOBI = 0, 1
 
 
 def _opts(mode="fp64", rtol=1e-8, inner_restart=0, inner_tol=0.0, inner_maxit=0, outer_restart=0,
-          outer_tol=0.0, outer_maxit=0, max_refine=0, relax=0, outer="gmres"):
+          outer_tol=0.0, outer_maxit=0, max_refine=0, relax=0, outer="gmres", precond="blockdiag"):
     m = {"fp64": MODE_FP64, "mixed": MODE_MIXED}[mode] if isinstance(mode, str) else int(mode)
     om = {"gmres": OUTER_GMRES, "jacobi": OUTER_JACOBI}[outer] if isinstance(outer, str) else int(outer)
+    pc = {"blockdiag": PRECOND_BLOCKDIAG, "full": PRECOND_FULL}[precond] if isinstance(precond, str) else int(precond)
     return SolveOptions(m, rtol, inner_restart, inner_tol, inner_maxit, outer_restart, outer_tol,
-                        outer_maxit, max_refine, int(relax), om)
+                        outer_maxit, max_refine, int(relax), om, pc)
 
 
 class System:

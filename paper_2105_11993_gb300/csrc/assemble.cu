@@ -686,6 +686,208 @@ __global__ void k_bt_factor(int mid, const Sub* __restrict__ subs, const Level* 
     }
 }
 
+// ---------------------------------------------------------------------------
+// The full 2x2 block operator of Section 3.2 ([[P, -B], [B, P]], the real form
+// of T = P + iB) factorised the same way in complex arithmetic: S_l and
+// W_l = S_l^{-1} complex (symmetric), couplings real.  2-D only: there B is
+// diagonal (the face masses of Gamma^inf and Sigma on the edge rows; the
+// order-2 bubbles have no tangential trace), so the level couplings of T are
+// those of P and the diagonal blocks gain i B on their diagonal.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double2 zmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 zdiv(double2 a, double2 b) {
+    const double d = b.x * b.x + b.y * b.y;
+    return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+
+__device__ bool cta_gauss_jordan_c(double2* W, int m, int ld, int* perm, double2* fcol, double* rv, int* ri) {
+    __shared__ int s_piv;
+    __shared__ int s_bad;
+    if (threadIdx.x == 0) s_bad = 0;
+    __syncthreads();
+    for (int k = 0; k < m; ++k) {
+        // pivot: largest |W[i][k]|, i >= k (lowest index on ties)
+        double best = -1;
+        int bi = -1;
+        for (int i = k + threadIdx.x; i < m; i += blockDim.x) {
+            const double2 v = W[(int64_t)i * ld + k];
+            const double a = hypot(v.x, v.y);
+            if (a > best) { best = a; bi = i; }
+        }
+        rv[threadIdx.x] = best;
+        ri[threadIdx.x] = bi;
+        __syncthreads();
+        for (int sh = blockDim.x / 2; sh > 0; sh >>= 1) {
+            if (threadIdx.x < sh) {
+                const double o = rv[threadIdx.x + sh];
+                const int oi = ri[threadIdx.x + sh];
+                if (o > rv[threadIdx.x] || (o == rv[threadIdx.x] && oi >= 0 && (ri[threadIdx.x] < 0 || oi < ri[threadIdx.x]))) {
+                    rv[threadIdx.x] = o;
+                    ri[threadIdx.x] = oi;
+                }
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            s_piv = ri[0];
+            if (!(rv[0] > 0) || !isfinite(rv[0])) s_bad = 1;
+            perm[k] = ri[0] < 0 ? k : ri[0];
+        }
+        __syncthreads();
+        if (s_bad) return false;
+        const int p = s_piv;
+        if (p != k)
+            for (int j = threadIdx.x; j < m; j += blockDim.x) {
+                const double2 a = W[(int64_t)k * ld + j];
+                W[(int64_t)k * ld + j] = W[(int64_t)p * ld + j];
+                W[(int64_t)p * ld + j] = a;
+            }
+        __syncthreads();
+        for (int i = threadIdx.x; i < m; i += blockDim.x)
+            fcol[i] = (i == k) ? make_double2(0, 0) : W[(int64_t)i * ld + k];
+        __syncthreads();
+        const double2 piv = W[(int64_t)k * ld + k];
+        __syncthreads();
+        for (int j = threadIdx.x; j < m; j += blockDim.x) {
+            const double2 v = (j == k) ? make_double2(1, 0) : W[(int64_t)k * ld + j];
+            W[(int64_t)k * ld + j] = zdiv(v, piv);
+        }
+        __syncthreads();
+        for (int64_t t = threadIdx.x; t < (int64_t)m * m; t += blockDim.x) {
+            const int i = (int)(t / m), j = (int)(t % m);
+            if (i == k) continue;
+            const int64_t o = (int64_t)i * ld + j;
+            const double2 a = (j == k) ? make_double2(0, 0) : W[o];
+            const double2 f = zmul(fcol[i], W[(int64_t)k * ld + j]);
+            W[o] = make_double2(a.x - f.x, a.y - f.y);
+        }
+        __syncthreads();
+    }
+    for (int k = m - 1; k >= 0; --k) {
+        const int p = perm[k];
+        if (p != k)
+            for (int i = threadIdx.x; i < m; i += blockDim.x) {
+                const double2 a = W[(int64_t)i * ld + k];
+                W[(int64_t)i * ld + k] = W[(int64_t)i * ld + p];
+                W[(int64_t)i * ld + p] = a;
+            }
+        __syncthreads();
+    }
+    return true;
+}
+
+// D_l + i B_l of level L (B diagonal: bg + bs of the rows)
+__device__ void extract_block_c(const Level& L, double2* dst, int ld, const int64_t* slice_ptr, const int32_t* col,
+                                const uint8_t* pad, const double* val, const double* bg, const double* bs) {
+    for (int64_t t = threadIdx.x; t < (int64_t)L.size * ld; t += blockDim.x) dst[t] = make_double2(0, 0);
+    __syncthreads();
+    for (int i = threadIdx.x; i < L.size; i += blockDim.x) {
+        const int64_t r = L.start + i;
+        const int64_t sl = r / SELL_C;
+        const int lane = (int)(r % SELL_C);
+        const int64_t base = slice_ptr[sl];
+        const int w = (int)((slice_ptr[sl + 1] - base) / SELL_C);
+        for (int t = 0; t < w; ++t) {
+            const int64_t idx = base + (int64_t)t * SELL_C + lane;
+            if (pad[idx]) continue;
+            const int64_t cc = col[idx];
+            if (cc >= L.start && cc < L.start + L.size) dst[(int64_t)i * ld + (cc - L.start)].x = val[idx];
+        }
+        dst[(int64_t)i * ld + i].y = bg[r] + bs[r];
+    }
+    __syncthreads();
+}
+
+// W (complex, m_l x r4(m_l)) -= C W_n C^T with the real coupling list C
+__device__ void schur_update_c(const Level& L, const Level& N, int side, double2* W, const double2* Wn, double2* tT,
+                               const int32_t* __restrict__ cptr, const int32_t* __restrict__ ccol,
+                               const double* __restrict__ cval) {
+    const int32_t* P = cptr + (side == 0 ? L.eptr : L.fptr);
+    const int32_t* Cc = ccol + (side == 0 ? L.eoff : L.foff);
+    const double* Cv = cval + (side == 0 ? L.eoff : L.foff);
+    const int ml = L.size, mn = N.size, ldn = ld4(mn), ldl = ld4(ml);
+    for (int64_t t = threadIdx.x; t < (int64_t)ml * mn; t += blockDim.x) {
+        const int i = (int)(t / mn), j = (int)(t % mn);
+        double2 acc = make_double2(0, 0);
+        for (int p = P[i]; p < P[i + 1]; ++p) {
+            const double2 wv = Wn[(int64_t)Cc[p] * ldn + j];
+            acc.x += Cv[p] * wv.x;
+            acc.y += Cv[p] * wv.y;
+        }
+        tT[t] = acc;
+    }
+    __syncthreads();
+    for (int64_t t = threadIdx.x; t < (int64_t)ml * ml; t += blockDim.x) {
+        const int i = (int)(t / ml), j = (int)(t % ml);
+        double2 acc = make_double2(0, 0);
+        for (int q = P[j]; q < P[j + 1]; ++q) {
+            const double2 tv = tT[(int64_t)i * mn + Cc[q]];
+            acc.x += tv.x * Cv[q];
+            acc.y += tv.y * Cv[q];
+        }
+        W[(int64_t)i * ldl + j].x -= acc.x;
+        W[(int64_t)i * ldl + j].y -= acc.y;
+    }
+    __syncthreads();
+}
+
+// As k_bt_factor, in complex arithmetic (mid 0: both chains; mid 1: middle level).
+__global__ void k_bt_factor_c(int mid, const Sub* __restrict__ subs, const Level* __restrict__ levels,
+                              const int64_t* __restrict__ slice_ptr, const int32_t* __restrict__ col,
+                              const uint8_t* __restrict__ pad, const double* __restrict__ sval,
+                              const double* __restrict__ bg, const double* __restrict__ bs,
+                              const int32_t* __restrict__ cptr, const int32_t* __restrict__ ccol,
+                              const double* __restrict__ cval, double2* fac, double2* tmp_all, int64_t tmp_stride,
+                              int* perm_all, int max_m, int* status) {
+    extern __shared__ unsigned char smem_raw[];
+    double2* fcol = reinterpret_cast<double2*>(smem_raw);
+    double* rv = reinterpret_cast<double*>(fcol + max_m);
+    int* ri = reinterpret_cast<int*>(rv + blockDim.x);
+    const int s = blockIdx.x, chain = mid ? 0 : blockIdx.y;
+    const Sub S = subs[s];
+    if (S.nlev == 0) return;
+    double2* tT = tmp_all + ((int64_t)s * 2 + chain) * tmp_stride;
+    int* perm = perm_all + ((int64_t)s * 2 + chain) * max_m;
+    const int k = S.kmid;
+    if (mid) {
+        const Level L = levels[S.lev0 + k];
+        double2* W = fac + L.offW;
+        extract_block_c(L, W, ld4(L.size), slice_ptr, col, pad, sval, bg, bs);
+        if (k > 0) {
+            const Level N = levels[S.lev0 + k - 1];
+            schur_update_c(L, N, 0, W, fac + N.offW, tT, cptr, ccol, cval);
+        }
+        if (k + 1 < S.nlev) {
+            const Level N = levels[S.lev0 + k + 1];
+            schur_update_c(L, N, 1, W, fac + N.offW, tT, cptr, ccol, cval);
+        }
+        if (!cta_gauss_jordan_c(W, L.size, ld4(L.size), perm, fcol, rv, ri) && threadIdx.x == 0) atomicExch(status, 1);
+        return;
+    }
+    const int n = chain == 0 ? k : S.nlev - 1 - k;
+    for (int q = 0; q < n; ++q) {
+        const int l = chain == 0 ? q : S.nlev - 1 - q;
+        const Level L = levels[S.lev0 + l];
+        double2* W = fac + L.offW;
+        extract_block_c(L, W, ld4(L.size), slice_ptr, col, pad, sval, bg, bs);
+        if (q > 0) {
+            const Level N = levels[S.lev0 + (chain == 0 ? l - 1 : l + 1)];
+            schur_update_c(L, N, chain == 0 ? 0 : 1, W, fac + N.offW, tT, cptr, ccol, cval);
+        }
+        if (!cta_gauss_jordan_c(W, L.size, ld4(L.size), perm, fcol, rv, ri)) {
+            if (threadIdx.x == 0) atomicExch(status, 1);
+            return;
+        }
+    }
+}
+
+__global__ void k_to_float2(int64_t n, const double2* __restrict__ a, float2* __restrict__ b) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) b[i] = make_float2((float)a[i].x, (float)a[i].y);
+}
+
 __global__ void k_gather_slots(int64_t n, const int64_t* __restrict__ slot, const double* __restrict__ v,
                                double* __restrict__ o64, float* __restrict__ o32) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -920,6 +1122,47 @@ static void factor64(thm_sys* s) {
     if (hs[0] != 0)
         fail(THM_ESINGULAR, "a diagonal block of P_i = A_i - omega^2 M_i is singular "
                             "(omega^2 is a natural-boundary eigenvalue of a subdomain block)");
+}
+
+static void factor_full64(thm_sys* s) {
+    const thm_mesh* m = s->m;
+    cudaStream_t st = s->st;
+    THM_REQUIRE(m->dim == 2, "the full 2x2 block preconditioner is built for 2-D meshes (diagonal B) only");
+    s->facc64.alloc(m->fac_elems);
+    s->facc64.zero(st);
+    DArr<double2> tmp;
+    const int64_t stride = (int64_t)m->max_m * m->max_m;
+    tmp.alloc((size_t)stride * m->n_sub * 2);
+    DArr<int> perm, status;
+    perm.alloc((size_t)m->max_m * m->n_sub * 2);
+    status.alloc(1);
+    status.zero(st);
+    const int threads = 512;
+    size_t smem = (size_t)m->max_m * sizeof(double2) + threads * (sizeof(double) + sizeof(int));
+    if (smem > 48 * 1024)
+        THM_CUDA(cudaFuncSetAttribute(k_bt_factor_c, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    THM_LAUNCH(THM_K_SETUP, st, k_bt_factor_c<<<dim3(m->n_sub, 2), threads, smem, st>>>(
+        0, m->d_subs.p, m->d_levels.p, m->d_slice_ptr.p, m->d_sell_col.p, m->d_sell_pad.p, s->sval64.p, s->bg64.p,
+        s->bs64.p, m->d_cpl_ptr.p, m->d_cpl_col.p, s->cpl64.p, s->facc64.p, tmp.p, stride, perm.p, m->max_m, status.p));
+    THM_LAUNCH(THM_K_SETUP, st, k_bt_factor_c<<<m->n_sub, threads, smem, st>>>(
+        1, m->d_subs.p, m->d_levels.p, m->d_slice_ptr.p, m->d_sell_col.p, m->d_sell_pad.p, s->sval64.p, s->bg64.p,
+        s->bs64.p, m->d_cpl_ptr.p, m->d_cpl_col.p, s->cpl64.p, s->facc64.p, tmp.p, stride, perm.p, m->max_m, status.p));
+    THM_CUDA(cudaGetLastError());
+    std::vector<int> hs;
+    status.download(hs, st);
+    if (hs[0] != 0) fail(THM_ESINGULAR, "a diagonal block of the complex subdomain operator T_i is singular");
+}
+
+// The full-block factors (complex), FP64 and for the mixed mode FP32.
+void ensure_factor_full(thm_sys* s, bool fp32) {
+    if (!s->facc64_ok) { factor_full64(s); s->facc64_ok = true; }
+    if (fp32 && !s->facc32_ok) {
+        s->facc32.alloc(s->facc64.n);
+        THM_LAUNCH(THM_K_SETUP, 0, k_to_float2<<<(unsigned)((s->facc64.n + 255) / 256), 256, 0, s->st>>>(
+            (int64_t)s->facc64.n, s->facc64.p, s->facc32.p));
+        THM_CUDA(cudaGetLastError());
+        s->facc32_ok = true;
+    }
 }
 
 // The factorisation runs in FP64 for both modes (pivots and Schur updates in

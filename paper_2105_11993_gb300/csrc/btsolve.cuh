@@ -45,9 +45,13 @@ namespace thm {
 constexpr int BT_NT = 384;                  // consumer threads
 constexpr int BT_NW = BT_NT / 32;           // consumer warps
 constexpr int BT_THREADS = BT_NT + 32;      // + one producer warp
-constexpr int BT_GQ = 8;                    // output quads per quad group (one group per warp pass)
-constexpr int BT_GMAX = 4;                  // quad groups per warp: m_l <= 4 * BT_GQ * BT_GMAX * BT_NW
-constexpr int BT_MAX_M = 4 * BT_GQ * BT_GMAX * BT_NW;
+// GEMV layout: a warp pass covers GQ = 8 output quads with 4 row subsets, and
+// a warp holds at most GMAX quad groups, so m_l <= 4 * GQ * GMAX * BT_NW.
+// (A finer layout, 2 quads x 16 row subsets, keeps every warp busy on 130-row
+// levels but measured slower: 139 against 116 us per launch.)
+constexpr int BT_GQ = 8;
+constexpr int BT_GMAX = 4;
+constexpr int BT_MAX_M = 4 * BT_GQ * BT_GMAX * BT_NW;     // 1536
 constexpr int BT_NC = 4;                    // slots of the coupling ring
 
 __host__ __device__ constexpr int bt_r4(int v) { return (v + 3) / 4 * 4; }
@@ -123,12 +127,45 @@ __device__ __forceinline__ bool mbar_try_cluster(uint64_t* bar, unsigned parity)
     return done != 0;
 }
 
-// Bounded wait that gives up at once when the CTA has already aborted.
+// try_wait with a suspend-time hint: a thread whose phase is not complete
+// sleeps (up to the hint) instead of spinning, so waiting warps take no issue
+// slots from the working ones.
+__device__ __forceinline__ bool mbar_try_sleep(uint64_t* bar, unsigned parity) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(2000u)
+        : "memory");
+    return done != 0;
+}
+__device__ __forceinline__ bool mbar_try_cluster_sleep(uint64_t* bar, unsigned parity) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2, %3;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(2000u)
+        : "memory");
+    return done != 0;
+}
+__device__ __forceinline__ unsigned long long bt_now_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+constexpr unsigned long long BT_WAIT_LIMIT_NS = 1000000000ull;     // 1 s per wait
+
+// Bounded wait (1 s of wall time) that gives up at once when the CTA has
+// already aborted; on expiry it raises the abort flag and *err.
 template <bool CLUSTER>
 __device__ __forceinline__ bool bt_wait(uint64_t* bar, unsigned parity, volatile int* abort, int* err) {
-    for (int it = 0; it < (1 << 22); ++it) {
-        if (CLUSTER ? mbar_try_cluster(bar, parity) : mbar_try(bar, parity)) return true;
+    if (CLUSTER ? mbar_try_cluster(bar, parity) : mbar_try(bar, parity)) return true;
+    const unsigned long long t0 = bt_now_ns();
+    while (true) {
+        if (CLUSTER ? mbar_try_cluster_sleep(bar, parity) : mbar_try_sleep(bar, parity)) return true;
         if (*abort) return false;
+        if (bt_now_ns() - t0 > BT_WAIT_LIMIT_NS) break;
     }
     *abort = 1;
     atomicExch(err, 1);
@@ -183,9 +220,47 @@ __host__ __device__ inline BtLayout bt_layout(int ns, int slot_bytes, int cslot_
     return L;
 }
 
-template <class V, class F>
+// W element types: real factors (Eq. 7) or complex ones (the full 2x2 block
+// operator of Section 3.2, T_i^{-1}).
+template <class T> struct BtCplx { static constexpr bool value = false; };
+template <> struct BtCplx<float2> { static constexpr bool value = true; };
+template <> struct BtCplx<double2> { static constexpr bool value = true; };
+
+// acc[c] += W[j][4q + c] * s for one quad of one W row (real or complex W)
+template <class FW, class Rt, class V>
+__device__ __forceinline__ void bt_quad_fma(const FW* p, const V s, Rt (&acc)[4][2]) {
+    if constexpr (BtCplx<FW>::value) {
+        Rt wr[4], wi[4];
+        if constexpr (sizeof(FW) == 8) {
+            const float4 a = reinterpret_cast<const float4*>(p)[0], b = reinterpret_cast<const float4*>(p)[1];
+            wr[0] = a.x; wi[0] = a.y; wr[1] = a.z; wi[1] = a.w; wr[2] = b.x; wi[2] = b.y; wr[3] = b.z; wi[3] = b.w;
+        } else {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const double2 v = reinterpret_cast<const double2*>(p)[c];
+                wr[c] = (Rt)v.x;
+                wi[c] = (Rt)v.y;
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            acc[c][0] += wr[c] * s.x - wi[c] * s.y;
+            acc[c][1] += wr[c] * s.y + wi[c] * s.x;
+        }
+    } else {
+        Rt w[4];
+        bt_load4<FW, Rt>(p, w);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            acc[c][0] += w[c] * s.x;
+            acc[c][1] += w[c] * s.y;
+        }
+    }
+}
+
+template <class V, class F, class FW = F>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(BT_THREADS, 1)
-k_bt_solve(const Sub* __restrict__ subs, const Level* __restrict__ levels, const F* __restrict__ fac,
+k_bt_solve(const Sub* __restrict__ subs, const Level* __restrict__ levels, const FW* __restrict__ fac,
            const int32_t* __restrict__ cptr, const int32_t* __restrict__ ccol, const F* __restrict__ cval,
            int64_t n_loc, int condensed, const int32_t* __restrict__ ai, const F* __restrict__ av,
            const int32_t* __restrict__ ci, const F* __restrict__ cv, const int32_t* __restrict__ ei,
@@ -279,7 +354,7 @@ k_bt_solve(const Sub* __restrict__ subs, const Level* __restrict__ levels, const
                     unsigned char* dst = slots + (size_t)q * slot_bytes;
                     fence_proxy_async();
                     const int nr = min(R, st.rb - r0);
-                    const unsigned wb = (unsigned)((size_t)nr * ldm * sizeof(F));
+                    const unsigned wb = (unsigned)((size_t)nr * ldm * sizeof(FW));
                     mbar_expect_tx(&full[q], wb);
                     tma_load_1d(dst, fac + Lv.offW + (int64_t)r0 * ldm, wb, &full[q]);
                 }
@@ -421,58 +496,43 @@ k_bt_solve(const Sub* __restrict__ subs, const Level* __restrict__ levels, const
             }
             bt_bar_consumers();
             // (b2) y = W_l^T s over the rows [ra, rb) this rank streams.  Warp w
-            // owns the quad groups g = w, w + NW, ... (8 output quads = 32
-            // outputs each); inside a warp, lane = (row subset rs, quad qq):
-            // the 8 lanes of a subset read 128 contiguous bytes of one W row
-            // (no bank conflicts whatever the row stride) and the 4 subsets
+            // owns the quad groups g = w, w + NW, ... (GQ = 8 output quads
+            // each); inside a warp, lane = (row subset rs, quad qq): the 8
+            // lanes of a subset read 128 contiguous bytes of one W row (no
+            // bank conflicts whatever the row stride) and the NRS = 4 subsets
             // take every 4th row.  The subsets are summed with shuffles, so
             // each output is complete inside one warp: no cross-warp combine.
+            constexpr int GQ = BT_GQ, GMAX = BT_GMAX;
+            constexpr int NRS = 32 / GQ;
             const int nq = ldm / 4;
-            const int ngr = (nq + BT_GQ - 1) / BT_GQ;
-            const int rs = lane >> 3, qq = lane & 7;
-            Rt acc[BT_GMAX][4][2];
+            const int ngr = (nq + GQ - 1) / GQ;
+            const int rs = lane / GQ, qq = lane % GQ;
+            Rt acc[GMAX][4][2];
 #pragma unroll
-            for (int u = 0; u < BT_GMAX; ++u)
+            for (int u = 0; u < GMAX; ++u)
 #pragma unroll
                 for (int c = 0; c < 4; ++c) acc[u][c][0] = acc[u][c][1] = 0;
             for (int r0 = st.ra; r0 < st.rb; r0 += R) {
                 const int q = t % ns;
                 bt_wait<false>(&full[q], (unsigned)((t / ns) & 1), abort, err);
-                const F* Wt = reinterpret_cast<const F*>(slots + (size_t)q * slot_bytes);
+                const FW* Wt = reinterpret_cast<const FW*>(slots + (size_t)q * slot_bytes);
                 const int nr = min(R, st.rb - r0);
 #pragma unroll
-                for (int u = 0; u < BT_GMAX; ++u) {
-                    const int quad = (warp + u * BT_NW) * BT_GQ + qq;
+                for (int u = 0; u < GMAX; ++u) {
+                    const int quad = (warp + u * BT_NW) * GQ + qq;
                     if (warp + u * BT_NW < ngr && quad < nq) {
-                        const F* wc = Wt + 4 * quad;
+                        const FW* wc = Wt + 4 * quad;
                         int jj = rs;
                         // four rows per pass: their loads are independent
-                        for (; jj + 12 < nr; jj += 16) {
+                        for (; jj + 3 * NRS < nr; jj += 4 * NRS) {
                             V sj[4];
-                            Rt w[4][4];
 #pragma unroll
-                            for (int r = 0; r < 4; ++r) {
-                                sj[r] = su[r0 + jj + 4 * r];
-                                bt_load4<F, Rt>(wc + (size_t)(jj + 4 * r) * ldm, w[r]);
-                            }
+                            for (int r = 0; r < 4; ++r) sj[r] = su[r0 + jj + NRS * r];
 #pragma unroll
                             for (int r = 0; r < 4; ++r)
-#pragma unroll
-                                for (int c = 0; c < 4; ++c) {
-                                    acc[u][c][0] += w[r][c] * sj[r].x;
-                                    acc[u][c][1] += w[r][c] * sj[r].y;
-                                }
+                                bt_quad_fma<FW, Rt, V>(wc + (size_t)(jj + NRS * r) * ldm, sj[r], acc[u]);
                         }
-                        for (; jj < nr; jj += 4) {
-                            const V sj = su[r0 + jj];
-                            Rt w[4];
-                            bt_load4<F, Rt>(wc + (size_t)jj * ldm, w);
-#pragma unroll
-                            for (int c = 0; c < 4; ++c) {
-                                acc[u][c][0] += w[c] * sj.x;
-                                acc[u][c][1] += w[c] * sj.y;
-                            }
-                        }
+                        for (; jj < nr; jj += NRS) bt_quad_fma<FW, Rt, V>(wc + (size_t)jj * ldm, su[r0 + jj], acc[u]);
                     }
                 }
                 __syncwarp();
@@ -481,16 +541,15 @@ k_bt_solve(const Sub* __restrict__ subs, const Level* __restrict__ levels, const
             }
             // (b3) sum the 4 row subsets and write each output from the lane of subset 0
 #pragma unroll
-            for (int u = 0; u < BT_GMAX; ++u) {
+            for (int u = 0; u < GMAX; ++u) {
                 if (warp + u * BT_NW >= ngr) break;              // uniform across the warp
 #pragma unroll
                 for (int c = 0; c < 4; ++c)
 #pragma unroll
-                    for (int z = 0; z < 2; ++z) {
-                        acc[u][c][z] += __shfl_xor_sync(0xffffffffu, acc[u][c][z], 8);
-                        acc[u][c][z] += __shfl_xor_sync(0xffffffffu, acc[u][c][z], 16);
-                    }
-                const int quad = (warp + u * BT_NW) * BT_GQ + qq;
+                    for (int z = 0; z < 2; ++z)
+#pragma unroll
+                        for (int o = GQ; o < 32; o <<= 1) acc[u][c][z] += __shfl_xor_sync(0xffffffffu, acc[u][c][z], o);
+                const int quad = (warp + u * BT_NW) * GQ + qq;
                 if (rs == 0 && quad < nq) {
 #pragma unroll
                     for (int c = 0; c < 4; ++c) {

@@ -452,6 +452,16 @@ int thm_work_bytes(const thm_sys* s, int mode, int cls, double* bytes) {
     });
 }
 
+int thm_factor_bytes(const thm_sys* s, int precond, int mode, double* bytes) {
+    return guarded([&]() -> int {
+        THM_REQUIRE(s && bytes, "NULL argument");
+        THM_REQUIRE(precond == THM_PRECOND_BLOCKDIAG || precond == THM_PRECOND_FULL, "unknown preconditioner");
+        const double bv = mode == THM_MODE_MIXED ? 4.0 : 8.0;
+        *bytes = (double)s->m->fac_elems * bv * (precond == THM_PRECOND_FULL ? 2.0 : 1.0);
+        return THM_OK;
+    });
+}
+
 int64_t thm_kernel_launches(void) { return (int64_t)g_launches.load(); }
 
 int thm_profile_enable(unsigned mask) {

@@ -174,7 +174,7 @@ struct thm_mesh {
     // factors, [1] FP32), 0 until the first apply of a system on this mesh.
     // The factor layout (levels, block sizes) is the mesh's, so every system
     // assembled on the mesh reuses the choice.
-    mutable size_t bt_tile[2] = {0, 0};
+    mutable size_t bt_tile[4] = {0, 0, 0, 0};    // [2], [3]: complex factors (full-block preconditioner)
     // level couplings of S as compact CSR lists (columns local to the
     // neighbouring level; slot = position of the value in the SELL arrays)
     std::vector<int32_t> cpl_ptr, cpl_col;
@@ -269,6 +269,11 @@ struct thm_sys {
     bool fac64_ok = false, fac32_ok = false;
     thm::DArr<double> fac64;
     thm::DArr<float> fac32;
+    // complex factors of the full 2x2 block operator (Section 3.2's
+    // alternative preconditioner), lazily built per precision
+    bool facc64_ok = false, facc32_ok = false;
+    thm::DArr<double2> facc64;
+    thm::DArr<float2> facc32;
     // static condensation of order-2 cell bubbles: S = P_EE - P_EI D^{-1} P_IE
     thm::DArr<double> sval64;          // SELL values of S on edge rows/columns (P elsewhere 0)
     thm::DArr<float> sval32;
@@ -296,4 +301,5 @@ namespace thm {
 void build_mesh(thm_mesh* m);
 void assemble(thm_sys* s);
 void ensure_factor(thm_sys* s, bool fp32);
+void ensure_factor_full(thm_sys* s, bool fp32);
 }  // namespace thm

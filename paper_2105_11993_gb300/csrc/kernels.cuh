@@ -130,13 +130,36 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
 constexpr int KT = 256;                       // threads per chunk block
 constexpr int EPT = CHUNK / KT;               // elements per thread
 
+// The last block of a segment to finish (per-segment arrival counter) sums
+// the segment's per-chunk partials in chunk order, so the result does not
+// depend on which block finishes last, and resets the counter for the next
+// launch.  Partials of other blocks are read through L2 (__ldcg).
+__device__ __forceinline__ bool last_block_of_segment(int seg, const int32_t* __restrict__ seg_ch, int* cnt) {
+    __shared__ int s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&cnt[seg], 1) == seg_ch[seg + 1] - seg_ch[seg] - 1;
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        if (threadIdx.x == 0) cnt[seg] = 0;
+    }
+    return s_last != 0;
+}
+
+// h[seg][k] = sum over the segment's chunks of v_k^H w (FP64), k < nk.
+// reset (optional): an int the first block sets to 0 (the active-segment
+// count that the Givens step of the same Arnoldi step accumulates).
 template <class V>
 __global__ void __launch_bounds__(KT) k_chunk_dots(const Chunk* __restrict__ chunks, const V* __restrict__ basis,
                                                    int64_t ld, int nk, const V* __restrict__ w,
                                                    double2* __restrict__ partial, int ldp,
-                                                   const int* __restrict__ act) {
+                                                   const int* __restrict__ act, const int32_t* __restrict__ seg_ch,
+                                                   int* __restrict__ cnt, double2* __restrict__ h, int ldh,
+                                                   int* __restrict__ reset) {
     using R = typename VT<V>::R;
     extern __shared__ double2 sred[];          // [nk][KT/32]
+    if (reset && blockIdx.x == 0 && threadIdx.x == 0) *reset = 0;
     const Chunk c = chunks[blockIdx.x];
     if (act && !act[c.seg]) return;            // converged segment: its partials are not read
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -160,15 +183,15 @@ __global__ void __launch_bounds__(KT) k_chunk_dots(const Chunk* __restrict__ chu
                 ai += v.x * wr[q].y - v.y * wr[q].x;
             }
         }
-        // each thread sums its EPT products in the vector precision; from the
-        // warp reduction on every sum is FP64
-        double dr = (double)ar, di = (double)ai;
+        // a warp sums its 4 * 32 products in the vector precision; from the
+        // cross-warp sum on every sum is FP64 (FP64 shuffles at the warp level
+        // cost 2.7x the kernel time on this part, measured)
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            dr += __shfl_down_sync(0xffffffffu, dr, o);
-            di += __shfl_down_sync(0xffffffffu, di, o);
+            ar += __shfl_down_sync(0xffffffffu, ar, o);
+            ai += __shfl_down_sync(0xffffffffu, ai, o);
         }
-        if (lane == 0) sred[k * (KT / 32) + warp] = make_double2(dr, di);
+        if (lane == 0) sred[k * (KT / 32) + warp] = make_double2((double)ar, (double)ai);
     }
     __syncthreads();
     for (int kk = threadIdx.x; kk < nk; kk += KT) {
@@ -176,19 +199,41 @@ __global__ void __launch_bounds__(KT) k_chunk_dots(const Chunk* __restrict__ chu
         for (int q = 0; q < KT / 32; ++q) s = cadd(s, sred[kk * (KT / 32) + q]);
         partial[(int64_t)blockIdx.x * ldp + kk] = s;
     }
+    if (!last_block_of_segment(c.seg, seg_ch, cnt)) return;
+    for (int kk = threadIdx.x; kk < nk; kk += KT) {
+        double2 s = make_double2(0, 0);
+        for (int cc = seg_ch[c.seg]; cc < seg_ch[c.seg + 1]; ++cc) {
+            const double2 p = __ldcg(&partial[(int64_t)cc * ldp + kk]);
+            s.x += p.x;
+            s.y += p.y;
+        }
+        h[(int64_t)c.seg * ldh + kk] = s;
+    }
 }
 
 // w -= sum_k h[seg][k] basis_k ;  optionally per-chunk ||w||^2
+template <class V>
+__device__ __forceinline__ void chunk_update_body(const Chunk& c, const V* __restrict__ basis, int64_t ld, int nk,
+                                                  const double2* __restrict__ h, int ldh, V* __restrict__ w,
+                                                  double* __restrict__ nrm_part, double2* sh);
+
 template <class V>
 __global__ void __launch_bounds__(KT) k_chunk_update(const Chunk* __restrict__ chunks, const V* __restrict__ basis,
                                                      int64_t ld, int nk, const double2* __restrict__ h, int ldh,
                                                      V* __restrict__ w, double* __restrict__ nrm_part,
                                                      const int* __restrict__ act) {
-    using R = typename VT<V>::R;
     extern __shared__ double2 sh[];            // [nk] coefficients of this segment
-    __shared__ double sw[KT / 32];
     const Chunk c = chunks[blockIdx.x];
     if (act && !act[c.seg]) return;            // converged segment: left as it is
+    chunk_update_body<V>(c, basis, ld, nk, h, ldh, w, nrm_part, sh);
+}
+
+template <class V>
+__device__ __forceinline__ void chunk_update_body(const Chunk& c, const V* __restrict__ basis, int64_t ld, int nk,
+                                                  const double2* __restrict__ h, int ldh, V* __restrict__ w,
+                                                  double* __restrict__ nrm_part, double2* sh) {
+    using R = typename VT<V>::R;
+    __shared__ double sw[KT / 32];
     for (int k = threadIdx.x; k < nk; k += KT) sh[k] = h[(int64_t)c.seg * ldh + k];
     __syncthreads();
     const bool full = c.end - c.begin == CHUNK;

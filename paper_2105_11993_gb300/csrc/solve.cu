@@ -14,17 +14,6 @@
 
 namespace thm {
 
-__global__ void k_seg_reduce(int nseg, const int32_t* __restrict__ seg_ch, const double2* __restrict__ partial,
-                             int ldp, int nk, double2* __restrict__ out, int ldo, int accumulate) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= nseg * nk) return;
-    int s = t / nk, k = t % nk;
-    double2 acc = make_double2(0, 0);
-    for (int c = seg_ch[s]; c < seg_ch[s + 1]; ++c) acc = cadd(acc, partial[(int64_t)c * ldp + k]);
-    if (accumulate) acc = cadd(acc, out[(int64_t)s * ldo + k]);
-    out[(int64_t)s * ldo + k] = acc;
-}
-
 __global__ void k_seg_reduce_real(int nseg, const int32_t* __restrict__ seg_ch, const double* __restrict__ part,
                                   double* __restrict__ out) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -35,25 +24,18 @@ __global__ void k_seg_reduce_real(int nseg, const int32_t* __restrict__ seg_ch, 
 }
 
 // Start of a cycle: beta = ||r||, activity, g = (beta, 0, ...).  On the first
-// cycle the per-segment target is tol * ||b_s|| (x = 0 there, so r = b), or
-// an absolute floor when that is larger: floor_fac * ||f_s|| with f_s the
-// segment's original right-hand side (fnrm2, optional), so that a refinement
-// cycle stops once the solve it refines is accurate enough.
+// cycle the per-segment target is tol * ||b_s|| (x = 0 there, so r = b).
 // A segment whose true residual did not fall below half of its value at the
 // previous cycle start has reached the accuracy its arithmetic allows
 // (FP32 iterates: about cond(T_i) * 6e-8) and stops as well.
 __global__ void k_cycle_start(int nseg, int m, const double* __restrict__ nrm2, double tol, int first,
-                              const double* __restrict__ fnrm2, double floor_fac,
                               double* __restrict__ target, double* __restrict__ beta, int* __restrict__ active,
                               int* __restrict__ kused, double2* __restrict__ gv, int* __restrict__ nact,
                               double* __restrict__ prev) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= nseg) return;
     double b = sqrt(nrm2[s]);
-    if (first) {
-        target[s] = fnrm2 ? fmax(tol * b, floor_fac * sqrt(fnrm2[s])) : tol * b;
-        prev[s] = INFINITY;
-    }
+    if (first) { target[s] = tol * b; prev[s] = INFINITY; }
     int a = b > target[s] && b > 0 && b < 0.5 * prev[s];
     prev[s] = b;
     active[s] = a;
@@ -66,35 +48,42 @@ __global__ void k_cycle_start(int nseg, int m, const double* __restrict__ nrm2, 
 // Column j of the Hessenberg matrix (h1 + h2 from the two Gram-Schmidt passes,
 // ||w|| below the diagonal), previous Givens rotations, a new rotation, the
 // updated residual estimate |g_{j+1}| and the per-segment convergence flag.
-__global__ void __launch_bounds__(32) k_givens(int nseg, int j, int m, const double2* __restrict__ h1,
-                                               const double2* __restrict__ h2, int ldh,
-                                               const double* __restrict__ nrm2, double2* __restrict__ Rm,
-                                               double* __restrict__ cs, double2* __restrict__ sn,
-                                               double2* __restrict__ gv, const double* __restrict__ target,
-                                               int* __restrict__ active, int* __restrict__ kused,
-                                               double* __restrict__ beta, int* __restrict__ nact,
-                                               int* __restrict__ flag) {
-    // one warp per segment: the column and the rotations are staged in shared
-    // memory in parallel; the rotations themselves run on lane 0
-    extern __shared__ unsigned char gsm[];
-    double2* col = reinterpret_cast<double2*>(gsm);          // [j+1]
-    double2* sg = col + (j + 1);                             // [j]
-    double* c = reinterpret_cast<double*>(sg + j);           // [j]
-    const int s = blockIdx.x;
-    const int lane = threadIdx.x;
-    if (!active[s]) {
-        if (lane == 0) beta[s] = 0.0;
-        return;
-    }
-    for (int i = lane; i <= j; i += 32) col[i] = cadd(h1[(int64_t)s * ldh + i], h2[(int64_t)s * ldh + i]);
-    for (int i = lane; i < j; i += 32) { c[i] = cs[(int64_t)s * m + i]; sg[i] = sn[(int64_t)s * m + i]; }
+struct GivensArgs {
+    int j, m, ldh;
+    const double2* h1;
+    const double2* h2;
+    double2* Rm;
+    double* cs;
+    double2* sn;
+    double2* gv;
+    const double* target;
+    int* active;
+    int* kused;
+    double* beta;
+    int* nact;                 // active segments after this step (the first dots pass of the step zeroes it)
+    int* flag;                 // breakdown (non-finite norm)
+    double2* gmon;             // g_{j+1} of segment 0 for the host monitor (single-segment solves), or null
+    const int32_t* seg_ch;
+    int* cnt;                  // per-segment arrival counters of the last-block reduction
+};
+
+// One warp: the column and the rotations are staged in shared memory by all
+// lanes; the rotations themselves run on lane 0.  hn2 = ||w||^2 of segment s.
+__device__ void givens_warp(const GivensArgs& ga, int s, double hn2, unsigned char* scratch) {
+    const int j = ga.j, m = ga.m;
+    double2* col = reinterpret_cast<double2*>(scratch);      // [j+1]
+    double2* sg = col + (j + 1);                              // [j]
+    double* c = reinterpret_cast<double*>(sg + j);            // [j]
+    const int lane = threadIdx.x & 31;
+    for (int i = lane; i <= j; i += 32) col[i] = cadd(ga.h1[(int64_t)s * ga.ldh + i], ga.h2[(int64_t)s * ga.ldh + i]);
+    for (int i = lane; i < j; i += 32) { c[i] = ga.cs[(int64_t)s * m + i]; sg[i] = ga.sn[(int64_t)s * m + i]; }
     __syncwarp();
     if (lane == 0) {
-        const double hn = sqrt(nrm2[s]);
+        const double hn = sqrt(hn2);
         if (!isfinite(hn)) {
-            atomicExch(flag, 1);
-            active[s] = 0;
-            beta[s] = 0.0;
+            atomicExch(ga.flag, 1);
+            ga.active[s] = 0;
+            ga.beta[s] = 0.0;
         } else {
             for (int i = 0; i < j; ++i) {
                 double2 a = col[i], b = col[i + 1];
@@ -113,23 +102,47 @@ __global__ void __launch_bounds__(32) k_givens(int nseg, int j, int m, const dou
                 cj = am / d;
                 sj = make_double2(a.x / am * hn / d, a.y / am * hn / d);      // (a/|a|) conj(hn)/d
             }
-            cs[(int64_t)s * m + j] = cj;
-            sn[(int64_t)s * m + j] = sj;
+            ga.cs[(int64_t)s * m + j] = cj;
+            ga.sn[(int64_t)s * m + j] = sj;
             col[j] = make_double2(cj * a.x + sj.x * hn, cj * a.y + sj.y * hn);
-            double2* g = gv + (int64_t)s * (m + 1);
+            double2* g = ga.gv + (int64_t)s * (m + 1);
             double2 gj = g[j];
             g[j + 1] = make_double2(-(sj.x * gj.x + sj.y * gj.y), -(sj.x * gj.y - sj.y * gj.x));   // -conj(s) g_j
             g[j] = make_double2(cj * gj.x, cj * gj.y);
-            kused[s] = j + 1;
-            beta[s] = hn;
+            if (ga.gmon && s == 0) *ga.gmon = g[j + 1];
+            ga.kused[s] = j + 1;
+            ga.beta[s] = hn;
             double res = hypot(g[j + 1].x, g[j + 1].y);
-            if (res <= target[s] || hn == 0.0) active[s] = 0;
-            else atomicAdd(nact, 1);
+            if (res <= ga.target[s] || hn == 0.0) ga.active[s] = 0;
+            else atomicAdd(ga.nact, 1);
         }
     }
     __syncwarp();
-    double2* out = Rm + ((int64_t)s * m + j) * m;             // column j, rows 0..j
+    double2* out = ga.Rm + ((int64_t)s * m + j) * m;          // column j, rows 0..j
     for (int i = lane; i <= j; i += 32) out[i] = col[i];
+}
+
+// Second Gram-Schmidt update w -= V h2 with the per-chunk ||w||^2; the last
+// block of each segment sums the segment's norm partials in chunk order and
+// runs that segment's Givens step (so no separate reduction or Givens launch).
+template <class V>
+__global__ void __launch_bounds__(KT) k_update_givens(const Chunk* __restrict__ chunks, const V* __restrict__ basis,
+                                                      int64_t ld, int nk, V* __restrict__ w,
+                                                      double* __restrict__ nrm_part, const int* __restrict__ act,
+                                                      GivensArgs ga) {
+    extern __shared__ double2 sh[];            // [nk] coefficients, then the Givens scratch
+    __shared__ double s_hn2;
+    const Chunk c = chunks[blockIdx.x];
+    if (act && !act[c.seg]) return;
+    chunk_update_body<V>(c, basis, ld, nk, ga.h2, ga.ldh, w, nrm_part, sh);
+    if (!last_block_of_segment(c.seg, ga.seg_ch, ga.cnt)) return;
+    if (threadIdx.x == 0) {
+        double t = 0;
+        for (int cc = ga.seg_ch[c.seg]; cc < ga.seg_ch[c.seg + 1]; ++cc) t += __ldcg(&nrm_part[cc]);
+        s_hn2 = t;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) givens_warp(ga, c.seg, s_hn2, reinterpret_cast<unsigned char*>(sh));
 }
 
 // y = R^{-1} g (upper triangular, k = kused[s])
@@ -300,15 +313,20 @@ struct Krylov {
     bool flexible = false;
     DArr<double2> partial, h1, h2, Rm, sn, gv, y;
     DArr<double> nrm_part, nrm, cs, beta, target, prev;
-    DArr<int> active, kused, nact, flag;
+    DArr<int> active, kused, cnt;
+    // monitor record of the latest Arnoldi step, 32 bytes: the active-segment
+    // count and the breakdown flag (two ints), then g_{j+1} of segment 0
+    DArr<double2> mon;
+    int* nact = nullptr;
+    int* flag = nullptr;
+    double2* gmon = nullptr;
     int* h_pinned = nullptr;
     std::vector<int> h_kused;
-    // asynchronous convergence monitor: per Arnoldi step the active-segment
-    // count and the breakdown flag land in a pinned ring; the host reads them
-    // a few steps behind the GPU instead of blocking every step
+    // asynchronous convergence monitor: per Arnoldi step the monitor record
+    // lands in a pinned ring (one copy); the host reads it a few steps behind
+    // the GPU instead of blocking every step
     static constexpr int RING = 4;
-    int* h_ring = nullptr;
-    double2* h_gring = nullptr;      // g_{j+1} of segment 0 (residual estimate)
+    double2* h_ring = nullptr;       // [RING][2] copies of the monitor record
     double h_beta0 = 0;              // ||r_0|| of segment 0 at the first cycle
     double last_rel = 1.0;           // latest residual estimate of segment 0 seen by the host, relative
     const int* step_mask = nullptr;  // device per-segment activity while an Arnoldi step applies A and M
@@ -317,7 +335,6 @@ struct Krylov {
     ~Krylov() {
         if (h_pinned) cudaFreeHost(h_pinned);
         if (h_ring) cudaFreeHost(h_ring);
-        if (h_gring) cudaFreeHost(h_gring);
         for (auto& e : ring_ev)
             if (e) cudaEventDestroy(e);
     }
@@ -342,11 +359,17 @@ struct Krylov {
         sn.alloc((size_t)nseg * m); cs.alloc((size_t)nseg * m);
         gv.alloc((size_t)nseg * (m + 1)); y.alloc((size_t)nseg * m);
         nrm_part.alloc(nch); nrm.alloc(nseg); beta.alloc(nseg); target.alloc(nseg); prev.alloc(nseg);
-        active.alloc(nseg); kused.alloc(nseg); nact.alloc(1); flag.alloc(1);
+        active.alloc(nseg); kused.alloc(nseg);
+        cnt.alloc(nseg);
+        cnt.zero(0);
+        mon.alloc(2);
+        mon.zero(0);
+        nact = reinterpret_cast<int*>(mon.p);
+        flag = nact + 1;
+        gmon = mon.p + 1;
         if (!h_pinned) THM_CUDA(cudaMallocHost(&h_pinned, 2 * sizeof(int)));
         if (!h_ring) {
-            THM_CUDA(cudaMallocHost(&h_ring, 2 * RING * sizeof(int)));
-            THM_CUDA(cudaMallocHost(&h_gring, RING * sizeof(double2)));
+            THM_CUDA(cudaMallocHost(&h_ring, 2 * RING * sizeof(double2)));
             for (auto& e : ring_ev) THM_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         }
         // the kernels are shared by every Krylov instance of this vector
@@ -358,6 +381,8 @@ struct Krylov {
             THM_CUDA(cudaFuncSetAttribute(k_chunk_dots<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dots_smem));
             THM_CUDA(cudaFuncSetAttribute(k_chunk_update<V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)((m + 1) * sizeof(double2))));
+            THM_CUDA(cudaFuncSetAttribute(k_update_givens<V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)givens_smem(m)));
             dots_attr = dots_smem;
         }
         THM_CUDA(cudaDeviceSynchronize());
@@ -368,22 +393,27 @@ struct Krylov {
         THM_LAUNCH(THM_K_KRYLOV, st, k_seg_reduce_real<<<nblk(nseg), 256, 0, st>>>(nseg, seg_ch.p, nrm_part.p, nrm.p));
     }
 
+    // dynamic shared memory of k_update_givens at step j <= m-1: the nk = j+1
+    // coefficients, or the Givens scratch (column, rotations)
+    static size_t givens_smem(int mm) {
+        return std::max((size_t)mm * sizeof(double2),
+                        (size_t)mm * sizeof(double2) + (size_t)mm * (sizeof(double2) + sizeof(double)));
+    }
+
     int read_nact(cudaStream_t st) {
-        THM_CUDA(cudaMemcpyAsync(h_pinned, nact.p, sizeof(int), cudaMemcpyDeviceToHost, st));
-        THM_CUDA(cudaMemcpyAsync(h_pinned + 1, flag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+        THM_CUDA(cudaMemcpyAsync(h_pinned, nact, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
         THM_CUDA(cudaStreamSynchronize(st));
         return h_pinned[0];
     }
 
     // Solve A x = b for all segments (x in/out).  A(in, out); M(in, out) or empty.
     KStats solve(const std::function<void(const V*, V*)>& A, const std::function<void(const V*, V*)>& M,
-                 const V* b, V* x, bool x_zero, double tol, int maxit, cudaStream_t st, bool single_cycle = false,
-                 const double* fnrm2 = nullptr, double floor_fac = 0.0) {
+                 const V* b, V* x, bool x_zero, double tol, int maxit, cudaStream_t st, bool single_cycle = false) {
         KStats ks;
         std::vector<int64_t> per_seg(nseg, 0);
         int total = 0;
         bool first = true;
-        flag.zero(st);
+        THM_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), st));
         if (x_zero) {
             THM_CUDA(cudaMemsetAsync(x, 0, n * sizeof(V), st));
             THM_CUDA(cudaMemcpyAsync(r.p, b, n * sizeof(V), cudaMemcpyDeviceToDevice, st));
@@ -393,10 +423,9 @@ struct Krylov {
         }
         while (true) {
             seg_norm2(r.p, st);
-            nact.zero(st);
-            THM_LAUNCH(THM_K_KRYLOV, st, k_cycle_start<<<nblk(nseg), 256, 0, st>>>(nseg, m, nrm.p, tol, first ? 1 : 0, fnrm2,
-                                                      floor_fac, target.p, beta.p, active.p, kused.p, gv.p,
-                                                      nact.p, prev.p));
+            THM_CUDA(cudaMemsetAsync(nact, 0, sizeof(int), st));
+            THM_LAUNCH(THM_K_KRYLOV, st, k_cycle_start<<<nblk(nseg), 256, 0, st>>>(nseg, m, nrm.p, tol, first ? 1 : 0,
+                                                      target.p, beta.p, active.p, kused.p, gv.p, nact, prev.p));
             if (first && nseg == 1) {
                 double b0 = 0;
                 THM_CUDA(cudaMemcpyAsync(&b0, beta.p, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -421,25 +450,25 @@ struct Krylov {
                 step_mask = nullptr;
                 const int nk = j + 1;
                 size_t sm = (size_t)nk * (KT / 32) * sizeof(double2);
-                THM_LAUNCH(THM_K_DOTS, st, k_chunk_dots<V><<<nch, KT, sm, st>>>(d_chunks, basis.p, n, nk, w.p, partial.p, m + 1, active.p));
-                THM_LAUNCH(THM_K_KRYLOV, st, k_seg_reduce<<<nblk((int64_t)nseg * nk), 256, 0, st>>>(nseg, seg_ch.p, partial.p, m + 1, nk, h1.p, m + 1, 0));
+                // CGS2: h1 = V^H w, w -= V h1, h2 = V^H w, w -= V h2 (the dot kernels
+                // reduce their segments themselves); the second update also forms
+                // ||w|| and the Givens step of each segment
+                THM_LAUNCH(THM_K_DOTS, st, k_chunk_dots<V><<<nch, KT, sm, st>>>(d_chunks, basis.p, n, nk, w.p, partial.p, m + 1,
+                                                                               active.p, seg_ch.p, cnt.p, h1.p, m + 1, nact));
                 THM_LAUNCH(THM_K_UPDATE, st, k_chunk_update<V><<<nch, KT, nk * sizeof(double2), st>>>(d_chunks, basis.p, n, nk, h1.p, m + 1, w.p, nullptr, active.p));
-                THM_LAUNCH(THM_K_DOTS, st, k_chunk_dots<V><<<nch, KT, sm, st>>>(d_chunks, basis.p, n, nk, w.p, partial.p, m + 1, active.p));
-                THM_LAUNCH(THM_K_KRYLOV, st, k_seg_reduce<<<nblk((int64_t)nseg * nk), 256, 0, st>>>(nseg, seg_ch.p, partial.p, m + 1, nk, h2.p, m + 1, 0));
-                THM_LAUNCH(THM_K_UPDATE, st, k_chunk_update<V><<<nch, KT, nk * sizeof(double2), st>>>(d_chunks, basis.p, n, nk, h2.p, m + 1, w.p, nrm_part.p, active.p));
-                THM_LAUNCH(THM_K_KRYLOV, st, k_seg_reduce_real<<<nblk(nseg), 256, 0, st>>>(nseg, seg_ch.p, nrm_part.p, nrm.p));
-                nact.zero(st);
-                const size_t gsm = (size_t)(j + 1) * sizeof(double2) + (size_t)j * (sizeof(double2) + sizeof(double));
-                THM_LAUNCH(THM_K_KRYLOV, st, k_givens<<<nseg, 32, gsm, st>>>(nseg, j, m, h1.p, h2.p, m + 1, nrm.p, Rm.p, cs.p, sn.p, gv.p,
-                                                     target.p, active.p, kused.p, beta.p, nact.p, flag.p));
+                THM_LAUNCH(THM_K_DOTS, st, k_chunk_dots<V><<<nch, KT, sm, st>>>(d_chunks, basis.p, n, nk, w.p, partial.p, m + 1,
+                                                                               active.p, seg_ch.p, cnt.p, h2.p, m + 1, nullptr));
+                GivensArgs ga{j, m, m + 1, h1.p, h2.p, Rm.p, cs.p, sn.p, gv.p, target.p, active.p, kused.p, beta.p,
+                              nact, flag, nseg == 1 ? gmon : nullptr, seg_ch.p, cnt.p};
+                const size_t gsm = std::max((size_t)nk * sizeof(double2),
+                                            (size_t)(j + 1) * sizeof(double2) + (size_t)j * (sizeof(double2) + sizeof(double)));
+                THM_LAUNCH(THM_K_UPDATE, st, k_update_givens<V><<<nch, KT, gsm, st>>>(d_chunks, basis.p, n, nk, w.p, nrm_part.p,
+                                                                                      active.p, ga));
                 THM_LAUNCH(THM_K_KRYLOV, st, k_chunk_scale<V><<<nch, 256, 0, st>>>(d_chunks, w.p, beta.p, basis.p + (int64_t)(j + 1) * n, active.p));
                 ++total;
-                // monitor: copy (active count, breakdown flag) of step j into the ring
+                // monitor: one copy of the step's record into the ring
                 const int slot = j % RING;
-                THM_CUDA(cudaMemcpyAsync(h_ring + 2 * slot, nact.p, sizeof(int), cudaMemcpyDeviceToHost, st));
-                THM_CUDA(cudaMemcpyAsync(h_ring + 2 * slot + 1, flag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
-                if (nseg == 1)
-                    THM_CUDA(cudaMemcpyAsync(h_gring + slot, gv.p + j + 1, sizeof(double2), cudaMemcpyDeviceToHost, st));
+                THM_CUDA(cudaMemcpyAsync(h_ring + 2 * slot, mon.p, 2 * sizeof(double2), cudaMemcpyDeviceToHost, st));
                 THM_CUDA(cudaEventRecord(ring_ev[slot], st));
                 // read every finished step; block only when the ring is full
                 bool stop = false;
@@ -448,9 +477,13 @@ struct Krylov {
                     cudaError_t q = (j - checked >= RING - 1) ? cudaEventSynchronize(ring_ev[rs_]) : cudaEventQuery(ring_ev[rs_]);
                     if (q == cudaErrorNotReady) break;
                     THM_CUDA(q);
-                    if (h_ring[2 * rs_ + 1]) { ks.status = THM_EBREAKDOWN; stop = true; break; }
-                    if (nseg == 1 && h_beta0 > 0) last_rel = std::hypot(h_gring[rs_].x, h_gring[rs_].y) / h_beta0;
-                    if (h_ring[2 * rs_] == 0) { stop = true; break; }
+                    const int* rec = reinterpret_cast<const int*>(h_ring + 2 * rs_);
+                    if (rec[1]) { ks.status = THM_EBREAKDOWN; stop = true; break; }
+                    if (nseg == 1 && h_beta0 > 0) {
+                        const double2 g1 = h_ring[2 * rs_ + 1];
+                        last_rel = std::hypot(g1.x, g1.y) / h_beta0;
+                    }
+                    if (rec[0] == 0) { stop = true; break; }
                     ++checked;
                 }
                 if (stop) break;
@@ -458,7 +491,8 @@ struct Krylov {
             // drain the monitor: any later step may still report breakdown
             THM_CUDA(cudaStreamSynchronize(st));
             for (; checked < j && ks.status != THM_EBREAKDOWN; ++checked)
-                if (h_ring[2 * (checked % RING) + 1]) ks.status = THM_EBREAKDOWN;            THM_CUDA(cudaGetLastError());
+                if (reinterpret_cast<const int*>(h_ring + 2 * (checked % RING))[1]) ks.status = THM_EBREAKDOWN;
+            THM_CUDA(cudaGetLastError());
             // x += M (V y)
             THM_LAUNCH(THM_K_KRYLOV, st, k_backsolve<<<nblk(nseg, 64), 64, 0, st>>>(nseg, m, Rm.p, gv.p, kused.p, y.p));
             if (flexible && M) {
@@ -580,6 +614,8 @@ SolveCfg make_cfg(const thm_solve_opts* o) {
     c.relax = o ? o->relax : 0;
     c.outer_method = o ? o->outer_method : THM_OUTER_GMRES;
     THM_REQUIRE(c.outer_method == THM_OUTER_GMRES || c.outer_method == THM_OUTER_JACOBI, "unknown outer method");
+    c.precond = o ? o->precond : THM_PRECOND_BLOCKDIAG;
+    THM_REQUIRE(c.precond == THM_PRECOND_BLOCKDIAG || c.precond == THM_PRECOND_FULL, "unknown preconditioner");
     if (const char* e = getenv("THM_CYCLE_TOL")) c.cycle_tol = atof(e);
     c.outer_tol = (o && o->outer_tol > 0) ? o->outer_tol : 1e-9;
     return c;
@@ -616,11 +652,11 @@ struct BtCfg {
     size_t slot = 0, cslot = 0, smem = 0;
 };
 
-template <class V, class F>
+template <class V, class F, class FW = F>
 static BtCfg bt_config(const thm_mesh* m, size_t target) {
     BtCfg c;
     const size_t cap = 227 * 1024 - 256;
-    const size_t row_bytes = (size_t)bt_r4(m->max_m) * sizeof(F);
+    const size_t row_bytes = (size_t)bt_r4(m->max_m) * sizeof(FW);
     const size_t cfull = bt_r16((size_t)(m->max_m + 1) * 4) + bt_r16((size_t)m->max_cnz * 4) +
                          bt_r16((size_t)m->max_cnz * sizeof(F));
     // coupling blocks larger than 12 KB are read from global memory in place
@@ -647,36 +683,38 @@ static BtCfg bt_config(const thm_mesh* m, size_t target) {
     return c;
 }
 
-template <class V, class F>
-static void bt_launch(const thm_sys* s, const BtCfg& c, const F* fac, const F* cval, const int32_t* ai, const F* av,
+template <class V, class F, class FW = F>
+static void bt_launch(const thm_sys* s, const BtCfg& c, const FW* fac, const F* cval, const int32_t* ai, const F* av,
                       const int32_t* ci, const F* cv, const int32_t* ei, const F* ev, const V* x, V* y,
                       const int* act = nullptr) {
     const thm_mesh* m = s->m;
     static size_t attr = 0;
     if (c.smem > 48 * 1024 && c.smem > attr) {
-        THM_CUDA(cudaFuncSetAttribute(k_bt_solve<V, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem));
+        THM_CUDA(cudaFuncSetAttribute(k_bt_solve<V, F, FW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem));
         attr = c.smem;
     }
+    // the work counter follows the Eq. 7 (real-factor) applies only
+    unsigned long long* work =
+        (s->bt_work.p && !BtCplx<FW>::value) ? s->bt_work.p + (sizeof(F) == 4 ? 2 : 0) : nullptr;
     THM_LAUNCH(THM_K_PINV, s->st,
-               k_bt_solve<V, F><<<dim3(2, m->n_sub), BT_THREADS, c.smem, s->st>>>(
+               (k_bt_solve<V, F, FW><<<dim3(2, m->n_sub), BT_THREADS, c.smem, s->st>>>(
                    m->d_subs.p, m->d_levels.p, fac, m->d_cpl_ptr.p, m->d_cpl_col.p, cval, m->n_loc,
                    m->order == 2 ? 1 : 0, ai, av, ci, cv, ei, ev, c.rows, c.ns, (int)c.slot, (int)c.cslot, c.cglob,
-                   m->max_lev, c.nvec, m->max_m, s->dev_err.p, act, m->d_bt_welem.p,
-                   s->bt_work.p ? s->bt_work.p + (sizeof(F) == 4 ? 2 : 0) : nullptr, x, y));
+                   m->max_lev, c.nvec, m->max_m, s->dev_err.p, act, m->d_bt_welem.p, work, x, y)));
 }
 
 // The tile size is tuned once per mesh and factor precision: on the first
 // apply of a system every candidate runs on the caller's vectors (the result
 // is the same each time) and the fastest of two timed launches wins; later
 // systems on the same mesh reuse it.  THM_BT_TILE_BYTES fixes it instead.
-template <class V, class F>
-static void apply_Pinv(const thm_sys* s, const F* fac, const F* cval, const int32_t* ai, const F* av,
+template <class V, class F, class FW = F>
+static void apply_Pinv(const thm_sys* s, const FW* fac, const F* cval, const int32_t* ai, const F* av,
                        const int32_t* ci, const F* cv, const int32_t* ei, const F* ev, const V* x, V* y,
                        const int* act = nullptr) {
     const thm_mesh* m = s->m;
     THM_REQUIRE(m->max_m <= BT_MAX_M, "level block larger than the block-solve kernel supports (" +
                                           std::to_string(m->max_m) + " > " + std::to_string(BT_MAX_M) + ")");
-    size_t& tile = m->bt_tile[sizeof(F) == 4 ? 1 : 0];
+    size_t& tile = m->bt_tile[(sizeof(F) == 4 ? 1 : 0) + (BtCplx<FW>::value ? 2 : 0)];
     if (!s->bt_work.p) {
         s->bt_work.alloc(4);
         s->bt_work.zero(s->st);
@@ -692,11 +730,11 @@ static void apply_Pinv(const thm_sys* s, const F* fac, const F* cval, const int3
             float best = 1e30f;
             int best_rows = -1;
             for (size_t t : cand) {
-                const BtCfg c = bt_config<V, F>(m, t);
+                const BtCfg c = bt_config<V, F, FW>(m, t);
                 if (c.rows == best_rows) continue;                // same tiles as a faster-or-equal candidate
-                bt_launch<V, F>(s, c, fac, cval, ai, av, ci, cv, ei, ev, x, y);      // warm
+                bt_launch<V, F, FW>(s, c, fac, cval, ai, av, ci, cv, ei, ev, x, y);      // warm
                 THM_CUDA(cudaEventRecord(e0, s->st));
-                for (int r = 0; r < 2; ++r) bt_launch<V, F>(s, c, fac, cval, ai, av, ci, cv, ei, ev, x, y);
+                for (int r = 0; r < 2; ++r) bt_launch<V, F, FW>(s, c, fac, cval, ai, av, ci, cv, ei, ev, x, y);
                 THM_CUDA(cudaEventRecord(e1, s->st));
                 THM_CUDA(cudaEventSynchronize(e1));
                 float ms = 0;
@@ -707,7 +745,19 @@ static void apply_Pinv(const thm_sys* s, const F* fac, const F* cval, const int3
             cudaEventDestroy(e1);
         }
     }
-    bt_launch<V, F>(s, bt_config<V, F>(m, tile), fac, cval, ai, av, ci, cv, ei, ev, x, y, act);
+    bt_launch<V, F, FW>(s, bt_config<V, F, FW>(m, tile), fac, cval, ai, av, ci, cv, ei, ev, x, y, act);
+}
+
+// The full 2x2 block preconditioner (Section 3.2's alternative): T_i^{-1} from
+// the complex factors.
+template <class V>
+static void apply_Tinv_mode(const thm_sys* s, bool f32, const V* x, V* y, const int* act = nullptr) {
+    if (f32)
+        apply_Pinv<V, float, float2>(s, s->facc32.p, s->cpl32.p, s->tab_ai.p, s->tab_av32.p, s->tab_ci.p,
+                                     s->tab_cv32.p, s->tab_ei.p, s->tab_ev32.p, x, y, act);
+    else
+        apply_Pinv<V, double, double2>(s, s->facc64.p, s->cpl64.p, s->tab_ai.p, s->tab_av64.p, s->tab_ci.p,
+                                       s->tab_cv64.p, s->tab_ei.p, s->tab_ev64.p, x, y, act);
 }
 
 template <class V>
@@ -738,7 +788,10 @@ static void subdomain_solves(thm_sys* s, const SolveCfg& c, const double2* b, do
         auto A = [&](const double2* in, double2* out) {
             apply_T<double2, double>(s, s->val64.p, s->bg64.p, s->bs64.p, 1, in, out, w->in64.step_mask);
         };
-        auto M = [&](const double2* in, double2* out) { apply_Pinv_mode<double2>(s, false, in, out, w->in64.step_mask); };
+        auto M = [&](const double2* in, double2* out) {
+            if (c.precond == THM_PRECOND_FULL) apply_Tinv_mode<double2>(s, false, in, out, w->in64.step_mask);
+            else apply_Pinv_mode<double2>(s, false, in, out, w->in64.step_mask);
+        };
         add(rs, w->in64.solve(A, M, b, x, true, c.inner_tol, c.inner_maxit, st));
     } else {
         // Mixed: GMRES-IR.  Each cycle solves T d = r in FP32 (FP32 operator,
@@ -749,7 +802,10 @@ static void subdomain_solves(thm_sys* s, const SolveCfg& c, const double2* b, do
         auto A = [&](const float2* in, float2* out) {
             apply_T<float2, float>(s, s->val32.p, s->bg32.p, s->bs32.p, 1, in, out, w->in32.step_mask);
         };
-        auto M = [&](const float2* in, float2* out) { apply_Pinv_mode<float2>(s, true, in, out, w->in32.step_mask); };
+        auto M = [&](const float2* in, float2* out) {
+            if (c.precond == THM_PRECOND_FULL) apply_Tinv_mode<float2>(s, true, in, out, w->in32.step_mask);
+            else apply_Pinv_mode<float2>(s, true, in, out, w->in32.step_mask);
+        };
         Krylov<float2>& K = w->in32;
         THM_CUDA(cudaMemsetAsync(x, 0, m->n_loc * sizeof(double2), st));
         THM_CUDA(cudaMemcpyAsync(w->r64.p, b, m->n_loc * sizeof(double2), cudaMemcpyDeviceToDevice, st));
@@ -767,11 +823,13 @@ static void subdomain_solves(thm_sys* s, const SolveCfg& c, const double2* b, do
             std::vector<int> na;
             w->nact_ir.download(na, st);
             if (na[0] == 0) break;
-            // the cycle stops at cycle_tol (the FP32 limit) relative to its own
-            // right-hand side, or once the refined solve meets a quarter of
-            // the subdomain tolerance, whichever comes first
-            KStats ks = K.solve(A, M, w->b32.p, w->x32.p, true, c.cycle_tol, c.m_in, st, true, w->bn2.p,
-                                0.25 * c.inner_tol);
+            // each cycle runs to cycle_tol relative to its own right-hand side
+            // (the FP32 limit).  It stops there even when the refined solve
+            // needs less: with the relaxed interface tolerances the margin is
+            // what keeps the interface GMRES from stalling (a floor at a
+            // quarter of the subdomain tolerance took 937 interface steps
+            // against 362 on the 256x256 order-2 workload, measured)
+            KStats ks = K.solve(A, M, w->b32.p, w->x32.p, true, c.cycle_tol, c.m_in, st, true);
             ks.status = THM_OK;      // the refinement loop owns convergence
             add(rs, ks);
             THM_LAUNCH(THM_K_DDM, st, k_ir_update<<<nblk(m->n_loc), 256, 0, st>>>(m->n_loc, w->x32.p, x));
@@ -989,6 +1047,7 @@ void fill_stats(const RunStats& rs, double rel, double sec, thm_stats* stats) {
 
 void prepare(thm_sys* s, const SolveCfg& c) {
     ensure_factor(s, c.fp32);
+    if (c.precond == THM_PRECOND_FULL) ensure_factor_full(s, c.fp32);
     ensure_work(s, c.fp32, c.m_in, c.m_out);
 }
 
@@ -1007,10 +1066,15 @@ int solve(thm_sys* s, const thm_solve_opts* opts, double2* u, thm_stats* stats) 
 // ---- diagnostics -----------------------------------------------------------
 void apply_local(thm_sys* s, int op, int mode, const double2* x, double2* y) {
     bool f32 = mode == THM_MODE_MIXED;
-    THM_REQUIRE(op == THM_OP_T || op == THM_OP_PINV || op == THM_OP_KLOC, "unknown op");
-    if (op == THM_OP_PINV) {
+    THM_REQUIRE(op == THM_OP_T || op == THM_OP_PINV || op == THM_OP_KLOC || op == THM_OP_TINV, "unknown op");
+    if (op == THM_OP_PINV || op == THM_OP_TINV) {
         ensure_factor(s, f32);
-        apply_Pinv_mode<double2>(s, f32, x, y);
+        if (op == THM_OP_TINV) {
+            ensure_factor_full(s, f32);
+            apply_Tinv_mode<double2>(s, f32, x, y);
+        } else {
+            apply_Pinv_mode<double2>(s, f32, x, y);
+        }
         THM_CUDA(cudaStreamSynchronize(s->st));
         check_device_error(s);
     } else {

@@ -12,6 +12,7 @@ struct SolveCfg {
     int m_in, m_out, inner_maxit, outer_maxit, max_refine;
     int relax;
     int outer_method;          // THM_OUTER_GMRES / THM_OUTER_JACOBI
+    int precond;               // THM_PRECOND_BLOCKDIAG / THM_PRECOND_FULL
 };
 
 struct RunStats {

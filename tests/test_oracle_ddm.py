@@ -152,3 +152,21 @@ def test_dirichlet_like_interface_conditions_do_not_converge_for_large_omega():
     _, idl = ddm.solve(ddm.setup(P, transmission=100.0), outer="jacobi", outer_tol=1e-8, outer_maxiter=300)
     assert ij["hist"][-1] < 1e-8
     assert idl["hist"][-1] > 1e-2
+
+
+def test_full_block_preconditioner_variant():
+    """Section 3.2's alternative preconditioner, the full 2x2 block operator.
+    With the signs of Eq. 3 its exact inverse is T_ff^{-1}: GMRES stops after
+    one step in every subdomain and the DDM reaches the monolithic solution.
+    With the off-diagonal signs as printed ([[P, -B], [-B, P]]) it is a
+    different real symmetric matrix: GMRES still reaches the same solution,
+    in more steps than one."""
+    P = W.square_problem(8, 2, 2, 11.0, mu_inv=W.mu_inv_lognormal(64, 0.3, "fb"))
+    D = ddm.setup(P)
+    u0 = fem.solve_monolithic(D.sys)
+    uf, info_f = ddm.solve(D, inner="full_block", inner_tol=1e-12, outer_tol=1e-12)
+    assert np.linalg.norm(uf - u0) <= 1e-10 * np.linalg.norm(u0)
+    assert {it for _, it in info_f["inner_iters"]} == {1}
+    up, info_p = ddm.solve(D, inner="full_block_printed", inner_tol=1e-12, outer_tol=1e-12)
+    assert np.linalg.norm(up - u0) <= 1e-9 * np.linalg.norm(u0)
+    assert max(it for _, it in info_p["inner_iters"]) > 1
