@@ -53,6 +53,8 @@ constexpr int BT_GQ = 8;
 constexpr int BT_GMAX = 4;
 constexpr int BT_MAX_M = 4 * BT_GQ * BT_GMAX * BT_NW;     // 1536
 constexpr int BT_NC = 4;                    // slots of the coupling ring
+constexpr int BT_PROW = 2;                  // rows per pass of the order-2 prologue and epilogue
+                                            // (3 measured slower: the epilogue went from 25k to 41k cycles)
 
 __host__ __device__ constexpr int bt_r4(int v) { return (v + 3) / 4 * 4; }
 __host__ __device__ constexpr size_t bt_r16(size_t v) { return (v + 15) / 16 * 16; }
@@ -154,18 +156,17 @@ __device__ __forceinline__ unsigned long long bt_now_ns() {
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
-constexpr unsigned long long BT_WAIT_LIMIT_NS = 1000000000ull;     // 1 s per wait
-
-// Bounded wait (1 s of wall time) that gives up at once when the CTA has
-// already aborted; on expiry it raises the abort flag and *err.
+// Bounded wait (limit_ns of wall time, 1 s by default) that gives up at once
+// when the CTA has already aborted; on expiry it raises the abort flag and *err.
 template <bool CLUSTER>
-__device__ __forceinline__ bool bt_wait(uint64_t* bar, unsigned parity, volatile int* abort, int* err) {
+__device__ __forceinline__ bool bt_wait(uint64_t* bar, unsigned parity, volatile int* abort, int* err,
+                                        unsigned long long limit_ns) {
     if (CLUSTER ? mbar_try_cluster(bar, parity) : mbar_try(bar, parity)) return true;
     const unsigned long long t0 = bt_now_ns();
     while (true) {
         if (CLUSTER ? mbar_try_cluster_sleep(bar, parity) : mbar_try_sleep(bar, parity)) return true;
         if (*abort) return false;
-        if (bt_now_ns() - t0 > BT_WAIT_LIMIT_NS) break;
+        if (bt_now_ns() - t0 > limit_ns) break;
     }
     *abort = 1;
     atomicExch(err, 1);
@@ -258,6 +259,8 @@ __device__ __forceinline__ void bt_quad_fma(const FW* p, const V s, Rt (&acc)[4]
     }
 }
 
+// 416 threads = 13 warps, allocated as 16 (4 per SM sub-partition): at most
+// 128 registers per thread (152 fails to launch)
 template <class V, class F, class FW = F>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(BT_THREADS, 1)
 k_bt_solve(const Sub* __restrict__ subs, const Level* __restrict__ levels, const FW* __restrict__ fac,
@@ -265,7 +268,7 @@ k_bt_solve(const Sub* __restrict__ subs, const Level* __restrict__ levels, const
            int64_t n_loc, int condensed, const int32_t* __restrict__ ai, const F* __restrict__ av,
            const int32_t* __restrict__ ci, const F* __restrict__ cv, const int32_t* __restrict__ ei,
            const F* __restrict__ ev, int R, int ns, int slot_bytes, int cslot_bytes, int cglob, int max_lev, int nvec,
-           int max_m,
+           int max_m, unsigned long long wait_ns, int stall_w,
            int* __restrict__ err, const int* __restrict__ act, const int64_t* __restrict__ welem,
            unsigned long long* __restrict__ work, const V* __restrict__ x, V* __restrict__ y) {
     using Rt = typename VT<V>::R;
@@ -333,7 +336,7 @@ k_bt_solve(const Sub* __restrict__ subs, const Level* __restrict__ levels, const
                 const int m = Lv.size, ldm = bt_r4(m);
                 if (st.cpl && !cglob) {
                     const int q = pc % BT_NC, n = pc / BT_NC;
-                    if (n > 0 && !bt_wait<false>(&cempty[q], (unsigned)((n - 1) & 1), abort, err)) { ok = false; break; }
+                    if (n > 0 && !bt_wait<false>(&cempty[q], (unsigned)((n - 1) & 1), abort, err, wait_ns)) { ok = false; break; }
                     unsigned char* dst = cslots + (size_t)q * cslot_bytes;
                     fence_proxy_async();
                     const bool e = st.cpl == 1;
@@ -350,17 +353,18 @@ k_bt_solve(const Sub* __restrict__ subs, const Level* __restrict__ levels, const
                 }
                 for (int r0 = st.ra; r0 < st.rb && ok; r0 += R, ++pw) {
                     const int q = pw % ns, n = pw / ns;
-                    if (n > 0 && !bt_wait<false>(&empty[q], (unsigned)((n - 1) & 1), abort, err)) { ok = false; break; }
+                    if (n > 0 && !bt_wait<false>(&empty[q], (unsigned)((n - 1) & 1), abort, err, wait_ns)) { ok = false; break; }
                     unsigned char* dst = slots + (size_t)q * slot_bytes;
                     fence_proxy_async();
                     const int nr = min(R, st.rb - r0);
                     const unsigned wb = (unsigned)((size_t)nr * ldm * sizeof(FW));
+                    if (stall_w) continue;           // failure-detection test: the W tiles never come
                     mbar_expect_tx(&full[q], wb);
                     tma_load_1d(dst, fac + Lv.offW + (int64_t)r0 * ldm, wb, &full[q]);
                 }
             }
             // let every issued copy land before the CTA may leave
-            for (int q = 0; q < ns && q < pw; ++q) {
+            for (int q = 0; q < ns && q < pw && !stall_w; ++q) {
                 const int last = q + ((pw - 1 - q) / ns) * ns;      // last tile issued into slot q
                 for (int it = 0; it < (1 << 22); ++it)
                     if (mbar_try(&full[q], (unsigned)((last / ns) & 1))) break;
@@ -377,25 +381,25 @@ k_bt_solve(const Sub* __restrict__ subs, const Level* __restrict__ levels, const
         const int vbase = rank == 0 ? lv[0].start : lv[k].start;
         const int vend = rank == 0 ? lv[k].start + lv[k].size : lv[L - 1].start + lv[L - 1].size;
         // (a) load r for this rank's levels; order 2: r_E <- r_E - G r_I.
-        // Two rows per pass: their table loads, then their gathers, are in
+        // BT_PROW rows per pass: their table loads, then their gathers, are in
         // flight together (each row's arithmetic is unchanged).
-        for (int e0 = vbase + tid; e0 < vend; e0 += 2 * BT_NT) {
-            int64_t ix[2][8];
-            Rt gv[2][8];
-            V xr[2];
+        for (int e0 = vbase + tid; e0 < vend; e0 += BT_PROW * BT_NT) {
+            int32_t ix[BT_PROW][8];
+            Rt gv[BT_PROW][8];
+            V xr[BT_PROW];
 #pragma unroll
-            for (int r = 0; r < 2; ++r) {
+            for (int r = 0; r < BT_PROW; ++r) {
                 const int e = e0 + r * BT_NT;
                 const bool ok = e < vend;
                 xr[r] = ok ? x[e] : mk<V>(0, 0);
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
-                    ix[r][u] = (ok && condensed) ? (int64_t)ai[u * n_loc + e] : -1;
+                    ix[r][u] = (ok && condensed) ? ai[u * n_loc + e] : -1;
                     gv[r][u] = (ok && condensed) ? (Rt)av[u * n_loc + e] : (Rt)0;
                 }
             }
 #pragma unroll
-            for (int r = 0; r < 2; ++r) {
+            for (int r = 0; r < BT_PROW; ++r) {
                 const int e = e0 + r * BT_NT;
                 Rt ar = xr[r].x, aim = xr[r].y;
                 V xb[8];
@@ -432,7 +436,7 @@ k_bt_solve(const Sub* __restrict__ subs, const Level* __restrict__ levels, const
                     C = ccol + qo;
                     Cv = cval + qo;
                 } else {
-                    bt_wait<false>(&cfull[q], (unsigned)((tc / BT_NC) & 1), abort, err);
+                    bt_wait<false>(&cfull[q], (unsigned)((tc / BT_NC) & 1), abort, err, wait_ns);
                     const unsigned char* buf = cslots + (size_t)q * cslot_bytes;
                     P = reinterpret_cast<const int*>(buf);
                     C = P + bt_r4(m + 1);
@@ -488,7 +492,7 @@ k_bt_solve(const Sub* __restrict__ subs, const Level* __restrict__ levels, const
                 // the peer's coupling term of the middle level arrives in rx
                 __syncwarp();
                 if (lane == 0) mbar_arrive_remote(mapa_u32(&xbar[0], (unsigned)peer));
-                bt_wait<true>(&xbar[0], 0u, abort, err);
+                bt_wait<true>(&xbar[0], 0u, abort, err, wait_ns);
                 for (int i = tid; i < m; i += BT_NT) {
                     const V r = vec[o + i], a = tx[i], b = rx[i];
                     su[i] = mk<V>(r.x - a.x - b.x, r.y - a.y - b.y);
@@ -514,7 +518,7 @@ k_bt_solve(const Sub* __restrict__ subs, const Level* __restrict__ levels, const
                 for (int c = 0; c < 4; ++c) acc[u][c][0] = acc[u][c][1] = 0;
             for (int r0 = st.ra; r0 < st.rb; r0 += R) {
                 const int q = t % ns;
-                bt_wait<false>(&full[q], (unsigned)((t / ns) & 1), abort, err);
+                bt_wait<false>(&full[q], (unsigned)((t / ns) & 1), abort, err, wait_ns);
                 const FW* Wt = reinterpret_cast<const FW*>(slots + (size_t)q * slot_bytes);
                 const int nr = min(R, st.rb - r0);
 #pragma unroll
@@ -573,7 +577,7 @@ k_bt_solve(const Sub* __restrict__ subs, const Level* __restrict__ levels, const
                 // warp of both CTAs has written its outputs)
                 __syncwarp();
                 if (lane == 0) mbar_arrive_remote(mapa_u32(&xbar[1], (unsigned)peer));
-                bt_wait<true>(&xbar[1], 0u, abort, err);
+                bt_wait<true>(&xbar[1], 0u, abort, err, wait_ns);
                 bt_bar_consumers();
                 for (int i = tid; i < m; i += BT_NT) {
                     const V a = tx[i], b = ry[i];
@@ -592,28 +596,28 @@ k_bt_solve(const Sub* __restrict__ subs, const Level* __restrict__ levels, const
         const int64_t b0 = S.off + S.ne, nbub = S.n - S.ne;
         const int64_t half = (nbub + 1) / 2;
         const int64_t lo = b0 + (rank == 0 ? 0 : half), hi = b0 + (rank == 0 ? half : nbub);
-        // two rows per pass, as in (a)
-        for (int64_t b0r = lo + tid; b0r < hi; b0r += 2 * (int64_t)blockDim.x) {
-            int64_t cix[2][4], eix[2][8];
-            Rt cc[2][4], ec[2][8];
+        // BT_PROW rows per pass, as in (a)
+        for (int64_t b0r = lo + tid; b0r < hi; b0r += BT_PROW * (int64_t)blockDim.x) {
+            int32_t cix[BT_PROW][4], eix[BT_PROW][8];
+            Rt cc[BT_PROW][4], ec[BT_PROW][8];
 #pragma unroll
-            for (int r = 0; r < 2; ++r) {
+            for (int r = 0; r < BT_PROW; ++r) {
                 const int64_t b = b0r + r * (int64_t)blockDim.x;
                 const bool ok = b < hi;
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    cix[r][j] = ok ? (int64_t)ci[j * n_loc + b] : -1;
+                    cix[r][j] = ok ? ci[j * n_loc + b] : -1;
                     cc[r][j] = ok ? (Rt)cv[j * n_loc + b] : (Rt)0;
                 }
 #pragma unroll
                 for (int a = 0; a < 8; ++a) {
                     const int64_t e = ok ? (int64_t)ei[a * n_loc + b] : -1;
-                    eix[r][a] = (e >= S.off && e < S.off + S.ne) ? e : -1;
+                    eix[r][a] = (e >= S.off && e < S.off + S.ne) ? (int32_t)e : -1;
                     ec[r][a] = eix[r][a] >= 0 ? (Rt)ev[a * n_loc + b] : (Rt)0;
                 }
             }
 #pragma unroll
-            for (int r = 0; r < 2; ++r) {
+            for (int r = 0; r < BT_PROW; ++r) {
                 const int64_t b = b0r + r * (int64_t)blockDim.x;
                 V xb[4], xe[8];
 #pragma unroll

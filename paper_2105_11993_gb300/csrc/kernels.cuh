@@ -53,13 +53,28 @@ __global__ void __launch_bounds__(256) k_spmv(int64_t n, const int64_t* __restri
             ai += v * xv.y + b * xv.x;
         }
     } else {
-#pragma unroll 4
-        for (int t = 0; t < w; ++t) {
-            int32_t c = __ldg(cp + (t << 5));
-            R v = (R)__ldg(vp + (t << 5));
-            V xv = x[c];
-            ar += v * xv.x;
-            ai += v * xv.y;
+        // slots in groups of 8: the 8 index and value loads, then the 8
+        // gathers of x, are in flight together
+        for (int t0 = 0; t0 < w; t0 += 8) {
+            int32_t c[8];
+            R v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                c[u] = (int32_t)r;
+                v[u] = 0;
+                if (t0 + u < w) {
+                    c[u] = __ldg(cp + ((t0 + u) << 5));
+                    v[u] = (R)__ldg(vp + ((t0 + u) << 5));
+                }
+            }
+            V xv[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) xv[u] = x[c[u]];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                ar += v[u] * xv[u].x;
+                ai += v[u] * xv[u].y;
+            }
         }
     }
     R b = (R)bg[r];
@@ -150,6 +165,14 @@ __device__ __forceinline__ bool last_block_of_segment(int seg, const int32_t* __
 // h[seg][k] = sum over the segment's chunks of v_k^H w (FP64), k < nk.
 // reset (optional): an int the first block sets to 0 (the active-segment
 // count that the Givens step of the same Arnoldi step accumulates).
+// h[seg][k] = v_k^H w for the chunk c of a block whose threads hold w in
+// wr (EPT elements each); the last block of the segment writes h.
+template <class V>
+__device__ __forceinline__ void chunk_dots_body(const Chunk& c, const V* __restrict__ basis, int64_t ld, int nk,
+                                                const V (&wr)[EPT], double2* __restrict__ partial, int ldp,
+                                                const int32_t* __restrict__ seg_ch, int* __restrict__ cnt,
+                                                double2* __restrict__ h, int ldh, double2* sred);
+
 template <class V>
 __global__ void __launch_bounds__(KT) k_chunk_dots(const Chunk* __restrict__ chunks, const V* __restrict__ basis,
                                                    int64_t ld, int nk, const V* __restrict__ w,
@@ -157,41 +180,67 @@ __global__ void __launch_bounds__(KT) k_chunk_dots(const Chunk* __restrict__ chu
                                                    const int* __restrict__ act, const int32_t* __restrict__ seg_ch,
                                                    int* __restrict__ cnt, double2* __restrict__ h, int ldh,
                                                    int* __restrict__ reset) {
-    using R = typename VT<V>::R;
     extern __shared__ double2 sred[];          // [nk][KT/32]
     if (reset && blockIdx.x == 0 && threadIdx.x == 0) *reset = 0;
     const Chunk c = chunks[blockIdx.x];
     if (act && !act[c.seg]) return;            // converged segment: its partials are not read
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     V wr[EPT];
 #pragma unroll
     for (int q = 0; q < EPT; ++q) {
         int64_t e = c.begin + threadIdx.x + (int64_t)q * KT;
         wr[q] = e < c.end ? w[e] : mk<V>(0, 0);
     }
+    chunk_dots_body<V>(c, basis, ld, nk, wr, partial, ldp, seg_ch, cnt, h, ldh, sred);
+}
+
+template <class V>
+__device__ __forceinline__ void chunk_dots_body(const Chunk& c, const V* __restrict__ basis, int64_t ld, int nk,
+                                                const V (&wr)[EPT], double2* __restrict__ partial, int ldp,
+                                                const int32_t* __restrict__ seg_ch, int* __restrict__ cnt,
+                                                double2* __restrict__ h, int ldh, double2* sred) {
+    using R = typename VT<V>::R;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const bool full = c.end - c.begin == CHUNK;
-    int k = 0;
-    for (; k < nk; ++k) {
-        const V* vk = basis + (int64_t)k * ld;
-        R ar = 0, ai = 0;
+    // basis vectors in blocks of KB: their KB * EPT loads are issued together,
+    // so a block of vectors costs one memory latency instead of KB
+    constexpr int KB = 4;
+    for (int k0 = 0; k0 < nk; k0 += KB) {
+        V v[KB][EPT];
 #pragma unroll
-        for (int q = 0; q < EPT; ++q) {
-            int64_t e = c.begin + threadIdx.x + (int64_t)q * KT;
-            if (full || e < c.end) {
-                V v = vk[e];
-                ar += v.x * wr[q].x + v.y * wr[q].y;       // conj(v) * w
-                ai += v.x * wr[q].y - v.y * wr[q].x;
+        for (int b = 0; b < KB; ++b) {
+            const V* vk = basis + (int64_t)(k0 + b) * ld;
+#pragma unroll
+            for (int q = 0; q < EPT; ++q) {
+                const int64_t e = c.begin + threadIdx.x + (int64_t)q * KT;
+                v[b][q] = mk<V>(0, 0);
+                if (k0 + b < nk && (full || e < c.end)) v[b][q] = vk[e];
+            }
+        }
+        R ar[KB], ai[KB];
+#pragma unroll
+        for (int b = 0; b < KB; ++b) {
+            ar[b] = 0;
+            ai[b] = 0;
+#pragma unroll
+            for (int q = 0; q < EPT; ++q) {
+                ar[b] += v[b][q].x * wr[q].x + v[b][q].y * wr[q].y;       // conj(v) * w
+                ai[b] += v[b][q].x * wr[q].y - v[b][q].y * wr[q].x;
             }
         }
         // a warp sums its 4 * 32 products in the vector precision; from the
         // cross-warp sum on every sum is FP64 (FP64 shuffles at the warp level
         // cost 2.7x the kernel time on this part, measured)
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            ar += __shfl_down_sync(0xffffffffu, ar, o);
-            ai += __shfl_down_sync(0xffffffffu, ai, o);
-        }
-        if (lane == 0) sred[k * (KT / 32) + warp] = make_double2((double)ar, (double)ai);
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int b = 0; b < KB; ++b) {
+                ar[b] += __shfl_down_sync(0xffffffffu, ar[b], o);
+                ai[b] += __shfl_down_sync(0xffffffffu, ai[b], o);
+            }
+        if (lane == 0)
+#pragma unroll
+            for (int b = 0; b < KB; ++b)
+                if (k0 + b < nk) sred[(k0 + b) * (KT / 32) + warp] = make_double2((double)ar[b], (double)ai[b]);
     }
     __syncthreads();
     for (int kk = threadIdx.x; kk < nk; kk += KT) {
@@ -215,7 +264,7 @@ __global__ void __launch_bounds__(KT) k_chunk_dots(const Chunk* __restrict__ chu
 template <class V>
 __device__ __forceinline__ void chunk_update_body(const Chunk& c, const V* __restrict__ basis, int64_t ld, int nk,
                                                   const double2* __restrict__ h, int ldh, V* __restrict__ w,
-                                                  double* __restrict__ nrm_part, double2* sh);
+                                                  double* __restrict__ nrm_part, double2* sh, V* wout = nullptr);
 
 template <class V>
 __global__ void __launch_bounds__(KT) k_chunk_update(const Chunk* __restrict__ chunks, const V* __restrict__ basis,
@@ -231,7 +280,7 @@ __global__ void __launch_bounds__(KT) k_chunk_update(const Chunk* __restrict__ c
 template <class V>
 __device__ __forceinline__ void chunk_update_body(const Chunk& c, const V* __restrict__ basis, int64_t ld, int nk,
                                                   const double2* __restrict__ h, int ldh, V* __restrict__ w,
-                                                  double* __restrict__ nrm_part, double2* sh) {
+                                                  double* __restrict__ nrm_part, double2* sh, V* wout) {
     using R = typename VT<V>::R;
     __shared__ double sw[KT / 32];
     for (int k = threadIdx.x; k < nk; k += KT) sh[k] = h[(int64_t)c.seg * ldh + k];
@@ -245,16 +294,28 @@ __device__ __forceinline__ void chunk_update_body(const Chunk& c, const V* __res
         xr[q] = a.x;
         xi[q] = a.y;
     }
-    for (int k = 0; k < nk; ++k) {             // basis index outer: EPT independent loads per step
-        const V* vk = basis + (int64_t)k * ld;
-        const R hr = (R)sh[k].x, hi = (R)sh[k].y;
+    // basis vectors in blocks of KB: KB * EPT independent loads in flight
+    constexpr int KB = 4;
+    for (int k0 = 0; k0 < nk; k0 += KB) {
+        V v[KB][EPT];
 #pragma unroll
-        for (int q = 0; q < EPT; ++q) {
-            int64_t e = c.begin + threadIdx.x + (int64_t)q * KT;
-            if (full || e < c.end) {
-                V v = vk[e];
-                xr[q] -= hr * v.x - hi * v.y;
-                xi[q] -= hr * v.y + hi * v.x;
+        for (int b = 0; b < KB; ++b) {
+            const V* vk = basis + (int64_t)(k0 + b) * ld;
+#pragma unroll
+            for (int q = 0; q < EPT; ++q) {
+                const int64_t e = c.begin + threadIdx.x + (int64_t)q * KT;
+                v[b][q] = mk<V>(0, 0);
+                if (k0 + b < nk && (full || e < c.end)) v[b][q] = vk[e];
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < KB; ++b) {
+            const int kk = min(k0 + b, nk - 1);
+            const R hr = k0 + b < nk ? (R)sh[kk].x : (R)0, hi = k0 + b < nk ? (R)sh[kk].y : (R)0;
+#pragma unroll
+            for (int q = 0; q < EPT; ++q) {
+                xr[q] -= hr * v[b][q].x - hi * v[b][q].y;
+                xi[q] -= hr * v[b][q].y + hi * v[b][q].x;
             }
         }
     }
@@ -266,6 +327,7 @@ __device__ __forceinline__ void chunk_update_body(const Chunk& c, const V* __res
             w[e] = mk<V>(xr[q], xi[q]);
             nr += xr[q] * xr[q] + xi[q] * xi[q];
         }
+        if (wout) wout[q] = (full || e < c.end) ? mk<V>(xr[q], xi[q]) : mk<V>(0, 0);
     }
     if (nrm_part) {
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -279,6 +341,25 @@ __device__ __forceinline__ void chunk_update_body(const Chunk& c, const V* __res
             nrm_part[blockIdx.x] = s;
         }
     }
+}
+
+// First Gram-Schmidt update and second projection in one pass over the
+// chunk: w <- w - V h1 (written back), then h2 = V^H w from the updated
+// values still in registers.  The block rereads its basis slab right after
+// the update, while it is in L2, so V is streamed from DRAM once for both.
+template <class V>
+__global__ void __launch_bounds__(KT) k_update_dots(const Chunk* __restrict__ chunks, const V* __restrict__ basis,
+                                                    int64_t ld, int nk, const double2* __restrict__ h1, int ldh,
+                                                    V* __restrict__ w, double2* __restrict__ partial, int ldp,
+                                                    const int* __restrict__ act, const int32_t* __restrict__ seg_ch,
+                                                    int* __restrict__ cnt, double2* __restrict__ h2) {
+    extern __shared__ double2 sh[];            // [nk] coefficients, then [nk][KT/32] warp sums
+    const Chunk c = chunks[blockIdx.x];
+    if (act && !act[c.seg]) return;
+    V wr[EPT];
+    chunk_update_body<V>(c, basis, ld, nk, h1, ldh, w, nullptr, sh, wr);
+    __syncthreads();                           // sh is reused for the warp sums
+    chunk_dots_body<V>(c, basis, ld, nk, wr, partial, ldp, seg_ch, cnt, h2, ldh, sh);
 }
 
 template <class V>

@@ -72,6 +72,197 @@ __global__ void k_cell_dofs(int dim, int order, int64_t n_cell, const int32_t* _
     }
 }
 
+// ---------------------------------------------------------------------------
+// Global edges on the device: every (cell, local edge) gives the key
+// min(id) * n_vert + max(id); the distinct keys in increasing order are the
+// edges in the lexicographic order of (min id, max id).  A stable LSD radix
+// sort (8-bit digits, 256-key tiles) orders the keys, then the first key of
+// each run of equal keys is kept.  Everything is deterministic.
+// ---------------------------------------------------------------------------
+constexpr int RX_TILE = 256;                      // keys per tile (one per thread)
+constexpr int RX_BINS = 256;                      // 8-bit digits
+
+__global__ void k_edge_keys(int dim, int64_t n_cell, const int32_t* __restrict__ cells, int64_t n_vert,
+                            unsigned long long* __restrict__ keys) {
+    const int ne = dim == 2 ? 4 : 12, nv = dim == 2 ? 4 : 8;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n_cell * ne) return;
+    const int64_t c = i / ne;
+    const int k = (int)(i % ne);
+    const int a = dim == 2 ? c_edges2[k][0] : c_edges3[k][0];
+    const int b = dim == 2 ? c_edges2[k][1] : c_edges3[k][1];
+    const int64_t va = cells[c * nv + a], vb = cells[c * nv + b];
+    const int64_t lo = va < vb ? va : vb, hi = va < vb ? vb : va;
+    keys[i] = (unsigned long long)lo * (unsigned long long)n_vert + (unsigned long long)hi;
+}
+
+// Per tile and warp: how many keys of each digit precede a key in its warp
+// (match mask), the warp's count per digit, and the tile's count per digit.
+__device__ __forceinline__ void rx_rank(unsigned digit, bool valid, int* wcnt /* [8][256] */, int& rank_w) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned vmask = __ballot_sync(0xffffffffu, valid);
+    const unsigned peers = __match_any_sync(0xffffffffu, valid ? digit : 0xffffffffu) & vmask;
+    rank_w = __popc(peers & ((1u << lane) - 1u));
+    if (valid && rank_w == 0) wcnt[warp * RX_BINS + digit] = __popc(peers);
+}
+
+// Tile histogram of the digit at `shift`: hist[bin * n_tiles + tile].
+__global__ void __launch_bounds__(RX_TILE) k_rx_hist(int64_t n, const unsigned long long* __restrict__ keys,
+                                                     int shift, int n_tiles, unsigned* __restrict__ hist) {
+    __shared__ int wcnt[RX_TILE / 32 * RX_BINS];
+    for (int t = threadIdx.x; t < RX_TILE / 32 * RX_BINS; t += blockDim.x) wcnt[t] = 0;
+    __syncthreads();
+    const int64_t i = blockIdx.x * (int64_t)RX_TILE + threadIdx.x;
+    const bool valid = i < n;
+    const unsigned d = valid ? (unsigned)((keys[i] >> shift) & (RX_BINS - 1)) : 0u;
+    int r;
+    rx_rank(d, valid, wcnt, r);
+    __syncthreads();
+    int sum = 0;
+    for (int w = 0; w < RX_TILE / 32; ++w) sum += wcnt[w * RX_BINS + threadIdx.x];
+    hist[(int64_t)threadIdx.x * n_tiles + blockIdx.x] = (unsigned)sum;
+}
+
+// Stable scatter: position = offs[bin * n_tiles + tile] (exclusive scan of
+// the histograms, bin major) + the counts of earlier warps + the rank in the warp.
+__global__ void __launch_bounds__(RX_TILE) k_rx_scatter(int64_t n, const unsigned long long* __restrict__ in,
+                                                        int shift, int n_tiles, const unsigned* __restrict__ offs,
+                                                        unsigned long long* __restrict__ out) {
+    __shared__ int wcnt[RX_TILE / 32 * RX_BINS];
+    for (int t = threadIdx.x; t < RX_TILE / 32 * RX_BINS; t += blockDim.x) wcnt[t] = 0;
+    __syncthreads();
+    const int64_t i = blockIdx.x * (int64_t)RX_TILE + threadIdx.x;
+    const bool valid = i < n;
+    const unsigned long long key = valid ? in[i] : 0ull;
+    const unsigned d = (unsigned)((key >> shift) & (RX_BINS - 1));
+    int r;
+    rx_rank(d, valid, wcnt, r);
+    __syncthreads();
+    if (!valid) return;
+    const int warp = threadIdx.x >> 5;
+    int before = 0;
+    for (int w = 0; w < warp; ++w) before += wcnt[w * RX_BINS + d];
+    out[offs[(int64_t)d * n_tiles + blockIdx.x] + before + r] = key;
+}
+
+// Exclusive scan of n unsigned values in place (three passes over blocks of
+// 1024 values; deterministic).
+__global__ void k_scan_block_sums(int64_t n, const unsigned* __restrict__ a, unsigned* __restrict__ sums) {
+    __shared__ unsigned sw[32];
+    unsigned s = 0;
+    for (int64_t i = blockIdx.x * 1024ll + threadIdx.x; i < n && i < (blockIdx.x + 1) * 1024ll; i += blockDim.x) s += a[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned t = 0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += sw[q];
+        sums[blockIdx.x] = t;
+    }
+}
+__global__ void k_scan_sums_serial(int nb, unsigned* __restrict__ sums) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    unsigned run = 0;
+    for (int b = 0; b < nb; ++b) {
+        const unsigned v = sums[b];
+        sums[b] = run;
+        run += v;
+    }
+}
+// one block of 1024 threads per 1024 values: block-local exclusive scan plus the block offset
+__global__ void __launch_bounds__(1024) k_scan_apply(int64_t n, unsigned* __restrict__ a,
+                                                     const unsigned* __restrict__ sums) {
+    __shared__ unsigned sw[32];
+    const int64_t i = blockIdx.x * 1024ll + threadIdx.x;
+    const unsigned v = i < n ? a[i] : 0u;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned incl = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) sw[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        unsigned x = sw[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned t = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += t;
+        }
+        sw[lane] = x;                              // inclusive over warps
+    }
+    __syncthreads();
+    const unsigned warp_off = warp > 0 ? sw[warp - 1] : 0u;
+    if (i < n) a[i] = sums[blockIdx.x] + warp_off + incl - v;
+}
+
+static void device_exclusive_scan(unsigned* a, int64_t n, DArr<unsigned>& sums) {
+    const int64_t nb = (n + 1023) / 1024;
+    if ((int64_t)sums.n < nb) sums.alloc(nb);
+    THM_LAUNCH(THM_K_SETUP, 0, k_scan_block_sums<<<(unsigned)nb, 256>>>(n, a, sums.p));
+    THM_LAUNCH(THM_K_SETUP, 0, k_scan_sums_serial<<<1, 32>>>((int)nb, sums.p));
+    THM_LAUNCH(THM_K_SETUP, 0, k_scan_apply<<<(unsigned)nb, 1024>>>(n, a, sums.p));
+}
+
+// flag[i] = 1 for the first key of each run of equal keys
+__global__ void k_run_heads(int64_t n, const unsigned long long* __restrict__ keys, unsigned* __restrict__ flag) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) flag[i] = (i == 0 || keys[i] != keys[i - 1]) ? 1u : 0u;
+}
+__global__ void k_edges_from_keys(int64_t n, const unsigned long long* __restrict__ keys,
+                                  const unsigned* __restrict__ pos, int64_t n_vert, int64_t* __restrict__ elo,
+                                  int64_t* __restrict__ ehi) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n || !(i == 0 || keys[i] != keys[i - 1])) return;
+    const unsigned long long k = keys[i];
+    elo[pos[i]] = (int64_t)(k / (unsigned long long)n_vert);
+    ehi[pos[i]] = (int64_t)(k % (unsigned long long)n_vert);
+}
+
+// The distinct edges (lexicographic (lo, hi)) of the cells, computed on the
+// device into m->d_edge_lo / d_edge_hi and copied to the host tables.
+static void device_edges(thm_mesh* m) {
+    const int ne = m->dim == 2 ? 4 : 12;
+    const int64_t n = m->n_cell * ne;
+    THM_REQUIRE(n < (int64_t)UINT32_MAX, "too many cell edges");
+    DArr<unsigned long long> ka, kb;
+    ka.alloc(n);
+    kb.alloc(n);
+    const int th = 256;
+    auto grid = [&](int64_t c) { return (unsigned)((c + th - 1) / th); };
+    THM_LAUNCH(THM_K_SETUP, 0, k_edge_keys<<<grid(n), th>>>(m->dim, m->n_cell, m->d_cells.p, m->n_vert, ka.p));
+    // digits needed for keys < n_vert^2
+    const unsigned long long kmax = (unsigned long long)m->n_vert * (unsigned long long)m->n_vert;
+    int bits = 1;
+    while (bits < 64 && (kmax >> bits) != 0) ++bits;
+    const int n_tiles = (int)((n + RX_TILE - 1) / RX_TILE);
+    DArr<unsigned> hist, sums;
+    hist.alloc((size_t)RX_BINS * n_tiles);
+    unsigned long long* src = ka.p;
+    unsigned long long* dst = kb.p;
+    for (int shift = 0; shift < bits; shift += 8) {
+        THM_LAUNCH(THM_K_SETUP, 0, k_rx_hist<<<n_tiles, RX_TILE>>>(n, src, shift, n_tiles, hist.p));
+        device_exclusive_scan(hist.p, (int64_t)RX_BINS * n_tiles, sums);
+        THM_LAUNCH(THM_K_SETUP, 0, k_rx_scatter<<<n_tiles, RX_TILE>>>(n, src, shift, n_tiles, hist.p, dst));
+        std::swap(src, dst);
+    }
+    DArr<unsigned> pos;
+    pos.alloc(n);
+    THM_LAUNCH(THM_K_SETUP, 0, k_run_heads<<<grid(n), th>>>(n, src, pos.p));
+    unsigned last_flag = 0, last_pos = 0;
+    THM_CUDA(cudaMemcpy(&last_flag, pos.p + (n - 1), sizeof(unsigned), cudaMemcpyDeviceToHost));
+    device_exclusive_scan(pos.p, n, sums);
+    THM_CUDA(cudaMemcpy(&last_pos, pos.p + (n - 1), sizeof(unsigned), cudaMemcpyDeviceToHost));
+    m->n_edge = (int64_t)last_pos + last_flag;
+    m->d_edge_lo.alloc(m->n_edge);
+    m->d_edge_hi.alloc(m->n_edge);
+    THM_LAUNCH(THM_K_SETUP, 0, k_edges_from_keys<<<grid(n), th>>>(n, src, pos.p, m->n_vert, m->d_edge_lo.p,
+                                                                  m->d_edge_hi.p));
+    THM_CUDA(cudaGetLastError());
+    m->d_edge_lo.download(m->edge_lo);
+    m->d_edge_hi.download(m->edge_hi);
+}
+
 static int64_t host_find_edge(const thm_mesh* m, int64_t a, int64_t b) {
     int64_t x = std::min(a, b), y = std::max(a, b);
     auto it = std::lower_bound(m->edge_lo.begin(), m->edge_lo.end(), x);
@@ -124,36 +315,15 @@ void build_mesh(thm_mesh* m) {
     m->dpc = (m->order == 1) ? ne : 12;
     check_axis_aligned(m);
 
-    // ---- global edges: distinct (lo, hi) pairs in lexicographic order
-    std::vector<std::pair<int64_t, int64_t>> keys;
-    keys.reserve(m->n_cell * ne);
-    for (int64_t c = 0; c < m->n_cell; ++c)
-        for (int k = 0; k < ne; ++k) {
-            int a = d == 2 ? h_edges2[k][0] : h_edges3[k][0];
-            int b = d == 2 ? h_edges2[k][1] : h_edges3[k][1];
-            int64_t va = m->cells[c * nv + a], vb = m->cells[c * nv + b];
-            keys.emplace_back(std::min(va, vb), std::max(va, vb));
-        }
-    std::sort(keys.begin(), keys.end());
-    keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
-    m->n_edge = (int64_t)keys.size();
-    m->edge_lo.resize(m->n_edge);
-    m->edge_hi.resize(m->n_edge);
-    for (int64_t e = 0; e < m->n_edge; ++e) {
-        m->edge_lo[e] = keys[e].first;
-        m->edge_hi[e] = keys[e].second;
-    }
-    keys.clear();
-    keys.shrink_to_fit();
+    // ---- global edges: distinct (lo, hi) pairs in lexicographic order (device sort)
+    std::vector<int32_t> cells32(m->cells.begin(), m->cells.end());
+    m->d_cells.upload(cells32);
+    m->d_coords.upload(m->coords);
+    device_edges(m);
     m->n_dof = m->order == 1 ? m->n_edge : 2 * m->n_edge + 4 * m->n_cell;
     THM_REQUIRE(m->n_dof < (int64_t)INT32_MAX, "more than 2^31 DOFs");
 
     // ---- per-cell DOFs and signs on the device
-    std::vector<int32_t> cells32(m->cells.begin(), m->cells.end());
-    m->d_cells.upload(cells32);
-    m->d_coords.upload(m->coords);
-    m->d_edge_lo.upload(m->edge_lo);
-    m->d_edge_hi.upload(m->edge_hi);
     m->d_cell_dofs.alloc(m->n_cell * m->dpc);
     m->d_cell_signs.alloc(m->n_cell * m->dpc);
     DArr<int> bad;

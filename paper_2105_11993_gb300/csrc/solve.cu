@@ -383,6 +383,7 @@ struct Krylov {
                                           (int)((m + 1) * sizeof(double2))));
             THM_CUDA(cudaFuncSetAttribute(k_update_givens<V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)givens_smem(m)));
+            THM_CUDA(cudaFuncSetAttribute(k_update_dots<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dots_smem));
             dots_attr = dots_smem;
         }
         THM_CUDA(cudaDeviceSynchronize());
@@ -450,14 +451,14 @@ struct Krylov {
                 step_mask = nullptr;
                 const int nk = j + 1;
                 size_t sm = (size_t)nk * (KT / 32) * sizeof(double2);
-                // CGS2: h1 = V^H w, w -= V h1, h2 = V^H w, w -= V h2 (the dot kernels
-                // reduce their segments themselves); the second update also forms
-                // ||w|| and the Givens step of each segment
+                // CGS2: h1 = V^H w, then w -= V h1 and h2 = V^H w in one pass, then
+                // w -= V h2 (the dot kernels reduce their segments themselves); the
+                // second update also forms ||w|| and the Givens step of each segment
                 THM_LAUNCH(THM_K_DOTS, st, k_chunk_dots<V><<<nch, KT, sm, st>>>(d_chunks, basis.p, n, nk, w.p, partial.p, m + 1,
                                                                                active.p, seg_ch.p, cnt.p, h1.p, m + 1, nact));
-                THM_LAUNCH(THM_K_UPDATE, st, k_chunk_update<V><<<nch, KT, nk * sizeof(double2), st>>>(d_chunks, basis.p, n, nk, h1.p, m + 1, w.p, nullptr, active.p));
-                THM_LAUNCH(THM_K_DOTS, st, k_chunk_dots<V><<<nch, KT, sm, st>>>(d_chunks, basis.p, n, nk, w.p, partial.p, m + 1,
-                                                                               active.p, seg_ch.p, cnt.p, h2.p, m + 1, nullptr));
+                THM_LAUNCH(THM_K_UPDATE, st, k_update_dots<V><<<nch, KT, sm, st>>>(d_chunks, basis.p, n, nk, h1.p, m + 1, w.p,
+                                                                                  partial.p, m + 1, active.p, seg_ch.p,
+                                                                                  cnt.p, h2.p));
                 GivensArgs ga{j, m, m + 1, h1.p, h2.p, Rm.p, cs.p, sn.p, gv.p, target.p, active.p, kused.p, beta.p,
                               nact, flag, nseg == 1 ? gmon : nullptr, seg_ch.p, cnt.p};
                 const size_t gsm = std::max((size_t)nk * sizeof(double2),
@@ -696,11 +697,19 @@ static void bt_launch(const thm_sys* s, const BtCfg& c, const FW* fac, const F* 
     // the work counter follows the Eq. 7 (real-factor) applies only
     unsigned long long* work =
         (s->bt_work.p && !BtCplx<FW>::value) ? s->bt_work.p + (sizeof(F) == 4 ? 2 : 0) : nullptr;
+    // every device wait gives up after THM_BT_WAIT_LIMIT_MS (default 1000 ms);
+    // THM_TEST_STALL_TMA=1 makes the tile stream never arrive, so that a test
+    // can see the bounded waits expire and THM_ETIMEOUT come back
+    const char* lim = getenv("THM_BT_WAIT_LIMIT_MS");
+    const unsigned long long wait_ns = 1000000ull * (unsigned long long)(lim ? std::max(1, atoi(lim)) : 1000);
+    const char* stall = getenv("THM_TEST_STALL_TMA");
+    const int stall_w = stall && atoi(stall) != 0 ? 1 : 0;
     THM_LAUNCH(THM_K_PINV, s->st,
                (k_bt_solve<V, F, FW><<<dim3(2, m->n_sub), BT_THREADS, c.smem, s->st>>>(
                    m->d_subs.p, m->d_levels.p, fac, m->d_cpl_ptr.p, m->d_cpl_col.p, cval, m->n_loc,
                    m->order == 2 ? 1 : 0, ai, av, ci, cv, ei, ev, c.rows, c.ns, (int)c.slot, (int)c.cslot, c.cglob,
-                   m->max_lev, c.nvec, m->max_m, s->dev_err.p, act, m->d_bt_welem.p, work, x, y)));
+                   m->max_lev, c.nvec, m->max_m, wait_ns, stall_w, s->dev_err.p, act, m->d_bt_welem.p, work, x,
+                   y)));
 }
 
 // The tile size is tuned once per mesh and factor precision: on the first
@@ -1010,6 +1019,12 @@ int solve_rhs(thm_sys* s, const SolveCfg& c, const double2* f_src, const double2
     }
     if (u0) THM_CUDA(cudaMemcpyAsync(u, u0, m->n_dof * sizeof(double2), cudaMemcpyDeviceToDevice, st));
     else THM_CUDA(cudaMemsetAsync(u, 0, m->n_dof * sizeof(double2), st));
+    if (!std::isfinite(fn)) {                    // a non-finite right-hand side (Dirichlet data or sources)
+        THM_CUDA(cudaStreamSynchronize(st));
+        rel = fn;
+        rs.status = THM_EBREAKDOWN;
+        return THM_EBREAKDOWN;
+    }
     THM_CUDA(cudaMemcpyAsync(w->src.p, f_src, m->n_loc * sizeof(double2), cudaMemcpyDeviceToDevice, st));
     rel = fn > 0 ? 1.0 : 0.0;
     for (int it = 0; it < c.max_refine && fn > 0; ++it) {

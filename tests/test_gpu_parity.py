@@ -329,3 +329,22 @@ def test_pinv_independent_of_tile_size(mode, monkeypatch):
     tol = 1e-12 if mode == "fp64" else 1e-5
     for y in ys[1:]:
         assert np.linalg.norm(y - ys[0]) <= tol * np.linalg.norm(ys[0])
+
+
+@pytest.mark.parametrize("name", ["square256_p2", "cube20_relabelled"])
+def test_numbering_on_large_meshes_bit_exact(name):
+    """The device edge numbering (radix sort of the cell-edge keys over many
+    tiles and digit passes) on a bench-sized 2-D mesh and a relabelled,
+    re-listed 3-D mesh: DOF ids and signs equal the oracle's definition."""
+    import paper_2105_11993_gb300 as thm
+    if name == "square256_p2":
+        P = W.config(name)
+        mesh_w, order = P.mesh, P.order
+    else:
+        mesh_w, order = W.structured_mesh_3d(20, 2, relabel=True, rotate_cells=True), 1
+    mesh = thm.Mesh.from_workload(mesh_w, order)
+    info = mesh.info(with_dofs=True)
+    d = fem.number_dofs(mesh_w.cells, mesh_w.dim, order)
+    assert info["n_dof"] == d.n_dof and info["n_edge"] == d.n_edge
+    assert np.array_equal(info["cell_dofs"], d.cell_dofs)
+    assert np.array_equal(info["cell_signs"], d.cell_signs)
