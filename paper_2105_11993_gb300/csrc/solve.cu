@@ -145,26 +145,32 @@ __global__ void __launch_bounds__(KT) k_update_givens(const Chunk* __restrict__ 
     if (threadIdx.x < 32) givens_warp(ga, c.seg, s_hn2, reinterpret_cast<unsigned char*>(sh));
 }
 
-// y = R^{-1} g (upper triangular, k = kused[s])
-__global__ void k_backsolve(int nseg, int m, const double2* __restrict__ Rm, const double2* __restrict__ gv,
-                            const int* __restrict__ kused, double2* __restrict__ y) {
-    int s = blockIdx.x * blockDim.x + threadIdx.x;
+// y = R^{-1} g (upper triangular, k = kused[s]), one warp per segment, by
+// columns: y_q = g_q / R_qq, then g_i -= R_iq y_q for i < q (column q of R is
+// contiguous).  The updated g lives in shared memory.
+__global__ void __launch_bounds__(32) k_backsolve(int nseg, int m, const double2* __restrict__ Rm,
+                                                  const double2* __restrict__ gv, const int* __restrict__ kused,
+                                                  double2* __restrict__ y) {
+    extern __shared__ double2 gsh[];           // [m]
+    const int s = blockIdx.x, lane = threadIdx.x;
     if (s >= nseg) return;
-    int k = kused[s];
+    const int k = kused[s];
     const double2* R = Rm + (int64_t)s * m * m;          // R[col * m + row]
-    const double2* g = gv + (int64_t)s * (m + 1);
-    double2* yy = y + (int64_t)s * m;
-    for (int i = k - 1; i >= 0; --i) {
-        double2 acc = g[i];
-        for (int q = i + 1; q < k; ++q) {
-            double2 r = R[(int64_t)q * m + i], v = yy[q];
-            acc.x -= r.x * v.x - r.y * v.y;
-            acc.y -= r.x * v.y + r.y * v.x;
+    for (int i = lane; i < k; i += 32) gsh[i] = gv[(int64_t)s * (m + 1) + i];
+    __syncwarp();
+    for (int q = k - 1; q >= 0; --q) {
+        const double2 d = R[(int64_t)q * m + q];
+        const double2 a = gsh[q];
+        const double den = d.x * d.x + d.y * d.y;
+        const double2 yq = den > 0 ? make_double2((a.x * d.x + a.y * d.y) / den, (a.y * d.x - a.x * d.y) / den)
+                                   : make_double2(0, 0);
+        if (lane == 0) y[(int64_t)s * m + q] = yq;
+        for (int i = lane; i < q; i += 32) {
+            const double2 r = R[(int64_t)q * m + i];
+            gsh[i].x -= r.x * yq.x - r.y * yq.y;
+            gsh[i].y -= r.x * yq.y + r.y * yq.x;
         }
-        double2 d = R[(int64_t)i * m + i];
-        double den = d.x * d.x + d.y * d.y;
-        yy[i] = den > 0 ? make_double2((acc.x * d.x + acc.y * d.y) / den, (acc.y * d.x - acc.x * d.y) / den)
-                        : make_double2(0, 0);
+        __syncwarp();
     }
 }
 
@@ -495,7 +501,8 @@ struct Krylov {
                 if (reinterpret_cast<const int*>(h_ring + 2 * (checked % RING))[1]) ks.status = THM_EBREAKDOWN;
             THM_CUDA(cudaGetLastError());
             // x += M (V y)
-            THM_LAUNCH(THM_K_KRYLOV, st, k_backsolve<<<nblk(nseg, 64), 64, 0, st>>>(nseg, m, Rm.p, gv.p, kused.p, y.p));
+            THM_LAUNCH(THM_K_KRYLOV, st, k_backsolve<<<nseg, 32, (size_t)m * sizeof(double2), st>>>(nseg, m, Rm.p, gv.p,
+                                                                                                  kused.p, y.p));
             if (flexible && M) {
                 // x += Z y: the preconditioned directions actually used by the Arnoldi process
                 THM_LAUNCH(THM_K_KRYLOV, st, k_chunk_combine<V><<<nch, KT, 0, st>>>(d_chunks, zbasis.p, n, kused.p, y.p, m, t.p));
