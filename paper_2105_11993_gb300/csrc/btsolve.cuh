@@ -45,10 +45,11 @@ namespace thm {
 constexpr int BT_NT = 384;                  // consumer threads
 constexpr int BT_NW = BT_NT / 32;           // consumer warps
 constexpr int BT_THREADS = BT_NT + 32;      // + one producer warp
-// GEMV layout: a warp pass covers GQ = 8 output quads with 4 row subsets, and
-// a warp holds at most GMAX quad groups, so m_l <= 4 * GQ * GMAX * BT_NW.
-// (A finer layout, 2 quads x 16 row subsets, keeps every warp busy on 130-row
-// levels but measured slower: 139 against 116 us per launch.)
+// GEMV layout of wide levels: a warp pass covers GQ = 8 output quads with 4
+// row subsets, and a warp holds at most GMAX quad groups, so
+// m_l <= 4 * GQ * GMAX * BT_NW.  (Levels of at most 48 quads take 4 quads with
+// 8 row subsets; 2 quads x 16 row subsets for every level measured slower:
+// 139 against 116 us per launch.)
 constexpr int BT_GQ = 8;
 constexpr int BT_GMAX = 4;
 constexpr int BT_MAX_M = 4 * BT_GQ * BT_GMAX * BT_NW;     // 1536
@@ -255,6 +256,87 @@ __device__ __forceinline__ void bt_quad_fma(const FW* p, const V s, Rt (&acc)[4]
         for (int c = 0; c < 4; ++c) {
             acc[c][0] += w[c] * s.x;
             acc[c][1] += w[c] * s.y;
+        }
+    }
+}
+
+// (b2)+(b3) of a level step: y = W_l^T s over the rows [ra, rb) of W_l that
+// this rank streams, then the step's output (forward: z_l, middle: this
+// rank's half of x_k, backward: x_l = z_l - y).  Warp w owns the quad groups
+// g = w, w + NW, ... (GQ output quads each, at most GMAX per warp); inside a
+// warp, lane = (row subset rs, quad qq): the GQ lanes of a subset read
+// 16 * GQ contiguous bytes of one W row and the NRS = 32 / GQ subsets take
+// every NRS-th row.  The subsets are summed with shuffles, so each output is
+// complete inside one warp: no cross-warp combine.  Every W tile of the step
+// is waited for and released by every consumer warp, whatever its share.
+template <int GQ, int GMAX, class V, class FW>
+__device__ __forceinline__ void bt_gemv(const BtStep& st, int m, int o, int ldm, int R, int ns, int slot_bytes,
+                                        const unsigned char* slots, uint64_t* full, uint64_t* empty, int& t,
+                                        const V* su, V* vec, V* tx, V* pry, int warp, int lane, volatile int* abort,
+                                        int* err, unsigned long long wait_ns) {
+    using Rt = typename VT<V>::R;
+    constexpr int NRS = 32 / GQ;
+    const int nq = ldm / 4;
+    const int ngr = (nq + GQ - 1) / GQ;
+    const int rs = lane / GQ, qq = lane % GQ;
+    Rt acc[GMAX][4][2];
+#pragma unroll
+    for (int u = 0; u < GMAX; ++u)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[u][c][0] = acc[u][c][1] = 0;
+    for (int r0 = st.ra; r0 < st.rb; r0 += R) {
+        const int q = t % ns;
+        bt_wait<false>(&full[q], (unsigned)((t / ns) & 1), abort, err, wait_ns);
+        const FW* Wt = reinterpret_cast<const FW*>(slots + (size_t)q * slot_bytes);
+        const int nr = min(R, st.rb - r0);
+#pragma unroll
+        for (int u = 0; u < GMAX; ++u) {
+            const int quad = (warp + u * BT_NW) * GQ + qq;
+            if (warp + u * BT_NW < ngr && quad < nq) {
+                const FW* wc = Wt + 4 * quad;
+                int jj = rs;
+                // four rows per pass: their loads are independent
+                for (; jj + 3 * NRS < nr; jj += 4 * NRS) {
+                    V sj[4];
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) sj[r] = su[r0 + jj + NRS * r];
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) bt_quad_fma<FW, Rt, V>(wc + (size_t)(jj + NRS * r) * ldm, sj[r], acc[u]);
+                }
+                for (; jj < nr; jj += NRS) bt_quad_fma<FW, Rt, V>(wc + (size_t)jj * ldm, su[r0 + jj], acc[u]);
+            }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive_local(&empty[q]);
+        ++t;
+    }
+    // sum the row subsets and write each output from the lane of subset 0
+#pragma unroll
+    for (int u = 0; u < GMAX; ++u) {
+        if (warp + u * BT_NW >= ngr) break;              // uniform across the warp
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+            for (int z = 0; z < 2; ++z)
+#pragma unroll
+                for (int sh = GQ; sh < 32; sh <<= 1) acc[u][c][z] += __shfl_xor_sync(0xffffffffu, acc[u][c][z], sh);
+        const int quad = (warp + u * BT_NW) * GQ + qq;
+        if (rs == 0 && quad < nq) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int i = 4 * quad + c;
+                if (i >= m) break;
+                const V yv = mk<V>(acc[u][c][0], acc[u][c][1]);
+                if (st.kind == 0) {
+                    vec[o + i] = yv;
+                } else if (st.kind == 1) {
+                    tx[i] = yv;
+                    pry[i] = yv;
+                } else {
+                    const V z = vec[o + i];
+                    vec[o + i] = mk<V>(z.x - yv.x, z.y - yv.y);
+                }
+            }
         }
     }
 }
@@ -499,79 +581,17 @@ k_bt_solve(const Sub* __restrict__ subs, const Level* __restrict__ levels, const
                 }
             }
             bt_bar_consumers();
-            // (b2) y = W_l^T s over the rows [ra, rb) this rank streams.  Warp w
-            // owns the quad groups g = w, w + NW, ... (GQ = 8 output quads
-            // each); inside a warp, lane = (row subset rs, quad qq): the 8
-            // lanes of a subset read 128 contiguous bytes of one W row (no
-            // bank conflicts whatever the row stride) and the NRS = 4 subsets
-            // take every 4th row.  The subsets are summed with shuffles, so
-            // each output is complete inside one warp: no cross-warp combine.
-            constexpr int GQ = BT_GQ, GMAX = BT_GMAX;
-            constexpr int NRS = 32 / GQ;
-            const int nq = ldm / 4;
-            const int ngr = (nq + GQ - 1) / GQ;
-            const int rs = lane / GQ, qq = lane % GQ;
-            Rt acc[GMAX][4][2];
-#pragma unroll
-            for (int u = 0; u < GMAX; ++u)
-#pragma unroll
-                for (int c = 0; c < 4; ++c) acc[u][c][0] = acc[u][c][1] = 0;
-            for (int r0 = st.ra; r0 < st.rb; r0 += R) {
-                const int q = t % ns;
-                bt_wait<false>(&full[q], (unsigned)((t / ns) & 1), abort, err, wait_ns);
-                const FW* Wt = reinterpret_cast<const FW*>(slots + (size_t)q * slot_bytes);
-                const int nr = min(R, st.rb - r0);
-#pragma unroll
-                for (int u = 0; u < GMAX; ++u) {
-                    const int quad = (warp + u * BT_NW) * GQ + qq;
-                    if (warp + u * BT_NW < ngr && quad < nq) {
-                        const FW* wc = Wt + 4 * quad;
-                        int jj = rs;
-                        // four rows per pass: their loads are independent
-                        for (; jj + 3 * NRS < nr; jj += 4 * NRS) {
-                            V sj[4];
-#pragma unroll
-                            for (int r = 0; r < 4; ++r) sj[r] = su[r0 + jj + NRS * r];
-#pragma unroll
-                            for (int r = 0; r < 4; ++r)
-                                bt_quad_fma<FW, Rt, V>(wc + (size_t)(jj + NRS * r) * ldm, sj[r], acc[u]);
-                        }
-                        for (; jj < nr; jj += NRS) bt_quad_fma<FW, Rt, V>(wc + (size_t)jj * ldm, su[r0 + jj], acc[u]);
-                    }
-                }
-                __syncwarp();
-                if (lane == 0) mbar_arrive_local(&empty[q]);
-                ++t;
-            }
-            // (b3) sum the 4 row subsets and write each output from the lane of subset 0
-#pragma unroll
-            for (int u = 0; u < GMAX; ++u) {
-                if (warp + u * BT_NW >= ngr) break;              // uniform across the warp
-#pragma unroll
-                for (int c = 0; c < 4; ++c)
-#pragma unroll
-                    for (int z = 0; z < 2; ++z)
-#pragma unroll
-                        for (int o = GQ; o < 32; o <<= 1) acc[u][c][z] += __shfl_xor_sync(0xffffffffu, acc[u][c][z], o);
-                const int quad = (warp + u * BT_NW) * GQ + qq;
-                if (rs == 0 && quad < nq) {
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        const int i = 4 * quad + c;
-                        if (i >= m) break;
-                        const V yv = mk<V>(acc[u][c][0], acc[u][c][1]);
-                        if (st.kind == 0) {
-                            vec[o + i] = yv;
-                        } else if (st.kind == 1) {
-                            tx[i] = yv;
-                            pry[i] = yv;
-                        } else {
-                            const V z = vec[o + i];
-                            vec[o + i] = mk<V>(z.x - yv.x, z.y - yv.y);
-                        }
-                    }
-                }
-            }
+            // (b2)+(b3) y = W_l^T s over the rows [ra, rb) this rank streams:
+            // narrow levels (at most 48 quads, e.g. the 130-row levels of a
+            // 2-D order-2 subdomain) in groups of 4 quads with 8 row subsets,
+            // so that 9 of the 12 warps work on a 130-row level instead of 5
+            // (4 of them on a full group); wider ones in groups of 8 quads
+            if (ldm / 4 <= 4 * BT_NW)
+                bt_gemv<4, 1, V, FW>(st, m, o, ldm, R, ns, slot_bytes, slots, full, empty, t, su, vec, tx, pry, warp,
+                                     lane, abort, err, wait_ns);
+            else
+                bt_gemv<BT_GQ, BT_GMAX, V, FW>(st, m, o, ldm, R, ns, slot_bytes, slots, full, empty, t, su, vec, tx,
+                                               pry, warp, lane, abort, err, wait_ns);
             if (st.kind == 1) {
                 // x_k = own half + the peer's half (both complete once every
                 // warp of both CTAs has written its outputs)
@@ -611,9 +631,11 @@ k_bt_solve(const Sub* __restrict__ subs, const Level* __restrict__ levels, const
                 }
 #pragma unroll
                 for (int a = 0; a < 8; ++a) {
+                    // the value is loaded whatever the index (it is masked
+                    // below), so that both loads are in flight together
                     const int64_t e = ok ? (int64_t)ei[a * n_loc + b] : -1;
                     eix[r][a] = (e >= S.off && e < S.off + S.ne) ? (int32_t)e : -1;
-                    ec[r][a] = eix[r][a] >= 0 ? (Rt)ev[a * n_loc + b] : (Rt)0;
+                    ec[r][a] = ok ? (Rt)ev[a * n_loc + b] : (Rt)0;
                 }
             }
 #pragma unroll
