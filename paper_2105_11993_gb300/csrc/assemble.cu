@@ -613,9 +613,11 @@ __device__ __forceinline__ int ld4(int m) { return (m + 3) / 4 * 4; }
 // level l to the already-eliminated neighbour n, taken from the level's sparse
 // coupling list (side 0: n = l-1, side 1: n = l+1; a few entries per row):
 //   T = C W_n  (m_l x m_n, row stride m_n),   W[i][j] -= sum_q T[i][c_q] C[j][c_q].
+// T is also the transpose of the neighbour's backward-sweep product
+// (H_n = W_n C^T, W_n symmetric), kept at Hn (stride r4(m_n)).
 __device__ void schur_update(const Level& L, const Level& N, int side, double* W, const double* Wn, double* tT,
                              const int32_t* __restrict__ cptr, const int32_t* __restrict__ ccol,
-                             const double* __restrict__ cval) {
+                             const double* __restrict__ cval, double* Hn) {
     const int32_t* P = cptr + (side == 0 ? L.eptr : L.fptr);
     const int32_t* Cc = ccol + (side == 0 ? L.eoff : L.foff);
     const double* Cv = cval + (side == 0 ? L.eoff : L.foff);
@@ -625,7 +627,10 @@ __device__ void schur_update(const Level& L, const Level& N, int side, double* W
         double acc = 0;
         for (int p = P[i]; p < P[i + 1]; ++p) acc += Cv[p] * Wn[(int64_t)Cc[p] * ldn + j];
         tT[t] = acc;
+        Hn[(int64_t)i * ldn + j] = acc;
     }
+    for (int64_t t = threadIdx.x; t < (int64_t)ml * (ldn - mn); t += blockDim.x)   // row padding
+        Hn[(t / (ldn - mn)) * ldn + mn + t % (ldn - mn)] = 0;
     __syncthreads();
     for (int64_t t = threadIdx.x; t < (int64_t)ml * ml; t += blockDim.x) {
         const int i = (int)(t / ml), j = (int)(t % ml);
@@ -660,11 +665,11 @@ __global__ void k_bt_factor(int mid, const Sub* __restrict__ subs, const Level* 
         extract_block(L, L.start, L.size, W, ld4(L.size), slice_ptr, col, pad, sval);
         if (k > 0) {
             const Level N = levels[S.lev0 + k - 1];
-            schur_update(L, N, 0, W, fac + N.offW, tT, cptr, ccol, cval);
+            schur_update(L, N, 0, W, fac + N.offW, tT, cptr, ccol, cval, fac + N.offH);
         }
         if (k + 1 < S.nlev) {
             const Level N = levels[S.lev0 + k + 1];
-            schur_update(L, N, 1, W, fac + N.offW, tT, cptr, ccol, cval);
+            schur_update(L, N, 1, W, fac + N.offW, tT, cptr, ccol, cval, fac + N.offH);
         }
         if (!cta_gauss_jordan(W, L.size, ld4(L.size), perm, fcol, rv, ri) && threadIdx.x == 0) atomicExch(status, 1);
         return;
@@ -677,7 +682,7 @@ __global__ void k_bt_factor(int mid, const Sub* __restrict__ subs, const Level* 
         extract_block(L, L.start, L.size, W, ld4(L.size), slice_ptr, col, pad, sval);
         if (q > 0) {
             const Level N = levels[S.lev0 + (chain == 0 ? l - 1 : l + 1)];
-            schur_update(L, N, chain == 0 ? 0 : 1, W, fac + N.offW, tT, cptr, ccol, cval);
+            schur_update(L, N, chain == 0 ? 0 : 1, W, fac + N.offW, tT, cptr, ccol, cval, fac + N.offH);
         }
         if (!cta_gauss_jordan(W, L.size, ld4(L.size), perm, fcol, rv, ri)) {
             if (threadIdx.x == 0) atomicExch(status, 1);
@@ -803,7 +808,7 @@ __device__ void extract_block_c(const Level& L, double2* dst, int ld, const int6
 // W (complex, m_l x r4(m_l)) -= C W_n C^T with the real coupling list C
 __device__ void schur_update_c(const Level& L, const Level& N, int side, double2* W, const double2* Wn, double2* tT,
                                const int32_t* __restrict__ cptr, const int32_t* __restrict__ ccol,
-                               const double* __restrict__ cval) {
+                               const double* __restrict__ cval, double2* Hn) {
     const int32_t* P = cptr + (side == 0 ? L.eptr : L.fptr);
     const int32_t* Cc = ccol + (side == 0 ? L.eoff : L.foff);
     const double* Cv = cval + (side == 0 ? L.eoff : L.foff);
@@ -817,7 +822,10 @@ __device__ void schur_update_c(const Level& L, const Level& N, int side, double2
             acc.y += Cv[p] * wv.y;
         }
         tT[t] = acc;
+        Hn[(int64_t)i * ldn + j] = acc;          // H_n^T, as in schur_update
     }
+    for (int64_t t = threadIdx.x; t < (int64_t)ml * (ldn - mn); t += blockDim.x)
+        Hn[(t / (ldn - mn)) * ldn + mn + t % (ldn - mn)] = make_double2(0, 0);
     __syncthreads();
     for (int64_t t = threadIdx.x; t < (int64_t)ml * ml; t += blockDim.x) {
         const int i = (int)(t / ml), j = (int)(t % ml);
@@ -857,11 +865,11 @@ __global__ void k_bt_factor_c(int mid, const Sub* __restrict__ subs, const Level
         extract_block_c(L, W, ld4(L.size), slice_ptr, col, pad, sval, bg, bs);
         if (k > 0) {
             const Level N = levels[S.lev0 + k - 1];
-            schur_update_c(L, N, 0, W, fac + N.offW, tT, cptr, ccol, cval);
+            schur_update_c(L, N, 0, W, fac + N.offW, tT, cptr, ccol, cval, fac + N.offH);
         }
         if (k + 1 < S.nlev) {
             const Level N = levels[S.lev0 + k + 1];
-            schur_update_c(L, N, 1, W, fac + N.offW, tT, cptr, ccol, cval);
+            schur_update_c(L, N, 1, W, fac + N.offW, tT, cptr, ccol, cval, fac + N.offH);
         }
         if (!cta_gauss_jordan_c(W, L.size, ld4(L.size), perm, fcol, rv, ri) && threadIdx.x == 0) atomicExch(status, 1);
         return;
@@ -874,7 +882,7 @@ __global__ void k_bt_factor_c(int mid, const Sub* __restrict__ subs, const Level
         extract_block_c(L, W, ld4(L.size), slice_ptr, col, pad, sval, bg, bs);
         if (q > 0) {
             const Level N = levels[S.lev0 + (chain == 0 ? l - 1 : l + 1)];
-            schur_update_c(L, N, chain == 0 ? 0 : 1, W, fac + N.offW, tT, cptr, ccol, cval);
+            schur_update_c(L, N, chain == 0 ? 0 : 1, W, fac + N.offW, tT, cptr, ccol, cval, fac + N.offH);
         }
         if (!cta_gauss_jordan_c(W, L.size, ld4(L.size), perm, fcol, rv, ri)) {
             if (threadIdx.x == 0) atomicExch(status, 1);

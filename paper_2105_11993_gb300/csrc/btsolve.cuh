@@ -16,10 +16,12 @@
 //   middle, both ranks:    x_k = W_k (r_k - E_k z_{k-1} - F_k z_{k+1})
 //                          (each rank forms its own coupling term and half of
 //                           the product; the halves meet through DSMEM)
-//   rank 0, l = k-1..0:    x_l = z_l - W_l F_l x_{l+1}
-//   rank 1, l = k+1..L-1:  x_l = z_l - W_l E_l x_{l-1}
+//   rank 0, l = k-1..0:    x_l = z_l - H_l x_{l+1},   H_l = W_l F_l
+//   rank 1, l = k+1..L-1:  x_l = z_l - H_l x_{l-1},   H_l = W_l E_l
 // so each SM streams half of the factor and the dependent chain is half as
-// long as a one-sided sweep.
+// long as a one-sided sweep.  The dense H_l (stored transposed; the
+// factorisation forms them in its Schur updates) make a backward step one
+// GEMV with no sparse coupling phase, for as many bytes as W_l would stream.
 //
 // Per CTA, one producer warp streams the tiles (the coupling CSR block of a
 // step, then row tiles of W_l) with 1-D TMA bulk copies into two rings of
@@ -37,6 +39,7 @@
 #pragma once
 
 #include <cooperative_groups.h>
+#include <type_traits>
 
 #include "kernels.cuh"
 
@@ -45,11 +48,14 @@ namespace thm {
 constexpr int BT_NT = 384;                  // consumer threads
 constexpr int BT_NW = BT_NT / 32;           // consumer warps
 constexpr int BT_THREADS = BT_NT + 32;      // + one producer warp
-// GEMV layout of wide levels: a warp pass covers GQ = 8 output quads with 4
-// row subsets, and a warp holds at most GMAX quad groups, so
-// m_l <= 4 * GQ * GMAX * BT_NW.  (Levels of at most 48 quads take 4 quads with
-// 8 row subsets; 2 quads x 16 row subsets for every level measured slower:
-// 139 against 116 us per launch.)
+// GEMV layout: a warp pass covers GQ = 8 output quads with 4 row subsets, and
+// a warp holds at most GMAX quad groups, so m_l <= 4 * GQ * GMAX * BT_NW.  The
+// 8 lanes of a quarter-warp read 128 contiguous bytes of one W row, so the
+// loads are free of bank conflicts whatever the row stride.  Narrower groups
+// keep more warps busy on 130-row levels but measured slower: 4 quads x 8 row
+// subsets 2024 against 1687 cycles per 130 x 132 tile alone (two rows 16 B
+// apart meet in the banks of one quarter-warp), 2 quads x 16 subsets 139
+// against 116 us per launch.
 constexpr int BT_GQ = 8;
 constexpr int BT_GMAX = 4;
 constexpr int BT_MAX_M = 4 * BT_GQ * BT_GMAX * BT_NW;     // 1536
@@ -61,10 +67,11 @@ __host__ __device__ constexpr int bt_r4(int v) { return (v + 3) / 4 * 4; }
 __host__ __device__ constexpr size_t bt_r16(size_t v) { return (v + 15) / 16 * 16; }
 
 // One step of a rank's chain: level l, coupling block (0 none, 1 E_l to
-// level l-1, 2 F_l to level l+1), rows [ra, rb) of W_l that this rank
-// streams, and the kind (0 forward, 1 middle, 2 backward).
+// level l-1, 2 F_l to level l+1), the rows [ra, rb) this rank streams (of W_l;
+// of H_l^T on a backward step, whose rows belong to the level nb it comes
+// from), and the kind (0 forward, 1 middle, 2 backward).
 struct BtStep {
-    int l, cpl, ra, rb, kind;
+    int l, cpl, ra, rb, kind, nb;
 };
 
 __device__ __forceinline__ int bt_nsteps(int rank, int L, int k) { return 2 * (rank == 0 ? k : L - 1 - k) + 1; }
@@ -84,8 +91,9 @@ __device__ __forceinline__ BtStep bt_step(int rank, int L, int k, int i, const L
         s.kind = 2;
         const int d = i - nf;
         s.l = rank == 0 ? k - d : k + d;
-        s.cpl = rank == 0 ? 2 : 1;
+        s.cpl = 0;
     }
+    s.nb = rank == 0 ? s.l + 1 : s.l - 1;        // the backward step's input level
     const int m = lv[s.l].size;
     if (s.kind == 1) {
         const int h = m / 2;
@@ -93,7 +101,7 @@ __device__ __forceinline__ BtStep bt_step(int rank, int L, int k, int i, const L
         s.rb = rank == 0 ? h : m;
     } else {
         s.ra = 0;
-        s.rb = m;
+        s.rb = s.kind == 2 ? lv[s.nb].size : m;
     }
     return s;
 }
@@ -260,6 +268,25 @@ __device__ __forceinline__ void bt_quad_fma(const FW* p, const V s, Rt (&acc)[4]
     }
 }
 
+// shared-memory loads by 32-bit shared-window address
+__device__ __forceinline__ float4 bt_lds128(uint32_t a) {
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];\n" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ float2 bt_lds64(uint32_t a) {
+    float2 v;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];\n" : "=f"(v.x), "=f"(v.y) : "r"(a) : "memory");
+    return v;
+}
+// acc[c] += w[c] * s for the four entries of one W quad (FP32)
+__device__ __forceinline__ void bt_fma4(const float4 w, const float2 sv, float (&acc)[4][2]) {
+    acc[0][0] = fmaf(w.x, sv.x, acc[0][0]); acc[0][1] = fmaf(w.x, sv.y, acc[0][1]);
+    acc[1][0] = fmaf(w.y, sv.x, acc[1][0]); acc[1][1] = fmaf(w.y, sv.y, acc[1][1]);
+    acc[2][0] = fmaf(w.z, sv.x, acc[2][0]); acc[2][1] = fmaf(w.z, sv.y, acc[2][1]);
+    acc[3][0] = fmaf(w.w, sv.x, acc[3][0]); acc[3][1] = fmaf(w.w, sv.y, acc[3][1]);
+}
+
 // (b2)+(b3) of a level step: y = W_l^T s over the rows [ra, rb) of W_l that
 // this rank streams, then the step's output (forward: z_l, middle: this
 // rank's half of x_k, backward: x_l = z_l - y).  Warp w owns the quad groups
@@ -293,40 +320,81 @@ __device__ __forceinline__ void bt_gemv(const BtStep& st, int m, int o, int ldm,
         for (int u = 0; u < GMAX; ++u) {
             const int quad = (warp + u * BT_NW) * GQ + qq;
             if (warp + u * BT_NW < ngr && quad < nq) {
-                const FW* wc = Wt + 4 * quad;
-                int jj = rs;
-                // four rows per pass: their loads are independent
-                for (; jj + 3 * NRS < nr; jj += 4 * NRS) {
-                    V sj[4];
+                if constexpr (std::is_same<FW, float>::value && std::is_same<V, float2>::value) {
+                    // real FP32 factors: 32-bit shared addresses stepped by
+                    // the row stride, ROWS rows per pass (their loads in flight together)
+                    constexpr int ROWS = 4;
+                    const uint32_t wstep = (uint32_t)NRS * 4u * (uint32_t)ldm, sstep = (uint32_t)NRS * 8u;
+                    uint32_t wa = smem_u32(Wt) + 16u * (uint32_t)quad + (uint32_t)rs * 4u * (uint32_t)ldm;
+                    uint32_t sa = smem_u32(su + r0) + (uint32_t)rs * 8u;
+                    int jj = rs;
+                    for (; jj + (ROWS - 1) * NRS < nr; jj += ROWS * NRS) {
+                        float4 wv[ROWS];
+                        float2 sv[ROWS];
 #pragma unroll
-                    for (int r = 0; r < 4; ++r) sj[r] = su[r0 + jj + NRS * r];
+                        for (int r = 0; r < ROWS; ++r) {
+                            sv[r] = bt_lds64(sa + (uint32_t)r * sstep);
+                            wv[r] = bt_lds128(wa + (uint32_t)r * wstep);
+                        }
 #pragma unroll
-                    for (int r = 0; r < 4; ++r) bt_quad_fma<FW, Rt, V>(wc + (size_t)(jj + NRS * r) * ldm, sj[r], acc[u]);
+                        for (int r = 0; r < ROWS; ++r) bt_fma4(wv[r], sv[r], acc[u]);
+                        wa += (uint32_t)ROWS * wstep;
+                        sa += (uint32_t)ROWS * sstep;
+                    }
+                    for (; jj < nr; jj += NRS, wa += wstep, sa += sstep) bt_fma4(bt_lds128(wa), bt_lds64(sa), acc[u]);
+                } else {
+                    const FW* wc = Wt + 4 * quad;
+                    int jj = rs;
+                    // four rows per pass: their loads are independent
+                    for (; jj + 3 * NRS < nr; jj += 4 * NRS) {
+                        V sj[4];
+#pragma unroll
+                        for (int r = 0; r < 4; ++r) sj[r] = su[r0 + jj + NRS * r];
+#pragma unroll
+                        for (int r = 0; r < 4; ++r)
+                            bt_quad_fma<FW, Rt, V>(wc + (size_t)(jj + NRS * r) * ldm, sj[r], acc[u]);
+                    }
+                    for (; jj < nr; jj += NRS) bt_quad_fma<FW, Rt, V>(wc + (size_t)jj * ldm, su[r0 + jj], acc[u]);
                 }
-                for (; jj < nr; jj += NRS) bt_quad_fma<FW, Rt, V>(wc + (size_t)jj * ldm, su[r0 + jj], acc[u]);
             }
         }
         __syncwarp();
         if (lane == 0) mbar_arrive_local(&empty[q]);
         ++t;
     }
-    // sum the row subsets and write each output from the lane of subset 0
+    // sum the row subsets by recursive halving over the lanes qq + GQ * rs of
+    // a quad: each of the log2(NRS) shuffle rounds halves the values a lane
+    // carries (6 shuffles per group instead of 16), and lane (rs, qq) ends
+    // with values 2 rs and 2 rs + 1 of its quad, value 2c + z being
+    // component z of output 4 quad + c: both components of output rs
+    static_assert(GQ == 8, "the halving leaves two values (one output) per lane");
 #pragma unroll
     for (int u = 0; u < GMAX; ++u) {
         if (warp + u * BT_NW >= ngr) break;              // uniform across the warp
+        Rt a[8];
 #pragma unroll
-        for (int c = 0; c < 4; ++c)
+        for (int c = 0; c < 4; ++c) {
+            a[2 * c] = acc[u][c][0];
+            a[2 * c + 1] = acc[u][c][1];
+        }
+        int n = 8;
 #pragma unroll
-            for (int z = 0; z < 2; ++z)
+        for (int off = 16; off >= GQ; off >>= 1, n >>= 1) {
+            const bool up = (lane & off) != 0;
 #pragma unroll
-                for (int sh = GQ; sh < 32; sh <<= 1) acc[u][c][z] += __shfl_xor_sync(0xffffffffu, acc[u][c][z], sh);
+            for (int i = 0; i < 4; ++i) {
+                if (i < n / 2) {
+                    const Rt send = up ? a[i] : a[i + n / 2];
+                    const Rt keep = up ? a[i + n / 2] : a[i];
+                    a[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+                }
+            }
+        }
         const int quad = (warp + u * BT_NW) * GQ + qq;
-        if (rs == 0 && quad < nq) {
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const int i = 4 * quad + c;
-                if (i >= m) break;
-                const V yv = mk<V>(acc[u][c][0], acc[u][c][1]);
+        if (quad < nq) {
+            const int i = 4 * quad + rs;                     // both components of output rs of the quad
+            if (i < m) {
+                const V yv = mk<V>(a[0], a[1]);
                 if (st.kind == 0) {
                     vec[o + i] = yv;
                 } else if (st.kind == 1) {
@@ -442,7 +510,7 @@ k_bt_solve(const Sub* __restrict__ subs, const Level* __restrict__ levels, const
                     const unsigned wb = (unsigned)((size_t)nr * ldm * sizeof(FW));
                     if (stall_w) continue;           // failure-detection test: the W tiles never come
                     mbar_expect_tx(&full[q], wb);
-                    tma_load_1d(dst, fac + Lv.offW + (int64_t)r0 * ldm, wb, &full[q]);
+                    tma_load_1d(dst, fac + (st.kind == 2 ? Lv.offH : Lv.offW) + (int64_t)r0 * ldm, wb, &full[q]);
                 }
             }
             // let every issued copy land before the CTA may leave
@@ -502,8 +570,10 @@ k_bt_solve(const Sub* __restrict__ subs, const Level* __restrict__ levels, const
         for (int si = 0; si < nst; ++si) {
             const BtStep st = bt_step(rank, L, k, si, lv);
             const int m = lv[st.l].size, o = lv[st.l].start - vbase, ldm = bt_r4(m);
-            // (b1) coupling term of the step
-            if (st.cpl) {
+            // (b1) coupling term of the step (a backward step has none: its
+            // GEMV input is x of level nb, final since the previous step)
+            if (st.kind == 2) {
+            } else if (st.cpl) {
                 const int q = tc % BT_NC;
                 const int nb = st.cpl == 1 ? st.l - 1 : st.l + 1;
                 const int ob = lv[nb].start - vbase;
@@ -548,11 +618,9 @@ k_bt_solve(const Sub* __restrict__ subs, const Level* __restrict__ levels, const
                     if (st.kind == 0) {
                         const V r = vec[o + i];
                         su[i] = mk<V>(r.x - ar, r.y - aim);
-                    } else if (st.kind == 1) {
+                    } else {
                         tx[i] = mk<V>(ar, aim);
                         prx[i] = mk<V>(ar, aim);
-                    } else {
-                        su[i] = mk<V>(ar, aim);
                     }
                 }
                 if (!cglob) {
@@ -580,18 +648,12 @@ k_bt_solve(const Sub* __restrict__ subs, const Level* __restrict__ levels, const
                     su[i] = mk<V>(r.x - a.x - b.x, r.y - a.y - b.y);
                 }
             }
-            bt_bar_consumers();
-            // (b2)+(b3) y = W_l^T s over the rows [ra, rb) this rank streams:
-            // narrow levels (at most 48 quads, e.g. the 130-row levels of a
-            // 2-D order-2 subdomain) in groups of 4 quads with 8 row subsets,
-            // so that 9 of the 12 warps work on a 130-row level instead of 5
-            // (4 of them on a full group); wider ones in groups of 8 quads
-            if (ldm / 4 <= 4 * BT_NW)
-                bt_gemv<4, 1, V, FW>(st, m, o, ldm, R, ns, slot_bytes, slots, full, empty, t, su, vec, tx, pry, warp,
-                                     lane, abort, err, wait_ns);
-            else
-                bt_gemv<BT_GQ, BT_GMAX, V, FW>(st, m, o, ldm, R, ns, slot_bytes, slots, full, empty, t, su, vec, tx,
-                                               pry, warp, lane, abort, err, wait_ns);
+            if (st.kind != 2) bt_bar_consumers();
+            // (b2)+(b3) y = W_l^T s (forward, middle) or H_l x_nb (backward) over
+            // the rows [ra, rb) this rank streams
+            const V* sin = st.kind == 2 ? vec + (lv[st.nb].start - vbase) : su;
+            bt_gemv<BT_GQ, BT_GMAX, V, FW>(st, m, o, ldm, R, ns, slot_bytes, slots, full, empty, t, sin, vec, tx, pry,
+                                           warp, lane, abort, err, wait_ns);
             if (st.kind == 1) {
                 // x_k = own half + the peer's half (both complete once every
                 // warp of both CTAs has written its outputs)

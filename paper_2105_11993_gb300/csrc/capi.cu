@@ -417,18 +417,14 @@ int thm_alg_bytes(const thm_sys* s, int mode, int cls, double* bytes) {
             for (uint8_t p : m->sell_pad) nnz += !p;
             *bytes = nnz * bv + 2.0 * m->n_loc * bv + 2.0 * m->n_loc * bx;
         } else if (cls == THM_K_PINV) {
-            double w = 0, cpl = 0, ne = 0, nb = 0;
+            double w = 0, ne = 0, nb = 0;
             for (const auto& S : m->subs) {
-                for (int l = 0; l < S.nlev; ++l) {
-                    const Level& L = m->levels[S.lev0 + l];
-                    w += (double)L.size * L.size * (l == S.kmid ? 1 : 2);   // the middle level once
-                    cpl += L.enz + L.fnz;
-                }
+                w += (double)bt_stream_values(S, m->levels.data());
                 ne += (double)S.ne;
                 nb += (double)(S.n - S.ne);
             }
             double tab = m->order == 2 ? (8 * ne + 12 * nb) : 0;
-            *bytes = (w + cpl + tab) * bv + 2.0 * m->n_loc * bx;
+            *bytes = (w + tab) * bv + 2.0 * m->n_loc * bx;
         } else {
             fail(THM_EINVAL, "no byte model for this kernel class");
         }

@@ -91,6 +91,9 @@ struct Level {
     int32_t prev;     // m_{l-1} (0 for the first level of a subdomain)
     int32_t next;     // m_{l+1} (0 for the last)
     int64_t offW;     // W_l = S_l^{-1}: m_l rows of stride r4(m_l) (16-byte aligned)
+    int64_t offH;     // H_l^T, the backward-sweep product (l != kmid): H_l = W_l F_l above the
+                      // middle level, W_l E_l below it; m_{l+1} resp. m_{l-1} rows of stride
+                      // r4(m_l), or -1 (16-byte aligned)
     // coupling blocks of S to level l-1 (E) and l+1 (F): m_l+1 row pointers
     // (0-based, at cpl_ptr[eptr..]) and nz (column local to the neighbour
     // level, value) entries at cpl_col/cpl_val[eoff..]; offsets 16-byte aligned
@@ -107,6 +110,23 @@ struct Sub {
     int32_t kmid;     // middle level of the twisted factorisation (0 <= kmid < nlev)
     int32_t pad_;
 };
+
+// Values one block solve streams for subdomain S (the byte model of the
+// block-solve kernel, in values): W_l once for every level (forward steps and
+// the middle level), H_l for every level but the middle (backward steps),
+// and the coupling lists of the forward and middle steps (E_1..E_k of the top
+// chain, F_k..F_{L-2} of the bottom one).
+inline int64_t bt_stream_values(const Sub& S, const Level* lv) {
+    int64_t w = 0;
+    for (int l = 0; l < S.nlev; ++l) {
+        const Level& L = lv[S.lev0 + l];
+        w += (int64_t)L.size * L.size;
+        if (l != S.kmid) w += (int64_t)L.size * (l < S.kmid ? L.next : L.prev);
+        if (l >= 1 && l <= S.kmid) w += L.enz;
+        if (l >= S.kmid && l + 1 < S.nlev) w += L.fnz;
+    }
+    return w;
+}
 
 // A contiguous piece of one segment, used for deterministic segmented reductions.
 struct Chunk {

@@ -588,6 +588,21 @@ void build_mesh(thm_mesh* m) {
             m->bt_nvec = std::max<int64_t>(m->bt_nvec, (int64_t)Le.start + Le.size - Lk.start);
         }
     }
+    // H_l^T after all W blocks: rows of the level the backward sweep comes
+    // from (l + 1 above the middle, l - 1 below it), stride r4(m_l)
+    for (int s = 0; s < ns; ++s) {
+        const auto& S = m->subs[s];
+        for (int l = 0; l < S.nlev; ++l) {
+            Level& L = m->levels[S.lev0 + l];
+            if (l == S.kmid) {
+                L.offH = -1;
+                continue;
+            }
+            const int nb = l < S.kmid ? L.next : L.prev;
+            L.offH = fo;
+            fo += (int64_t)nb * (((int64_t)L.size + 3) / 4 * 4);
+        }
+    }
     m->fac_elems = fo + 4;
 
     // ---- SELL-32 pattern
@@ -662,16 +677,12 @@ void build_mesh(thm_mesh* m) {
     pad4i(m->cpl_ptr);
     for (int k = 0; k < 8; ++k) { m->cpl_ptr.push_back(0); m->cpl_col.push_back(0); m->cpl_slot.push_back(-1); }
     // values one block solve reads per subdomain (the byte model of the
-    // block-solve kernel): W_l in both sweeps but the middle level once, the
-    // coupling lists, and the order-2 condensation tables
+    // block-solve kernel): the factor blocks and coupling lists it streams,
+    // and the order-2 condensation tables
     m->bt_welem.assign(ns, 0);
     for (int s = 0; s < ns; ++s) {
         const auto& S = m->subs[s];
-        int64_t w = 0;
-        for (int l = 0; l < S.nlev; ++l) {
-            const Level& L = m->levels[S.lev0 + l];
-            w += (int64_t)L.size * L.size * (l == S.kmid ? 1 : 2) + L.enz + L.fnz;
-        }
+        int64_t w = bt_stream_values(S, m->levels.data());
         if (m->order == 2) w += 8 * S.ne + 12 * (S.n - S.ne);
         m->bt_welem[s] = w;
     }

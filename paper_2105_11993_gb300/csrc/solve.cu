@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <functional>
+#include <string>
 
 #include "btsolve.cuh"
 #include "kernels.cuh"
@@ -67,59 +68,113 @@ struct GivensArgs {
     int* cnt;                  // per-segment arrival counters of the last-block reduction
 };
 
-// One warp: the column and the rotations are staged in shared memory by all
-// lanes; the rotations themselves run on lane 0.  hn2 = ||w||^2 of segment s.
-__device__ void givens_warp(const GivensArgs& ga, int s, double hn2, unsigned char* scratch) {
-    const int j = ga.j, m = ga.m;
-    double2* col = reinterpret_cast<double2*>(scratch);      // [j+1]
-    double2* sg = col + (j + 1);                              // [j]
-    double* c = reinterpret_cast<double*>(sg + j);            // [j]
+__device__ __forceinline__ double2 gv_mul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 gv_fma(double2 a, double2 b, double2 c) {     // a * b + c
+    return make_double2(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
+}
+
+// One warp.  Applying the previous rotations to the new column is a chain:
+// with a_0 = h_0 and, for i < j,
+//     r_i     = c_i a_i + s_i h_{i+1}               (entry i of the rotated column)
+//     a_{i+1} = -conj(s_i) a_i + c_i h_{i+1}         (carried into rotation i + 1)
+// the carry follows the affine maps a -> A_i a + B_i (A_i = -conj(s_i),
+// B_i = c_i h_{i+1}), which compose associatively.  Each lane composes the
+// maps of its range of i, a shuffle scan gives every lane the composition of
+// the ranges below it (so its incoming carry), and the lanes then walk their
+// ranges in parallel.  FP64 instructions cost a full warp slot on this part
+// whatever the active lanes, so the serial chain of about 12 of them per
+// rotation on one lane becomes about (j / 32) * 16 + 5 * 8 per lane.
+// Column j of segment s: hin[0..j] (shared memory, unrotated), hn = the
+// subdiagonal entry (||w||); the rotated column goes to col[0..j] (shared
+// memory, another array) and to R.  stop: the segment stops after this
+// column whatever its residual (the last column of a cycle).
+__device__ bool givens_core(const GivensArgs& ga, int s, int j, const double2* hin, double hn, double2* col,
+                            bool stop = false) {
+    const int m = ga.m;
     const int lane = threadIdx.x & 31;
-    for (int i = lane; i <= j; i += 32) col[i] = cadd(ga.h1[(int64_t)s * ga.ldh + i], ga.h2[(int64_t)s * ga.ldh + i]);
-    for (int i = lane; i < j; i += 32) { c[i] = ga.cs[(int64_t)s * m + i]; sg[i] = ga.sn[(int64_t)s * m + i]; }
-    __syncwarp();
-    if (lane == 0) {
-        const double hn = sqrt(hn2);
-        if (!isfinite(hn)) {
+    if (!isfinite(hn)) {
+        if (lane == 0) {
             atomicExch(ga.flag, 1);
             ga.active[s] = 0;
             ga.beta[s] = 0.0;
-        } else {
-            for (int i = 0; i < j; ++i) {
-                double2 a = col[i], b = col[i + 1];
-                // [a; b] <- [[c, s], [-conj(s), c]] [a; b]
-                col[i] = make_double2(c[i] * a.x + sg[i].x * b.x - sg[i].y * b.y, c[i] * a.y + sg[i].x * b.y + sg[i].y * b.x);
-                col[i + 1] = make_double2(-(sg[i].x * a.x + sg[i].y * a.y) + c[i] * b.x, -(sg[i].x * a.y - sg[i].y * a.x) + c[i] * b.y);
-            }
-            double2 a = col[j];
-            double am = hypot(a.x, a.y);
-            double d = hypot(am, hn);
-            double cj;
-            double2 sj;
-            if (d == 0.0) { cj = 1.0; sj = make_double2(0, 0); }
-            else if (am == 0.0) { cj = 0.0; sj = make_double2(1.0, 0.0); }
-            else {
-                cj = am / d;
-                sj = make_double2(a.x / am * hn / d, a.y / am * hn / d);      // (a/|a|) conj(hn)/d
-            }
-            ga.cs[(int64_t)s * m + j] = cj;
-            ga.sn[(int64_t)s * m + j] = sj;
-            col[j] = make_double2(cj * a.x + sj.x * hn, cj * a.y + sj.y * hn);
-            double2* g = ga.gv + (int64_t)s * (m + 1);
-            double2 gj = g[j];
-            g[j + 1] = make_double2(-(sj.x * gj.x + sj.y * gj.y), -(sj.x * gj.y - sj.y * gj.x));   // -conj(s) g_j
-            g[j] = make_double2(cj * gj.x, cj * gj.y);
-            if (ga.gmon && s == 0) *ga.gmon = g[j + 1];
-            ga.kused[s] = j + 1;
-            ga.beta[s] = hn;
-            double res = hypot(g[j + 1].x, g[j + 1].y);
-            if (res <= ga.target[s] || hn == 0.0) ga.active[s] = 0;
-            else atomicAdd(ga.nact, 1);
         }
+        return false;
+    }
+    const double* cs = ga.cs + (int64_t)s * m;
+    const double2* sn = ga.sn + (int64_t)s * m;
+    const double2 h0 = hin[0];
+    const int per = (j + 31) / 32;
+    const int b = min(j, lane * per), e = min(j, b + per);
+    // this lane's maps composed: (A, B) = M_{e-1} o ... o M_b
+    double2 A = make_double2(1, 0), B = make_double2(0, 0);
+    for (int i = b; i < e; ++i) {
+        const double2 Ai = make_double2(-sn[i].x, sn[i].y);
+        const double2 hi1 = hin[i + 1];
+        const double2 Bi = make_double2(cs[i] * hi1.x, cs[i] * hi1.y);
+        B = gv_fma(Ai, B, Bi);
+        A = gv_mul(Ai, A);
+    }
+    // inclusive scan over the lanes: (A, B) <- (A, B) o (A, B) of lane - d
+    for (int d = 1; d < 32; d <<= 1) {
+        const double2 Ao = make_double2(__shfl_up_sync(0xffffffffu, A.x, d), __shfl_up_sync(0xffffffffu, A.y, d));
+        const double2 Bo = make_double2(__shfl_up_sync(0xffffffffu, B.x, d), __shfl_up_sync(0xffffffffu, B.y, d));
+        if (lane >= d) {
+            B = gv_fma(A, Bo, B);
+            A = gv_mul(A, Ao);
+        }
+    }
+    // exclusive prefix: the composition of the lanes below
+    double2 Ae = make_double2(__shfl_up_sync(0xffffffffu, A.x, 1), __shfl_up_sync(0xffffffffu, A.y, 1));
+    double2 Be = make_double2(__shfl_up_sync(0xffffffffu, B.x, 1), __shfl_up_sync(0xffffffffu, B.y, 1));
+    if (lane == 0) { Ae = make_double2(1, 0); Be = make_double2(0, 0); }
+    double2 a = gv_fma(Ae, h0, Be);                 // a_b
+    for (int i = b; i < e; ++i) {
+        const double c = cs[i];
+        const double2 si = sn[i];
+        const double2 hi1 = hin[i + 1];
+        col[i] = gv_fma(si, hi1, make_double2(c * a.x, c * a.y));
+        a = gv_fma(make_double2(-si.x, si.y), a, make_double2(c * hi1.x, c * hi1.y));
+    }
+    // a_j: the carry out of the last non-empty range (h_0 when j = 0)
+    const int last = j > 0 ? (j - 1) / per : 0;
+    a = make_double2(__shfl_sync(0xffffffffu, a.x, last), __shfl_sync(0xffffffffu, a.y, last));
+    if (j == 0) a = h0;
+    // the new rotation, from (a_j, ||w||): c = |a| / d, s = (a / |a|) ||w|| / d, d = sqrt(|a|^2 + ||w||^2)
+    const double n2a = a.x * a.x + a.y * a.y, d2 = n2a + hn * hn;
+    double cj;
+    double2 sj;
+    if (d2 == 0.0) { cj = 1.0; sj = make_double2(0, 0); }
+    else if (n2a == 0.0) { cj = 0.0; sj = make_double2(1.0, 0.0); }
+    else {
+        const double ia = rsqrt(n2a), id = rsqrt(d2);
+        cj = n2a * ia * id;
+        const double f = hn * ia * id;
+        sj = make_double2(a.x * f, a.y * f);
+    }
+    int keep = 0;
+    if (lane == 0) {
+        ga.cs[(int64_t)s * m + j] = cj;
+        ga.sn[(int64_t)s * m + j] = sj;
+        col[j] = make_double2(cj * a.x + sj.x * hn, cj * a.y + sj.y * hn);
+        double2* g = ga.gv + (int64_t)s * (m + 1);
+        const double2 gj = g[j];
+        const double2 gn = make_double2(-(sj.x * gj.x + sj.y * gj.y), -(sj.x * gj.y - sj.y * gj.x));   // -conj(s) g_j
+        g[j + 1] = gn;
+        g[j] = make_double2(cj * gj.x, cj * gj.y);
+        if (ga.gmon && s == 0) *ga.gmon = gn;
+        ga.kused[s] = j + 1;
+        ga.beta[s] = hn;
+        const double t = ga.target[s];
+        keep = !(stop || gn.x * gn.x + gn.y * gn.y <= t * t || hn == 0.0);
+        if (!keep) ga.active[s] = 0;
+        else atomicAdd(ga.nact, 1);
     }
     __syncwarp();
     double2* out = ga.Rm + ((int64_t)s * m + j) * m;          // column j, rows 0..j
     for (int i = lane; i <= j; i += 32) out[i] = col[i];
+    return __shfl_sync(0xffffffffu, keep, 0) != 0;
 }
 
 // Second Gram-Schmidt update w -= V h2 with the per-chunk ||w||^2; the last
@@ -142,7 +197,297 @@ __global__ void __launch_bounds__(KT) k_update_givens(const Chunk* __restrict__ 
         s_hn2 = t;
     }
     __syncthreads();
-    if (threadIdx.x < 32) givens_warp(ga, c.seg, s_hn2, reinterpret_cast<unsigned char*>(sh));
+    if (threadIdx.x < 32) {
+        const int j = ga.j;
+        double2* hin = sh;                   // [j+1] h1 + h2
+        double2* col = sh + (j + 1);         // [j+1] the rotated column
+        for (int i = threadIdx.x; i <= j; i += 32)
+            hin[i] = cadd(ga.h1[(int64_t)c.seg * ga.ldh + i], ga.h2[(int64_t)c.seg * ga.ldh + i]);
+        __syncwarp();
+        givens_core(ga, c.seg, j, hin, sqrt(s_hn2), col);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Flexible cycles with delayed re-orthogonalisation (DCGS2): two passes over
+// the basis per Arnoldi step instead of four.
+//
+// Step j holds the orthonormal v_0..v_{j-1} and, in basis slot j, u_j: the
+// next vector orthogonalised once.  z_j = M u_j (kept in the flexible basis),
+// w_j = A z_j.  One pass over the basis gives s = V^H u_j, b = V^H w_j,
+// c1 = u_j^H u_j and c2 = u_j^H w_j, and then
+//     gamma_j = sqrt(c1 - |s|^2),      v_j = (u_j - V s) / gamma_j,
+//     d_j     = v_j^H w_j = (c2 - s^H b) / gamma_j,
+//     u_{j+1} = (w_j - V b - v_j d_j) / gamma_j
+//             = w_j / gamma_j - u_j d_j / gamma_j^2 - V (b - s d_j / gamma_j) / gamma_j,
+// which the second pass writes (v_j over u_j in slot j, u_{j+1} into slot
+// j + 1).  (Without the division by gamma_j the norms of the u_j grow
+// geometrically, ~1e13 after 40 steps, and the cycle loses its accuracy;
+// with it |u_{j+1}| is about h_{j+1,j}.)  One step later
+// u_{j+1} = V_{0..j} s_{j+1} + gamma_{j+1} v_{j+1}, so
+//     A z_j = V_{0..j} ([b_j; d_j] + gamma_j s_{j+1}) + gamma_j gamma_{j+1} v_{j+1}:
+// Hessenberg column j becomes final at step j + 1, where its Givens step and
+// the residual test run.  The directions z_j span the same space as the
+// M v_j, and x = x_0 + Z y minimises the residual over it as in flexible
+// GMRES.  v_0 = r / ||r|| is taken as it is (gamma_0 = 1); a cycle of m
+// columns ends with a step that only finalises column m - 1 (no M, no A).
+struct DcgsArgs {
+    int j, last;
+    double2* pre;              // [nseg][m+1]: [b; d] of the previous step (column j-1 before gamma_{j-1} s_j is
+                               // added) at 0..j-1, gamma_{j-1} at m
+    double2* coef;             // [nseg][2m+2]: alpha_k = -s_k / gamma (k < j) at 0, beta_k = -(b_k - s_k d / gamma) / gamma
+                               // at m, 1 / gamma at 2m, -d / gamma^2 at 2m + 1
+    int* nact;                 // active-segment count of this step (the step's update zeroes the next one's)
+    GivensArgs g;              // rotations, R, g, targets, activity (h1 and h2 unused)
+};
+
+// Sums NV values per lane over the warp by recursive halving (NV/2 + NV/4 +
+// ... + 1 shuffles, then plain ones): lane l ends with the total of value
+// l >> (5 - log2 NV).
+template <int NV, class R>
+__device__ __forceinline__ R warp_sum_many(R (&a)[NV], int lane) {
+    int off = 16;
+#pragma unroll
+    for (int n = NV; n > 1; n >>= 1, off >>= 1) {
+        const bool up = (lane & off) != 0;
+#pragma unroll
+        for (int i = 0; i < n / 2; ++i) {
+            const R send = up ? a[i] : a[i + n / 2];
+            const R keep = up ? a[i + n / 2] : a[i];
+            a[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+        }
+    }
+    R v = a[0];
+    for (; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
+// First pass of step j: per chunk the dot products of v_0..v_{j-1} with u_j
+// and w (w = null on the finalising step), u_j^H u_j and u_j^H w; the last
+// block of each segment sums them in chunk order and runs the segment's
+// scalar step (gamma, d, Hessenberg column j-1 and its Givens step, the
+// coefficients of the second pass).  Partial layout: 2k = v_k^H u_j,
+// 2k + 1 = v_k^H w, 2j = (c1, 0), 2j + 1 = c2.
+template <class V>
+__global__ void __launch_bounds__(KT, 4) k_dcgs_dots(const Chunk* __restrict__ chunks, const V* __restrict__ basis,
+                                                  int64_t ld, const V* __restrict__ w, double2* __restrict__ partial,
+                                                  int ldp, const int* __restrict__ act, DcgsArgs da) {
+    using R = typename VT<V>::R;
+    extern __shared__ double2 sred[];          // [2j+2][KT/32]; the last block reuses it
+    constexpr int NW = KT / 32;
+    const Chunk c = chunks[blockIdx.x];
+    if (!act[c.seg]) return;
+    const int j = da.j, nv = 2 * j + 2;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const bool full = c.end - c.begin == CHUNK;
+    const V* u = basis + (int64_t)j * ld;
+    V ur[EPT], wr[EPT];
+#pragma unroll
+    for (int q = 0; q < EPT; ++q) {
+        const int64_t e = c.begin + threadIdx.x + (int64_t)q * KT;
+        const bool ok = full || e < c.end;
+        ur[q] = ok ? u[e] : mk<V>(0, 0);
+        wr[q] = (ok && w) ? w[e] : mk<V>(0, 0);
+    }
+    double* sd = reinterpret_cast<double*>(sred);
+    constexpr int KB = 4;
+    for (int k0 = 0; k0 < j; k0 += KB) {
+        V v[KB][EPT];
+#pragma unroll
+        for (int b = 0; b < KB; ++b) {
+            const V* vk = basis + (int64_t)(k0 + b) * ld;
+#pragma unroll
+            for (int q = 0; q < EPT; ++q) {
+                const int64_t e = c.begin + threadIdx.x + (int64_t)q * KT;
+                v[b][q] = mk<V>(0, 0);
+                if (k0 + b < j && (full || e < c.end)) v[b][q] = vk[e];
+            }
+        }
+        R a[4 * KB];                            // per vector: conj(v).u (re, im), conj(v).w (re, im)
+#pragma unroll
+        for (int b = 0; b < KB; ++b) {
+            a[4 * b] = a[4 * b + 1] = a[4 * b + 2] = a[4 * b + 3] = 0;
+#pragma unroll
+            for (int q = 0; q < EPT; ++q) {
+                a[4 * b] += v[b][q].x * ur[q].x + v[b][q].y * ur[q].y;
+                a[4 * b + 1] += v[b][q].x * ur[q].y - v[b][q].y * ur[q].x;
+                a[4 * b + 2] += v[b][q].x * wr[q].x + v[b][q].y * wr[q].y;
+                a[4 * b + 3] += v[b][q].x * wr[q].y - v[b][q].y * wr[q].x;
+            }
+        }
+        const R tot = warp_sum_many<4 * KB>(a, lane);
+        const int idx = lane >> 1, b = idx >> 2, comp = idx & 3;
+        if ((lane & 1) == 0 && k0 + b < j)                   // value (2(k0+b) + comp/2), component comp%2
+            sd[((2 * (k0 + b) + (comp >> 1)) * NW + warp) * 2 + (comp & 1)] = (double)tot;
+    }
+    {
+        R a[4] = {0, 0, 0, 0};                  // u.u, 0, conj(u).w (re, im)
+#pragma unroll
+        for (int q = 0; q < EPT; ++q) {
+            a[0] += ur[q].x * ur[q].x + ur[q].y * ur[q].y;
+            a[2] += ur[q].x * wr[q].x + ur[q].y * wr[q].y;
+            a[3] += ur[q].x * wr[q].y - ur[q].y * wr[q].x;
+        }
+        const R tot = warp_sum_many<4>(a, lane);
+        const int comp = lane >> 3;
+        if ((lane & 7) == 0) sd[((2 * j + (comp >> 1)) * NW + warp) * 2 + (comp & 1)] = (double)tot;
+    }
+    __syncthreads();
+    for (int kk = threadIdx.x; kk < nv; kk += KT) {
+        double2 t = make_double2(0, 0);
+        for (int q = 0; q < NW; ++q) t = cadd(t, sred[kk * NW + q]);
+        partial[(int64_t)blockIdx.x * ldp + kk] = t;
+    }
+    if (!last_block_of_segment(c.seg, da.g.seg_ch, da.g.cnt)) return;
+    double2* tot = sred;                        // [2j+2] segment totals
+    for (int kk = threadIdx.x; kk < nv; kk += KT) {
+        double2 t = make_double2(0, 0);
+        for (int cc = da.g.seg_ch[c.seg]; cc < da.g.seg_ch[c.seg + 1]; ++cc) t = cadd(t, __ldcg(&partial[(int64_t)cc * ldp + kk]));
+        tot[kk] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x >= 32) return;
+    // ---- the segment's scalar step (one warp, FP64) ----
+    const int sg = c.seg, m = da.g.m;
+    double ss = 0, sbr = 0, sbi = 0;            // |s|^2, s^H b
+    for (int k = lane; k < j; k += 32) {
+        const double2 sk = tot[2 * k], bk = tot[2 * k + 1];
+        ss += sk.x * sk.x + sk.y * sk.y;
+        sbr += sk.x * bk.x + sk.y * bk.y;
+        sbi += sk.x * bk.y - sk.y * bk.x;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        ss += __shfl_xor_sync(0xffffffffu, ss, o);
+        sbr += __shfl_xor_sync(0xffffffffu, sbr, o);
+        sbi += __shfl_xor_sync(0xffffffffu, sbi, o);
+    }
+    const double c1 = tot[2 * j].x;
+    const double2 c2 = tot[2 * j + 1];
+    double gamma = 1.0;
+    if (j > 0) {
+        const double g2 = c1 - ss;
+        gamma = g2 > 0 ? sqrt(g2) : 0.0;        // 0: u_j lies in span(V) (a lucky breakdown)
+    }
+    if (!isfinite(c1) || !isfinite(c2.x) || !isfinite(c2.y) || !isfinite(gamma)) {
+        if (lane == 0) {
+            atomicExch(da.g.flag, 1);
+            da.g.active[sg] = 0;
+        }
+        return;
+    }
+    double2* pre = da.pre + (int64_t)sg * (m + 1);
+    bool keep = true;
+    if (j > 0) {
+        // Hessenberg column j-1: [b_{j-1}; d_{j-1}] + gamma_{j-1} s_j over gamma_{j-1} gamma_j
+        const double gp = pre[m].x;
+        double2* hin = tot + nv;
+        double2* col = hin + j;
+        for (int i = lane; i < j; i += 32) {
+            const double2 si = tot[2 * i];
+            hin[i] = make_double2(pre[i].x + gp * si.x, pre[i].y + gp * si.y);
+        }
+        __syncwarp();
+        GivensArgs ga = da.g;
+        ga.nact = da.nact;
+        keep = givens_core(ga, sg, j - 1, hin, gp * gamma, col, da.last != 0);
+    } else if (lane == 0) {
+        atomicAdd(da.nact, 1);                  // no column yet: the segment goes on
+    }
+    if (!keep || da.last) return;
+    const double ig = 1.0 / gamma;
+    const double2 d = make_double2((c2.x - sbr) * ig, (c2.y - sbi) * ig);
+    double2* cf = da.coef + (int64_t)sg * (2 * m + 2);
+    __syncwarp();                               // pre[m] (gamma_{j-1}) was read above
+    for (int k = lane; k < j; k += 32) {
+        const double2 sk = tot[2 * k], bk = tot[2 * k + 1];
+        pre[k] = bk;
+        cf[k] = make_double2(-sk.x * ig, -sk.y * ig);
+        const double2 sd_ = make_double2((sk.x * d.x - sk.y * d.y) * ig, (sk.x * d.y + sk.y * d.x) * ig);
+        cf[m + k] = make_double2(-(bk.x - sd_.x) * ig, -(bk.y - sd_.y) * ig);
+    }
+    if (lane == 0) {
+        pre[j] = d;
+        pre[m] = make_double2(gamma, 0.0);
+        cf[2 * m] = make_double2(ig, 0.0);
+        cf[2 * m + 1] = make_double2(-d.x * ig * ig, -d.y * ig * ig);
+    }
+}
+
+// Second pass of step j: v_j = u_j / gamma + sum_k alpha_k v_k over slot j and
+// u_{j+1} = w / gamma - (d / gamma^2) u_j + sum_k beta_k v_k into slot j + 1.
+// Block 0 first zeroes the active count of the next step.
+template <class V>
+__global__ void __launch_bounds__(KT, 4) k_dcgs_update(const Chunk* __restrict__ chunks, V* __restrict__ basis,
+                                                    int64_t ld, int j, int m, const V* __restrict__ w,
+                                                    const double2* __restrict__ coef, const int* __restrict__ act,
+                                                    int* __restrict__ nact_next) {
+    using R = typename VT<V>::R;
+    extern __shared__ double2 sc[];            // [2j+2]: alpha_k, beta_k, 1/gamma, -d/gamma^2
+    if (blockIdx.x == 0 && threadIdx.x == 0) *nact_next = 0;
+    const Chunk c = chunks[blockIdx.x];
+    if (!act[c.seg]) return;
+    const double2* cf = coef + (int64_t)c.seg * (2 * m + 2);
+    for (int k = threadIdx.x; k < j; k += KT) {
+        sc[k] = cf[k];
+        sc[j + k] = cf[m + k];
+    }
+    if (threadIdx.x == 0) {
+        sc[2 * j] = cf[2 * m];
+        sc[2 * j + 1] = cf[2 * m + 1];
+    }
+    __syncthreads();
+    const bool full = c.end - c.begin == CHUNK;
+    V* u = basis + (int64_t)j * ld;
+    V* un = basis + (int64_t)(j + 1) * ld;
+    const R cv = (R)sc[2 * j].x, cur = (R)sc[2 * j + 1].x, cui = (R)sc[2 * j + 1].y;
+    R xr[EPT], xi[EPT], yr[EPT], yi[EPT];       // v_j and u_{j+1}
+#pragma unroll
+    for (int q = 0; q < EPT; ++q) {
+        const int64_t e = c.begin + threadIdx.x + (int64_t)q * KT;
+        const bool ok = full || e < c.end;
+        const V a = ok ? u[e] : mk<V>(0, 0), b = ok ? w[e] : mk<V>(0, 0);
+        xr[q] = cv * a.x;
+        xi[q] = cv * a.y;
+        yr[q] = cv * b.x + cur * a.x - cui * a.y;
+        yi[q] = cv * b.y + cur * a.y + cui * a.x;
+    }
+    constexpr int KB = 4;
+    for (int k0 = 0; k0 < j; k0 += KB) {
+        V v[KB][EPT];
+#pragma unroll
+        for (int b = 0; b < KB; ++b) {
+            const V* vk = basis + (int64_t)(k0 + b) * ld;
+#pragma unroll
+            for (int q = 0; q < EPT; ++q) {
+                const int64_t e = c.begin + threadIdx.x + (int64_t)q * KT;
+                v[b][q] = mk<V>(0, 0);
+                if (k0 + b < j && (full || e < c.end)) v[b][q] = vk[e];
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < KB; ++b) {
+            const int kk = min(k0 + b, j - 1);
+            const bool in = k0 + b < j;
+            const R ar = in ? (R)sc[kk].x : (R)0, ai = in ? (R)sc[kk].y : (R)0;
+            const R br = in ? (R)sc[j + kk].x : (R)0, bi = in ? (R)sc[j + kk].y : (R)0;
+#pragma unroll
+            for (int q = 0; q < EPT; ++q) {
+                xr[q] += ar * v[b][q].x - ai * v[b][q].y;
+                xi[q] += ar * v[b][q].y + ai * v[b][q].x;
+                yr[q] += br * v[b][q].x - bi * v[b][q].y;
+                yi[q] += br * v[b][q].y + bi * v[b][q].x;
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < EPT; ++q) {
+        const int64_t e = c.begin + threadIdx.x + (int64_t)q * KT;
+        if (full || e < c.end) {
+            if (j > 0) u[e] = mk<V>(xr[q], xi[q]);
+            un[e] = mk<V>(yr[q], yi[q]);
+        }
+    }
 }
 
 // y = R^{-1} g (upper triangular, k = kused[s]), one warp per segment, by
@@ -320,9 +665,13 @@ struct Krylov {
     DArr<double2> partial, h1, h2, Rm, sn, gv, y;
     DArr<double> nrm_part, nrm, cs, beta, target, prev;
     DArr<int> active, kused, cnt;
-    // monitor record of the latest Arnoldi step, 32 bytes: the active-segment
-    // count and the breakdown flag (two ints), then g_{j+1} of segment 0
+    // monitor record of the latest Arnoldi step, 32 bytes: two active-segment
+    // counts (the CGS2 steps use the first; the DCGS2 steps alternate between
+    // them, each step's update zeroing the next one's), the breakdown flag,
+    // then g_{j+1} of segment 0
     DArr<double2> mon;
+    DArr<double2> pre, coef;   // DCGS2: previous step's [b; d] and the second pass's coefficients
+    bool dcgs = false;
     int* nact = nullptr;
     int* flag = nullptr;
     double2* gmon = nullptr;
@@ -349,7 +698,12 @@ struct Krylov {
               const std::vector<int64_t>& segn, bool flexible_ = false) {
         n = n_; nseg = nseg_; m = m_; nch = (int)chunks.size();
         flexible = flexible_;
+        dcgs = flexible && !(getenv("THM_GS") && std::string(getenv("THM_GS")) == "cgs2");
         if (flexible) zbasis.alloc((size_t)m * n);
+        if (dcgs) {
+            pre.alloc((size_t)nseg_ * (m_ + 1));
+            coef.alloc((size_t)nseg_ * (2 * m_ + 2));
+        }
         seg_n = segn;
         if (dch) d_chunks = dch;
         else { own_chunks.upload(chunks); d_chunks = own_chunks.p; }
@@ -359,7 +713,7 @@ struct Krylov {
         seg_ch.upload(sc);
         basis.alloc((size_t)(m + 1) * n);
         w.alloc(n); z.alloc(n); r.alloc(n); t.alloc(n);
-        partial.alloc((size_t)nch * (m + 1));
+        partial.alloc((size_t)nch * (2 * m + 2));
         h1.alloc((size_t)nseg * (m + 1)); h2.alloc((size_t)nseg * (m + 1));
         Rm.alloc((size_t)nseg * m * m);
         sn.alloc((size_t)nseg * m); cs.alloc((size_t)nseg * m);
@@ -371,7 +725,7 @@ struct Krylov {
         mon.alloc(2);
         mon.zero(0);
         nact = reinterpret_cast<int*>(mon.p);
-        flag = nact + 1;
+        flag = nact + 2;
         gmon = mon.p + 1;
         if (!h_pinned) THM_CUDA(cudaMallocHost(&h_pinned, 2 * sizeof(int)));
         if (!h_ring) {
@@ -381,8 +735,14 @@ struct Krylov {
         // the kernels are shared by every Krylov instance of this vector
         // type (inner and outer solvers): only ever raise their limit
         size_t dots_smem = (size_t)(m + 1) * (KT / 32) * sizeof(double2);
-        THM_REQUIRE(dots_smem <= 200 * 1024, "restart length too large");
-        static size_t dots_attr = 0;
+        THM_REQUIRE((dcgs ? dcgs_smem(m) : dots_smem) <= 200 * 1024, "restart length too large");
+        static size_t dots_attr = 0, dcgs_attr = 0;
+        if (dcgs && dcgs_smem(m) > dcgs_attr) {
+            THM_CUDA(cudaFuncSetAttribute(k_dcgs_dots<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dcgs_smem(m)));
+            THM_CUDA(cudaFuncSetAttribute(k_dcgs_update<V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)((2 * m + 2) * sizeof(double2))));
+            dcgs_attr = dcgs_smem(m);
+        }
         if (dots_smem > dots_attr) {
             THM_CUDA(cudaFuncSetAttribute(k_chunk_dots<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dots_smem));
             THM_CUDA(cudaFuncSetAttribute(k_chunk_update<V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -401,11 +761,11 @@ struct Krylov {
     }
 
     // dynamic shared memory of k_update_givens at step j <= m-1: the nk = j+1
-    // coefficients, or the Givens scratch (column, rotations)
-    static size_t givens_smem(int mm) {
-        return std::max((size_t)mm * sizeof(double2),
-                        (size_t)mm * sizeof(double2) + (size_t)mm * (sizeof(double2) + sizeof(double)));
-    }
+    // coefficients, or the Givens column and its rotated copy
+    static size_t givens_smem(int mm) { return 2 * (size_t)mm * sizeof(double2); }
+    // dynamic shared memory of k_dcgs_dots at step j <= m: the warp sums of
+    // its 2j + 2 dot products (the last block reuses them for the scalar step)
+    static size_t dcgs_smem(int j) { return (size_t)(2 * j + 2) * (KT / 32) * sizeof(double2); }
 
     int read_nact(cudaStream_t st) {
         THM_CUDA(cudaMemcpyAsync(h_pinned, nact, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -445,6 +805,60 @@ struct Krylov {
             if (total >= maxit) { ks.status = THM_ENOCONV; break; }
             THM_LAUNCH(THM_K_KRYLOV, st, k_chunk_scale<V><<<nch, 256, 0, st>>>(d_chunks, r.p, beta.p, basis.p, nullptr));
             int j = 0, checked = 0;
+            // the monitor record of step jj is in the ring; true when the host
+            // has seen every segment stop or a breakdown (reads run a few
+            // steps behind the GPU and block only when the ring is full)
+            auto monitor = [&](int jj, int cnt_slot_of_step) -> bool {
+                const int slot = jj % RING;
+                THM_CUDA(cudaMemcpyAsync(h_ring + 2 * slot, mon.p, 2 * sizeof(double2), cudaMemcpyDeviceToHost, st));
+                THM_CUDA(cudaEventRecord(ring_ev[slot], st));
+                while (checked <= jj) {
+                    const int rs_ = checked % RING;
+                    cudaError_t q = (jj - checked >= RING - 1) ? cudaEventSynchronize(ring_ev[rs_]) : cudaEventQuery(ring_ev[rs_]);
+                    if (q == cudaErrorNotReady) break;
+                    THM_CUDA(q);
+                    const int* rec = reinterpret_cast<const int*>(h_ring + 2 * rs_);
+                    if (rec[2]) { ks.status = THM_EBREAKDOWN; return true; }
+                    if (nseg == 1 && h_beta0 > 0) {
+                        const double2 g1 = h_ring[2 * rs_ + 1];
+                        last_rel = std::hypot(g1.x, g1.y) / h_beta0;
+                    }
+                    if (rec[cnt_slot_of_step < 0 ? 0 : (checked & 1)] == 0) return true;
+                    ++checked;
+                }
+                return false;
+            };
+            if (dcgs && M) {
+                // DCGS2 steps 0..m (step m, or the step after the iteration
+                // cap, only finalises the last column)
+                THM_CUDA(cudaMemsetAsync(nact, 0, 2 * sizeof(int), st));
+                for (; j <= m; ++j) {
+                    const bool last = j == m || total >= maxit;
+                    V* uj = basis.p + (int64_t)j * n;
+                    if (!last) {
+                        V* zj = zbasis.p + (int64_t)j * n;
+                        step_mask = active.p;
+                        M(uj, zj);
+                        A(zj, w.p);
+                        step_mask = nullptr;
+                    }
+                    GivensArgs ga{j, m, m + 1, nullptr, nullptr, Rm.p, cs.p, sn.p, gv.p, target.p, active.p, kused.p,
+                                  beta.p, nact, flag, nullptr, seg_ch.p, cnt.p};
+                    DcgsArgs da{j, last ? 1 : 0, pre.p, coef.p, nact + (j & 1), ga};
+                    THM_LAUNCH(THM_K_DOTS, st, k_dcgs_dots<V><<<nch, KT, dcgs_smem(j), st>>>(d_chunks, basis.p, n,
+                                                                                             last ? nullptr : w.p,
+                                                                                             partial.p, 2 * m + 2,
+                                                                                             active.p, da));
+                    if (!last) {
+                        THM_LAUNCH(THM_K_UPDATE, st, k_dcgs_update<V><<<nch, KT, (size_t)(2 * j + 2) * sizeof(double2), st>>>(
+                                                         d_chunks, basis.p, n, j, m, w.p, coef.p, active.p,
+                                                         nact + ((j + 1) & 1)));
+                        ++total;
+                    }
+                    if (monitor(j, 1) || last) break;
+                }
+                ++j;                        // steps 0..j-1 ran: the drain below reads them all
+            } else
             for (; j < m && total < maxit; ++j) {
                 V* vj = basis.p + (int64_t)j * n;
                 const V* zin = vj;
@@ -467,38 +881,18 @@ struct Krylov {
                                                                                   cnt.p, h2.p));
                 GivensArgs ga{j, m, m + 1, h1.p, h2.p, Rm.p, cs.p, sn.p, gv.p, target.p, active.p, kused.p, beta.p,
                               nact, flag, nseg == 1 ? gmon : nullptr, seg_ch.p, cnt.p};
-                const size_t gsm = std::max((size_t)nk * sizeof(double2),
-                                            (size_t)(j + 1) * sizeof(double2) + (size_t)j * (sizeof(double2) + sizeof(double)));
+                const size_t gsm = 2 * (size_t)(j + 1) * sizeof(double2);      // coefficients, or column + rotated column
                 THM_LAUNCH(THM_K_UPDATE, st, k_update_givens<V><<<nch, KT, gsm, st>>>(d_chunks, basis.p, n, nk, w.p, nrm_part.p,
                                                                                       active.p, ga));
                 THM_LAUNCH(THM_K_KRYLOV, st, k_chunk_scale<V><<<nch, 256, 0, st>>>(d_chunks, w.p, beta.p, basis.p + (int64_t)(j + 1) * n, active.p));
                 ++total;
                 // monitor: one copy of the step's record into the ring
-                const int slot = j % RING;
-                THM_CUDA(cudaMemcpyAsync(h_ring + 2 * slot, mon.p, 2 * sizeof(double2), cudaMemcpyDeviceToHost, st));
-                THM_CUDA(cudaEventRecord(ring_ev[slot], st));
-                // read every finished step; block only when the ring is full
-                bool stop = false;
-                while (checked <= j) {
-                    const int rs_ = checked % RING;
-                    cudaError_t q = (j - checked >= RING - 1) ? cudaEventSynchronize(ring_ev[rs_]) : cudaEventQuery(ring_ev[rs_]);
-                    if (q == cudaErrorNotReady) break;
-                    THM_CUDA(q);
-                    const int* rec = reinterpret_cast<const int*>(h_ring + 2 * rs_);
-                    if (rec[1]) { ks.status = THM_EBREAKDOWN; stop = true; break; }
-                    if (nseg == 1 && h_beta0 > 0) {
-                        const double2 g1 = h_ring[2 * rs_ + 1];
-                        last_rel = std::hypot(g1.x, g1.y) / h_beta0;
-                    }
-                    if (rec[0] == 0) { stop = true; break; }
-                    ++checked;
-                }
-                if (stop) break;
+                if (monitor(j, -1)) break;
             }
             // drain the monitor: any later step may still report breakdown
             THM_CUDA(cudaStreamSynchronize(st));
             for (; checked < j && ks.status != THM_EBREAKDOWN; ++checked)
-                if (reinterpret_cast<const int*>(h_ring + 2 * (checked % RING))[1]) ks.status = THM_EBREAKDOWN;
+                if (reinterpret_cast<const int*>(h_ring + 2 * (checked % RING))[2]) ks.status = THM_EBREAKDOWN;
             THM_CUDA(cudaGetLastError());
             // x += M (V y)
             THM_LAUNCH(THM_K_KRYLOV, st, k_backsolve<<<nseg, 32, (size_t)m * sizeof(double2), st>>>(nseg, m, Rm.p, gv.p,
