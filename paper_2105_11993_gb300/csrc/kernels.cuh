@@ -283,7 +283,13 @@ __device__ __forceinline__ void chunk_update_body(const Chunk& c, const V* __res
                                                   double* __restrict__ nrm_part, double2* sh, V* wout) {
     using R = typename VT<V>::R;
     __shared__ double sw[KT / 32];
-    for (int k = threadIdx.x; k < nk; k += KT) sh[k] = h[(int64_t)c.seg * ldh + k];
+    // the coefficients in the vector precision, rounded once per block (a
+    // double-to-float conversion per use would run on the slow FP64 path)
+    V* shv = reinterpret_cast<V*>(sh);
+    for (int k = threadIdx.x; k < nk; k += KT) {
+        const double2 hk = h[(int64_t)c.seg * ldh + k];
+        shv[k] = mk<V>((R)hk.x, (R)hk.y);
+    }
     __syncthreads();
     const bool full = c.end - c.begin == CHUNK;
     R xr[EPT], xi[EPT];
@@ -311,7 +317,8 @@ __device__ __forceinline__ void chunk_update_body(const Chunk& c, const V* __res
 #pragma unroll
         for (int b = 0; b < KB; ++b) {
             const int kk = min(k0 + b, nk - 1);
-            const R hr = k0 + b < nk ? (R)sh[kk].x : (R)0, hi = k0 + b < nk ? (R)sh[kk].y : (R)0;
+            const V hv = shv[kk];
+            const R hr = k0 + b < nk ? hv.x : (R)0, hi = k0 + b < nk ? hv.y : (R)0;
 #pragma unroll
             for (int q = 0; q < EPT; ++q) {
                 xr[q] -= hr * v[b][q].x - hi * v[b][q].y;
@@ -396,10 +403,15 @@ template <class V>
 __global__ void k_chunk_scale(const Chunk* __restrict__ chunks, const V* __restrict__ r,
                               const double* __restrict__ beta, V* __restrict__ x, const int* __restrict__ act) {
     using R = typename VT<V>::R;
+    __shared__ R s_inv;
     const Chunk c = chunks[blockIdx.x];
     if (act && !act[c.seg]) return;
-    double b = beta[c.seg];
-    R inv = b > 0 ? (R)(1.0 / b) : (R)0;
+    if (threadIdx.x == 0) {                    // one FP64 division per block, not per thread
+        const double b = beta[c.seg];
+        s_inv = b > 0 ? (R)(1.0 / b) : (R)0;
+    }
+    __syncthreads();
+    const R inv = s_inv;
     for (int64_t e = c.begin + threadIdx.x; e < c.end; e += blockDim.x) {
         V v = r[e];
         x[e] = mk<V>(v.x * inv, v.y * inv);
@@ -412,16 +424,19 @@ __global__ void __launch_bounds__(KT) k_chunk_combine(const Chunk* __restrict__ 
                                                       int64_t ld, const int* __restrict__ kused,
                                                       const double2* __restrict__ y, int ldy, V* __restrict__ t) {
     using R = typename VT<V>::R;
+    extern __shared__ double2 ys_raw[];        // [ldy] y of this segment in the vector precision
+    V* ys = reinterpret_cast<V*>(ys_raw);
     const Chunk c = chunks[blockIdx.x];
     const int nk = kused[c.seg];
     const double2* yy = y + (int64_t)c.seg * ldy;
+    for (int k = threadIdx.x; k < nk; k += KT) ys[k] = mk<V>((R)yy[k].x, (R)yy[k].y);
+    __syncthreads();
     for (int64_t e = c.begin + threadIdx.x; e < c.end; e += KT) {
         R xr = 0, xi = 0;
         for (int k = 0; k < nk; ++k) {
-            V v = basis[(int64_t)k * ld + e];
-            R a = (R)yy[k].x, b = (R)yy[k].y;
-            xr += a * v.x - b * v.y;
-            xi += a * v.y + b * v.x;
+            const V v = basis[(int64_t)k * ld + e], a = ys[k];
+            xr += a.x * v.x - a.y * v.y;
+            xi += a.x * v.y + a.y * v.x;
         }
         t[e] = mk<V>(xr, xi);
     }

@@ -423,24 +423,28 @@ __global__ void __launch_bounds__(KT, 4) k_dcgs_update(const Chunk* __restrict__
                                                     const double2* __restrict__ coef, const int* __restrict__ act,
                                                     int* __restrict__ nact_next) {
     using R = typename VT<V>::R;
-    extern __shared__ double2 sc[];            // [2j+2]: alpha_k, beta_k, 1/gamma, -d/gamma^2
+    using C2 = V;                              // coefficient pairs in the vector precision
+    extern __shared__ double2 sc_raw[];        // [2j+2]: alpha_k, beta_k, 1/gamma, -d/gamma^2
+    C2* sc = reinterpret_cast<C2*>(sc_raw);
     if (blockIdx.x == 0 && threadIdx.x == 0) *nact_next = 0;
     const Chunk c = chunks[blockIdx.x];
     if (!act[c.seg]) return;
+    // the coefficients are rounded to the vector precision once per block
+    // (a double-to-float conversion per use would run on the slow FP64 path)
     const double2* cf = coef + (int64_t)c.seg * (2 * m + 2);
     for (int k = threadIdx.x; k < j; k += KT) {
-        sc[k] = cf[k];
-        sc[j + k] = cf[m + k];
+        sc[k] = mk<V>((R)cf[k].x, (R)cf[k].y);
+        sc[j + k] = mk<V>((R)cf[m + k].x, (R)cf[m + k].y);
     }
     if (threadIdx.x == 0) {
-        sc[2 * j] = cf[2 * m];
-        sc[2 * j + 1] = cf[2 * m + 1];
+        sc[2 * j] = mk<V>((R)cf[2 * m].x, (R)cf[2 * m].y);
+        sc[2 * j + 1] = mk<V>((R)cf[2 * m + 1].x, (R)cf[2 * m + 1].y);
     }
     __syncthreads();
     const bool full = c.end - c.begin == CHUNK;
     V* u = basis + (int64_t)j * ld;
     V* un = basis + (int64_t)(j + 1) * ld;
-    const R cv = (R)sc[2 * j].x, cur = (R)sc[2 * j + 1].x, cui = (R)sc[2 * j + 1].y;
+    const R cv = sc[2 * j].x, cur = sc[2 * j + 1].x, cui = sc[2 * j + 1].y;
     R xr[EPT], xi[EPT], yr[EPT], yi[EPT];       // v_j and u_{j+1}
 #pragma unroll
     for (int q = 0; q < EPT; ++q) {
@@ -469,8 +473,9 @@ __global__ void __launch_bounds__(KT, 4) k_dcgs_update(const Chunk* __restrict__
         for (int b = 0; b < KB; ++b) {
             const int kk = min(k0 + b, j - 1);
             const bool in = k0 + b < j;
-            const R ar = in ? (R)sc[kk].x : (R)0, ai = in ? (R)sc[kk].y : (R)0;
-            const R br = in ? (R)sc[j + kk].x : (R)0, bi = in ? (R)sc[j + kk].y : (R)0;
+            const C2 al = sc[kk], be = sc[j + kk];
+            const R ar = in ? al.x : (R)0, ai = in ? al.y : (R)0;
+            const R br = in ? be.x : (R)0, bi = in ? be.y : (R)0;
 #pragma unroll
             for (int q = 0; q < EPT; ++q) {
                 xr[q] += ar * v[b][q].x - ai * v[b][q].y;
@@ -899,10 +904,10 @@ struct Krylov {
                                                                                                   kused.p, y.p));
             if (flexible && M) {
                 // x += Z y: the preconditioned directions actually used by the Arnoldi process
-                THM_LAUNCH(THM_K_KRYLOV, st, k_chunk_combine<V><<<nch, KT, 0, st>>>(d_chunks, zbasis.p, n, kused.p, y.p, m, t.p));
+                THM_LAUNCH(THM_K_KRYLOV, st, k_chunk_combine<V><<<nch, KT, (size_t)m * sizeof(double2), st>>>(d_chunks, zbasis.p, n, kused.p, y.p, m, t.p));
                 THM_LAUNCH(THM_K_KRYLOV, st, k_axpy<V><<<nblk(n), 256, 0, st>>>(n, t.p, x));
             } else {
-            THM_LAUNCH(THM_K_KRYLOV, st, k_chunk_combine<V><<<nch, KT, 0, st>>>(d_chunks, basis.p, n, kused.p, y.p, m, t.p));
+            THM_LAUNCH(THM_K_KRYLOV, st, k_chunk_combine<V><<<nch, KT, (size_t)m * sizeof(double2), st>>>(d_chunks, basis.p, n, kused.p, y.p, m, t.p));
             if (M) {
                 M(t.p, z.p);
                 THM_LAUNCH(THM_K_KRYLOV, st, k_axpy<V><<<nblk(n), 256, 0, st>>>(n, z.p, x));
