@@ -517,11 +517,14 @@ def main():
     p1 = torch.cuda.Event(enable_timing=True)
     p0.record(st)
     pinv_work = 0.0          # algorithmic bytes the block solve actually processed (converged subdomains skipped)
+    other_work = {thm.K_SPMV: 0.0, thm.K_DOTS: 0.0, thm.K_UPDATE: 0.0}
     pstats = []
     for _ in range(max(1, args.prof_steps)):
         sysg, _, s1 = step(mode)
         pstats.append(s1)
         pinv_work += thm.work_bytes(sysg, mode, thm.K_PINV)
+        for c in other_work:
+            other_work[c] += thm.work_bytes(sysg, mode, c)
     p1.record(st)
     torch.cuda.synchronize()
     prof_ms = p0.elapsed_time(p1)
@@ -556,6 +559,22 @@ def main():
                 "classes": kernel_classes_report(thm, prof, prof_ms),
                 "instrumented_ms_per_step": prof_ms / max(1, args.prof_steps),
                 "instrumented_time_to_1e8_s": statistics.median(s["seconds"] for s in pstats)}
+    # the other per-iteration kernels, the same way (bytes counted on the device)
+    names = {thm.K_SPMV: "k_spmv (subdomain operator T_i)",
+             thm.K_DOTS: "k_dcgs_dots (Gram-Schmidt dot-product pass)",
+             thm.K_UPDATE: "k_dcgs_update (Gram-Schmidt update pass)"}
+    others = {}
+    for c, work in other_work.items():
+        n_c, ms_c = prof[c]
+        ach = work / (ms_c / 1e3) / 1e9 if n_c and ms_c > 0 else None
+        others[names[c]] = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                            "frac": (ach / hbm_peak) if ach else None, "launches": n_c,
+                            "avg_launch_us": 1e3 * ms_c / max(1, n_c), "alg_bytes_processed": work}
+    roofline["other_kernels"] = others
+    roofline["other_kernels_definition"] = (
+        "per launch class: algorithmic bytes counted on the device / summed CUDA-event time of the class's "
+        "launches in the instrumented steps (the class time also holds the interface GMRES's few small "
+        "Gram-Schmidt launches, whose FP64 bytes are counted apart)")
 
     # plain FP64 form, timed beside (time-to-1e-8); warmed first: FP64 kernels,
     # the FP64 factorisation path and the FP64 tile autotuning on this mesh.

@@ -375,20 +375,27 @@ int thm_dirichlet_values(thm_sys* s, double* u_d);
  * overhead and not counted):
  *   THM_K_SPMV: nnz(P_i) values + 2 diagonal face terms per row
  *               + x read + y written (complex vectors)
- *   THM_K_PINV: inverse blocks W_l read in the forward and backward sweeps
- *               (sum_l m_l^2 + sum_{l<L-1} m_l^2 per subdomain), the level
- *               coupling values twice, the order-2 condensation tables,
- *               x read + y written
+ *   THM_K_PINV: the inverse blocks W_l of the forward sweeps and the middle
+ *               level (sum_l m_l^2 per subdomain), the backward-sweep blocks
+ *               H_l = W_l F_l resp. W_l E_l (sum_{l != k} m_l m_{l+-1}), the
+ *               level coupling values of the forward and middle steps, the
+ *               order-2 condensation tables, x read + y written
  * Other classes: THM_EINVAL. */
 int thm_alg_bytes(const thm_sys* s, int mode, int cls, double* bytes);
 
-/* Algorithmic bytes of the block-solve work (cls THM_K_PINV) that this system
- * has actually done so far with the factors of `mode`'s precision, by the
- * byte model of thm_alg_bytes: inside the Arnoldi steps the kernel skips the
+/* Algorithmic bytes of the work that this system has actually done so far in
+ * `mode`'s precision: inside the Arnoldi steps the kernels skip the
  * subdomains whose Krylov segment has converged, so the work per launch
- * varies and thm_alg_bytes (every subdomain) overstates it.  The kernel sums
- * the values and rows of the subdomains it processes on the device; this
- * call reads the sums (synchronising the system's stream). */
+ * varies and thm_alg_bytes (every subdomain) overstates it.  The kernels count
+ * on the device, one atomic per block; this call reads the sums (synchronising
+ * the system's stream).
+ *   THM_K_PINV:   values and rows of the subdomains processed, by the byte
+ *                 model of thm_alg_bytes
+ *   THM_K_SPMV:   rows processed x thm_alg_bytes(THM_K_SPMV) / n_local
+ *   THM_K_DOTS:   the dot-product passes over the Krylov basis (basis vectors
+ *                 and the vectors they are dotted with, read once per pass)
+ *   THM_K_UPDATE: the update passes (vectors read, vectors written)
+ * Other classes: THM_EINVAL. */
 int thm_work_bytes(const thm_sys* s, int mode, int cls, double* bytes);
 
 /* ------------------------------------------------------------------------

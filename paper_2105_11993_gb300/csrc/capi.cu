@@ -435,8 +435,24 @@ int thm_alg_bytes(const thm_sys* s, int mode, int cls, double* bytes) {
 int thm_work_bytes(const thm_sys* s, int mode, int cls, double* bytes) {
     return guarded([&]() -> int {
         THM_REQUIRE(s && bytes, "NULL argument");
-        THM_REQUIRE(cls == THM_K_PINV, "work counters exist for the block-solve kernel only");
+        THM_REQUIRE(cls == THM_K_PINV || cls == THM_K_SPMV || cls == THM_K_DOTS || cls == THM_K_UPDATE,
+                    "no work counter for this kernel class");
         *bytes = 0;
+        if (cls != THM_K_PINV) {
+            if (!s->kwork.p) return THM_OK;
+            std::vector<unsigned long long> h;
+            s->kwork.download(h, s->st);
+            const int o = mode == THM_MODE_MIXED ? 4 : 0;
+            if (cls == THM_K_SPMV) {
+                // rows processed x the SpMV byte model per row
+                double full = 0;
+                THM_REQUIRE(thm_alg_bytes(s, mode, THM_K_SPMV, &full) == THM_OK, "byte model");
+                *bytes = full * (double)h[o] / (double)std::max<int64_t>(1, s->m->n_loc);
+            } else {
+                *bytes = (double)h[o + (cls == THM_K_DOTS ? 1 : 2)];
+            }
+            return THM_OK;
+        }
         if (!s->bt_work.p) return THM_OK;
         std::vector<unsigned long long> h;
         s->bt_work.download(h, s->st);

@@ -165,6 +165,11 @@ struct thm_mesh {
     int64_t n_slices = 0, n_slots = 0;
     std::vector<int64_t> slice_ptr;                 // [n_slices+1]
     std::vector<int32_t> sell_col;                  // [n_slots]; padding = own row
+    // the same columns relative to the row's subdomain (col - off of the
+    // row's subdomain) in 16 bits, for the SpMV, when every subdomain has at
+    // most 65,536 local DOFs (col16); the factorisation keeps sell_col
+    std::vector<uint16_t> sell_col16;
+    bool col16 = false;
     std::vector<uint8_t> sell_pad;                  // [n_slots] 1 = padding
     // assembly plan: cells holding each local row (ascending), <= maxc
     int maxc = 0;
@@ -231,6 +236,7 @@ struct thm_mesh {
     // device mirrors
     thm::DArr<double> d_coords;
     thm::DArr<int32_t> d_cells, d_cell_dofs, d_cell_loc, d_sell_col, d_row_cell, d_row_k;
+    thm::DArr<uint16_t> d_sell_col16;
     thm::DArr<int64_t> d_edge_lo, d_edge_hi, d_slice_ptr, d_dir_edges, d_loc_gdof, d_rowg_ptr,
         d_copy_ptr;
     thm::DArr<int8_t> d_cell_signs, d_face_sgn, d_face_kind, d_row_face_a, d_row_face_side, d_if_ta, d_if_tb;
@@ -312,6 +318,9 @@ struct thm_sys {
     // FP32): values read and local rows processed, summed by the kernel over
     // the subdomains it did not skip
     mutable thm::DArr<unsigned long long> bt_work;
+    // work counters of the SpMV and Gram-Schmidt kernels, [8]: (FP32 ? 4 : 0)
+    // + 0 SpMV rows processed, 1 dot-product pass bytes, 2 update pass bytes
+    mutable thm::DArr<unsigned long long> kwork;
     // solver workspace (allocated on first solve, see solve.cu)
     thm::Work* w = nullptr;
     ~thm_sys();

@@ -22,33 +22,45 @@ __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_doub
 // ---------------------------------------------------------------------------
 // 3-D: the face terms are not diagonal; their values (times kappa*omega) ride
 // on the same SELL pattern (bvg: Gamma^inf, bvs: Sigma), non-null only then.
-template <class V, class F>
+// Column indices: int32 local indices, or (CI = uint16_t) indices relative
+// to the row's subdomain (subs[row_seg[r]].off added back), half the bytes of
+// the index stream.
+template <class V, class F, class CI = int32_t>
 __global__ void __launch_bounds__(256) k_spmv(int64_t n, const int64_t* __restrict__ slice_ptr,
-                                              const int32_t* __restrict__ col, const F* __restrict__ val,
+                                              const CI* __restrict__ col, const Sub* __restrict__ subs,
+                                              const F* __restrict__ val,
                                               const F* __restrict__ bg, const F* __restrict__ bs, int use_bs,
                                               const F* __restrict__ bvg, const F* __restrict__ bvs,
                                               const V* __restrict__ x, V* __restrict__ y,
-                                              const int32_t* __restrict__ row_seg, const int* __restrict__ act) {
+                                              const int32_t* __restrict__ row_seg, const int* __restrict__ act,
+                                              unsigned long long* __restrict__ work) {
     using R = typename VT<V>::R;
     int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (r >= n) return;
-    if (act && !act[row_seg[r]]) return;       // a converged subdomain's rows are not needed
+    // a converged subdomain's rows are not needed
+    const bool on = r < n && !(act && !act[row_seg[r < n ? r : 0]]);
+    if (work) {                                // rows processed (uniform branch: every thread reaches the count)
+        const int cnt = __syncthreads_count(on);
+        if (threadIdx.x == 0 && cnt) atomicAdd(work, (unsigned long long)cnt);
+    }
+    if (!on) return;
     int64_t sl = r >> 5;
     int lane = (int)(r & 31);
     int64_t base = slice_ptr[sl];
     int w = (int)((slice_ptr[sl + 1] - base) >> 5);
     R ar = 0, ai = 0;
-    const int32_t* cp = col + base + lane;
+    const CI* cp = col + base + lane;
+    const V* xs = x;                           // column origin
+    if constexpr (sizeof(CI) == 2) xs = x + subs[row_seg[r]].off;
     const F* vp = val + base + lane;
     if (bvg) {
         const F* gp = bvg + base + lane;
         const F* sp = bvs + base + lane;
         for (int t = 0; t < w; ++t) {
-            int32_t c = __ldg(cp + (t << 5));
+            int32_t c = (int32_t)__ldg(cp + (t << 5));
             R v = (R)__ldg(vp + (t << 5));
             R b = (R)__ldg(gp + (t << 5));
             if (use_bs) b += (R)__ldg(sp + (t << 5));
-            V xv = x[c];
+            V xv = xs[c];
             ar += v * xv.x - b * xv.y;
             ai += v * xv.y + b * xv.x;
         }
@@ -60,16 +72,16 @@ __global__ void __launch_bounds__(256) k_spmv(int64_t n, const int64_t* __restri
             R v[8];
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
-                c[u] = (int32_t)r;
+                c[u] = (int32_t)(r - (xs - x));    // own row (its x is read below anyway)
                 v[u] = 0;
                 if (t0 + u < w) {
-                    c[u] = __ldg(cp + ((t0 + u) << 5));
+                    c[u] = (int32_t)__ldg(cp + ((t0 + u) << 5));
                     v[u] = (R)__ldg(vp + ((t0 + u) << 5));
                 }
             }
             V xv[8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) xv[u] = x[c[u]];
+            for (int u = 0; u < 8; ++u) xv[u] = xs[c[u]];
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
                 ar += v[u] * xv[u].x;
@@ -179,11 +191,12 @@ __global__ void __launch_bounds__(KT) k_chunk_dots(const Chunk* __restrict__ chu
                                                    double2* __restrict__ partial, int ldp,
                                                    const int* __restrict__ act, const int32_t* __restrict__ seg_ch,
                                                    int* __restrict__ cnt, double2* __restrict__ h, int ldh,
-                                                   int* __restrict__ reset) {
+                                                   int* __restrict__ reset, unsigned long long* __restrict__ work) {
     extern __shared__ double2 sred[];          // [nk][KT/32]
     if (reset && blockIdx.x == 0 && threadIdx.x == 0) *reset = 0;
     const Chunk c = chunks[blockIdx.x];
     if (act && !act[c.seg]) return;            // converged segment: its partials are not read
+    if (work && threadIdx.x == 0) atomicAdd(work, (unsigned long long)((nk + 1) * (c.end - c.begin) * sizeof(V)));
     V wr[EPT];
 #pragma unroll
     for (int q = 0; q < EPT; ++q) {
@@ -359,10 +372,13 @@ __global__ void __launch_bounds__(KT) k_update_dots(const Chunk* __restrict__ ch
                                                     int64_t ld, int nk, const double2* __restrict__ h1, int ldh,
                                                     V* __restrict__ w, double2* __restrict__ partial, int ldp,
                                                     const int* __restrict__ act, const int32_t* __restrict__ seg_ch,
-                                                    int* __restrict__ cnt, double2* __restrict__ h2) {
+                                                    int* __restrict__ cnt, double2* __restrict__ h2,
+                                                    unsigned long long* __restrict__ work) {
     extern __shared__ double2 sh[];            // [nk] coefficients, then [nk][KT/32] warp sums
     const Chunk c = chunks[blockIdx.x];
     if (act && !act[c.seg]) return;
+    // the basis twice, w read and written
+    if (work && threadIdx.x == 0) atomicAdd(work, (unsigned long long)((2 * nk + 2) * (c.end - c.begin) * sizeof(V)));
     V wr[EPT];
     chunk_update_body<V>(c, basis, ld, nk, h1, ldh, w, nullptr, sh, wr);
     __syncthreads();                           // sh is reused for the warp sums

@@ -632,6 +632,25 @@ void build_mesh(thm_mesh* m) {
             }
         }
     }
+    m->col16 = true;
+    for (const auto& S : m->subs) m->col16 = m->col16 && S.n <= 65536;
+    if (m->col16) {
+        m->sell_col16.assign(m->n_slots, 0);
+        for (int64_t sl = 0; sl < m->n_slices; ++sl) {
+            int64_t w = (m->slice_ptr[sl + 1] - m->slice_ptr[sl]) / SELL_C;
+            for (int lane = 0; lane < SELL_C; ++lane) {
+                int64_t r = sl * SELL_C + lane;
+                if (r >= m->n_loc) continue;                  // never read (beyond the last row)
+                const int64_t off = m->subs[m->loc_sub[r]].off;
+                for (int64_t t = 0; t < w; ++t) {
+                    const int64_t idx = m->slice_ptr[sl] + t * SELL_C + lane;
+                    const int64_t rel = m->sell_col[idx] - off;
+                    THM_REQUIRE(rel >= 0 && rel < 65536, "SpMV column outside its row's subdomain");
+                    m->sell_col16[idx] = (uint16_t)rel;
+                }
+            }
+        }
+    }
     // ---- level coupling lists: for every level row, its S entries in the
     //      previous level (E_l) and in the next level (F_l), one 16-byte
     //      aligned block per (level, side)
@@ -900,6 +919,7 @@ void build_mesh(thm_mesh* m) {
     std::vector<int32_t> cl32(m->cell_loc.begin(), m->cell_loc.end());
     m->d_cell_loc.upload(cl32);
     m->d_sell_col.upload(m->sell_col);
+    if (m->col16) m->d_sell_col16.upload(m->sell_col16);
     m->d_sell_pad.upload(m->sell_pad);
     m->d_slice_ptr.upload(m->slice_ptr);
     m->d_row_cell.upload(m->row_cell);

@@ -184,11 +184,12 @@ template <class V>
 __global__ void __launch_bounds__(KT) k_update_givens(const Chunk* __restrict__ chunks, const V* __restrict__ basis,
                                                       int64_t ld, int nk, V* __restrict__ w,
                                                       double* __restrict__ nrm_part, const int* __restrict__ act,
-                                                      GivensArgs ga) {
+                                                      GivensArgs ga, unsigned long long* __restrict__ work) {
     extern __shared__ double2 sh[];            // [nk] coefficients, then the Givens scratch
     __shared__ double s_hn2;
     const Chunk c = chunks[blockIdx.x];
     if (act && !act[c.seg]) return;
+    if (work && threadIdx.x == 0) atomicAdd(work, (unsigned long long)((nk + 2) * (c.end - c.begin) * sizeof(V)));
     chunk_update_body<V>(c, basis, ld, nk, ga.h2, ga.ldh, w, nrm_part, sh);
     if (!last_block_of_segment(c.seg, ga.seg_ch, ga.cnt)) return;
     if (threadIdx.x == 0) {
@@ -271,13 +272,16 @@ __device__ __forceinline__ R warp_sum_many(R (&a)[NV], int lane) {
 template <class V>
 __global__ void __launch_bounds__(KT, 4) k_dcgs_dots(const Chunk* __restrict__ chunks, const V* __restrict__ basis,
                                                   int64_t ld, const V* __restrict__ w, double2* __restrict__ partial,
-                                                  int ldp, const int* __restrict__ act, DcgsArgs da) {
+                                                  int ldp, const int* __restrict__ act, DcgsArgs da,
+                                                  unsigned long long* __restrict__ work) {
     using R = typename VT<V>::R;
     extern __shared__ double2 sred[];          // [2j+2][KT/32]; the last block reuses it
     constexpr int NW = KT / 32;
     const Chunk c = chunks[blockIdx.x];
     if (!act[c.seg]) return;
     const int j = da.j, nv = 2 * j + 2;
+    if (work && threadIdx.x == 0)                 // v_0..v_{j-1}, u_j and w (none on the finalising step)
+        atomicAdd(work, (unsigned long long)((j + 1 + (w ? 1 : 0)) * (c.end - c.begin) * sizeof(V)));
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const bool full = c.end - c.begin == CHUNK;
     const V* u = basis + (int64_t)j * ld;
@@ -289,7 +293,9 @@ __global__ void __launch_bounds__(KT, 4) k_dcgs_dots(const Chunk* __restrict__ c
         ur[q] = ok ? u[e] : mk<V>(0, 0);
         wr[q] = (ok && w) ? w[e] : mk<V>(0, 0);
     }
-    double* sd = reinterpret_cast<double*>(sred);
+    // warp sums in the vector precision, [2j+2][KT/32] pairs (a float pair
+    // takes half a double2 slot; the FP64 sums start at the chunk partials)
+    R* sd = reinterpret_cast<R*>(sred);
     constexpr int KB = 4;
     for (int k0 = 0; k0 < j; k0 += KB) {
         V v[KB][EPT];
@@ -318,7 +324,7 @@ __global__ void __launch_bounds__(KT, 4) k_dcgs_dots(const Chunk* __restrict__ c
         const R tot = warp_sum_many<4 * KB>(a, lane);
         const int idx = lane >> 1, b = idx >> 2, comp = idx & 3;
         if ((lane & 1) == 0 && k0 + b < j)                   // value (2(k0+b) + comp/2), component comp%2
-            sd[((2 * (k0 + b) + (comp >> 1)) * NW + warp) * 2 + (comp & 1)] = (double)tot;
+            sd[((2 * (k0 + b) + (comp >> 1)) * NW + warp) * 2 + (comp & 1)] = tot;
     }
     {
         R a[4] = {0, 0, 0, 0};                  // u.u, 0, conj(u).w (re, im)
@@ -330,13 +336,16 @@ __global__ void __launch_bounds__(KT, 4) k_dcgs_dots(const Chunk* __restrict__ c
         }
         const R tot = warp_sum_many<4>(a, lane);
         const int comp = lane >> 3;
-        if ((lane & 7) == 0) sd[((2 * j + (comp >> 1)) * NW + warp) * 2 + (comp & 1)] = (double)tot;
+        if ((lane & 7) == 0) sd[((2 * j + (comp >> 1)) * NW + warp) * 2 + (comp & 1)] = tot;
     }
     __syncthreads();
     for (int kk = threadIdx.x; kk < nv; kk += KT) {
-        double2 t = make_double2(0, 0);
-        for (int q = 0; q < NW; ++q) t = cadd(t, sred[kk * NW + q]);
-        partial[(int64_t)blockIdx.x * ldp + kk] = t;
+        R tr = 0, ti = 0;                     // the block's sum in the vector precision, then FP64
+        for (int q = 0; q < NW; ++q) {
+            tr += sd[(kk * NW + q) * 2];
+            ti += sd[(kk * NW + q) * 2 + 1];
+        }
+        partial[(int64_t)blockIdx.x * ldp + kk] = make_double2((double)tr, (double)ti);
     }
     if (!last_block_of_segment(c.seg, da.g.seg_ch, da.g.cnt)) return;
     double2* tot = sred;                        // [2j+2] segment totals
@@ -346,11 +355,17 @@ __global__ void __launch_bounds__(KT, 4) k_dcgs_dots(const Chunk* __restrict__ c
         tot[kk] = t;
     }
     __syncthreads();
-    if (threadIdx.x >= 32) return;
-    // ---- the segment's scalar step (one warp, FP64) ----
+    // ---- the segment's scalar step, FP64, on warps 0-3 (one per SM
+    // sub-partition, so that their FP64 work runs side by side): the sums
+    // |s|^2 and s^H b, gamma and d; then warp 0 finalises Hessenberg column
+    // j-1 and its Givens step while warps 1-3 write the second pass's
+    // coefficients (harmless, and unused, if the segment stops here) ----
+    constexpr int NSC = 128;
+    if (threadIdx.x >= NSC) return;
+    __shared__ double s_red[NSC / 32][3];
     const int sg = c.seg, m = da.g.m;
     double ss = 0, sbr = 0, sbi = 0;            // |s|^2, s^H b
-    for (int k = lane; k < j; k += 32) {
+    for (int k = threadIdx.x; k < j; k += NSC) {
         const double2 sk = tot[2 * k], bk = tot[2 * k + 1];
         ss += sk.x * sk.x + sk.y * sk.y;
         sbr += sk.x * bk.x + sk.y * bk.y;
@@ -362,6 +377,15 @@ __global__ void __launch_bounds__(KT, 4) k_dcgs_dots(const Chunk* __restrict__ c
         sbr += __shfl_xor_sync(0xffffffffu, sbr, o);
         sbi += __shfl_xor_sync(0xffffffffu, sbi, o);
     }
+    if (lane == 0) {
+        s_red[warp][0] = ss;
+        s_red[warp][1] = sbr;
+        s_red[warp][2] = sbi;
+    }
+    asm volatile("bar.sync 2, %0;\n" ::"n"(NSC) : "memory");
+    ss = (s_red[0][0] + s_red[1][0]) + (s_red[2][0] + s_red[3][0]);
+    sbr = (s_red[0][1] + s_red[1][1]) + (s_red[2][1] + s_red[3][1]);
+    sbi = (s_red[0][2] + s_red[1][2]) + (s_red[2][2] + s_red[3][2]);
     const double c1 = tot[2 * j].x;
     const double2 c2 = tot[2 * j + 1];
     double gamma = 1.0;
@@ -370,43 +394,45 @@ __global__ void __launch_bounds__(KT, 4) k_dcgs_dots(const Chunk* __restrict__ c
         gamma = g2 > 0 ? sqrt(g2) : 0.0;        // 0: u_j lies in span(V) (a lucky breakdown)
     }
     if (!isfinite(c1) || !isfinite(c2.x) || !isfinite(c2.y) || !isfinite(gamma)) {
-        if (lane == 0) {
+        if (threadIdx.x == 0) {
             atomicExch(da.g.flag, 1);
             da.g.active[sg] = 0;
         }
         return;
     }
     double2* pre = da.pre + (int64_t)sg * (m + 1);
-    bool keep = true;
-    if (j > 0) {
-        // Hessenberg column j-1: [b_{j-1}; d_{j-1}] + gamma_{j-1} s_j over gamma_{j-1} gamma_j
-        const double gp = pre[m].x;
-        double2* hin = tot + nv;
-        double2* col = hin + j;
-        for (int i = lane; i < j; i += 32) {
-            const double2 si = tot[2 * i];
-            hin[i] = make_double2(pre[i].x + gp * si.x, pre[i].y + gp * si.y);
-        }
-        __syncwarp();
-        GivensArgs ga = da.g;
-        ga.nact = da.nact;
-        keep = givens_core(ga, sg, j - 1, hin, gp * gamma, col, da.last != 0);
-    } else if (lane == 0) {
-        atomicAdd(da.nact, 1);                  // no column yet: the segment goes on
+    // Hessenberg column j-1: [b_{j-1}; d_{j-1}] + gamma_{j-1} s_j over gamma_{j-1} gamma_j,
+    // built from the old pre before warps 1-3 overwrite it
+    const double gp = j > 0 ? pre[m].x : 1.0;
+    double2* hin = tot + nv;
+    double2* col = hin + j;
+    for (int i = threadIdx.x; i < j; i += NSC) {
+        const double2 si = tot[2 * i];
+        hin[i] = make_double2(pre[i].x + gp * si.x, pre[i].y + gp * si.y);
     }
-    if (!keep || da.last) return;
+    asm volatile("bar.sync 2, %0;\n" ::"n"(NSC) : "memory");
+    if (warp == 0) {
+        if (j > 0) {
+            GivensArgs ga = da.g;
+            ga.nact = da.nact;
+            givens_core(ga, sg, j - 1, hin, gp * gamma, col, da.last != 0);
+        } else if (lane == 0) {
+            atomicAdd(da.nact, 1);              // no column yet: the segment goes on
+        }
+        return;
+    }
+    if (da.last) return;
     const double ig = 1.0 / gamma;
     const double2 d = make_double2((c2.x - sbr) * ig, (c2.y - sbi) * ig);
     double2* cf = da.coef + (int64_t)sg * (2 * m + 2);
-    __syncwarp();                               // pre[m] (gamma_{j-1}) was read above
-    for (int k = lane; k < j; k += 32) {
+    for (int k = threadIdx.x - 32; k < j; k += NSC - 32) {
         const double2 sk = tot[2 * k], bk = tot[2 * k + 1];
         pre[k] = bk;
         cf[k] = make_double2(-sk.x * ig, -sk.y * ig);
         const double2 sd_ = make_double2((sk.x * d.x - sk.y * d.y) * ig, (sk.x * d.y + sk.y * d.x) * ig);
         cf[m + k] = make_double2(-(bk.x - sd_.x) * ig, -(bk.y - sd_.y) * ig);
     }
-    if (lane == 0) {
+    if (threadIdx.x == 32) {
         pre[j] = d;
         pre[m] = make_double2(gamma, 0.0);
         cf[2 * m] = make_double2(ig, 0.0);
@@ -421,7 +447,7 @@ template <class V>
 __global__ void __launch_bounds__(KT, 4) k_dcgs_update(const Chunk* __restrict__ chunks, V* __restrict__ basis,
                                                     int64_t ld, int j, int m, const V* __restrict__ w,
                                                     const double2* __restrict__ coef, const int* __restrict__ act,
-                                                    int* __restrict__ nact_next) {
+                                                    int* __restrict__ nact_next, unsigned long long* __restrict__ work) {
     using R = typename VT<V>::R;
     using C2 = V;                              // coefficient pairs in the vector precision
     extern __shared__ double2 sc_raw[];        // [2j+2]: alpha_k, beta_k, 1/gamma, -d/gamma^2
@@ -429,6 +455,8 @@ __global__ void __launch_bounds__(KT, 4) k_dcgs_update(const Chunk* __restrict__
     if (blockIdx.x == 0 && threadIdx.x == 0) *nact_next = 0;
     const Chunk c = chunks[blockIdx.x];
     if (!act[c.seg]) return;
+    if (work && threadIdx.x == 0)                 // v_0..v_{j-1}, u_j, w read; v_j (j > 0) and u_{j+1} written
+        atomicAdd(work, (unsigned long long)((j + 2 + (j > 0 ? 2 : 1)) * (c.end - c.begin) * sizeof(V)));
     // the coefficients are rounded to the vector precision once per block
     // (a double-to-float conversion per use would run on the slow FP64 path)
     const double2* cf = coef + (int64_t)c.seg * (2 * m + 2);
@@ -677,6 +705,7 @@ struct Krylov {
     DArr<double2> mon;
     DArr<double2> pre, coef;   // DCGS2: previous step's [b; d] and the second pass's coefficients
     bool dcgs = false;
+    unsigned long long* work = nullptr;   // [2]: dot-product and update pass bytes (the system's counters), or null
     int* nact = nullptr;
     int* flag = nullptr;
     double2* gmon = nullptr;
@@ -772,6 +801,8 @@ struct Krylov {
     // its 2j + 2 dot products (the last block reuses them for the scalar step)
     static size_t dcgs_smem(int j) { return (size_t)(2 * j + 2) * (KT / 32) * sizeof(double2); }
 
+    unsigned long long* kw(int k) const { return work ? work + k : nullptr; }
+
     int read_nact(cudaStream_t st) {
         THM_CUDA(cudaMemcpyAsync(h_pinned, nact, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
         THM_CUDA(cudaStreamSynchronize(st));
@@ -853,11 +884,11 @@ struct Krylov {
                     THM_LAUNCH(THM_K_DOTS, st, k_dcgs_dots<V><<<nch, KT, dcgs_smem(j), st>>>(d_chunks, basis.p, n,
                                                                                              last ? nullptr : w.p,
                                                                                              partial.p, 2 * m + 2,
-                                                                                             active.p, da));
+                                                                                             active.p, da, kw(0)));
                     if (!last) {
                         THM_LAUNCH(THM_K_UPDATE, st, k_dcgs_update<V><<<nch, KT, (size_t)(2 * j + 2) * sizeof(double2), st>>>(
                                                          d_chunks, basis.p, n, j, m, w.p, coef.p, active.p,
-                                                         nact + ((j + 1) & 1)));
+                                                         nact + ((j + 1) & 1), kw(1)));
                         ++total;
                     }
                     if (monitor(j, 1) || last) break;
@@ -880,15 +911,16 @@ struct Krylov {
                 // w -= V h2 (the dot kernels reduce their segments themselves); the
                 // second update also forms ||w|| and the Givens step of each segment
                 THM_LAUNCH(THM_K_DOTS, st, k_chunk_dots<V><<<nch, KT, sm, st>>>(d_chunks, basis.p, n, nk, w.p, partial.p, m + 1,
-                                                                               active.p, seg_ch.p, cnt.p, h1.p, m + 1, nact));
+                                                                               active.p, seg_ch.p, cnt.p, h1.p, m + 1, nact,
+                                                                               kw(0)));
                 THM_LAUNCH(THM_K_UPDATE, st, k_update_dots<V><<<nch, KT, sm, st>>>(d_chunks, basis.p, n, nk, h1.p, m + 1, w.p,
                                                                                   partial.p, m + 1, active.p, seg_ch.p,
-                                                                                  cnt.p, h2.p));
+                                                                                  cnt.p, h2.p, kw(1)));
                 GivensArgs ga{j, m, m + 1, h1.p, h2.p, Rm.p, cs.p, sn.p, gv.p, target.p, active.p, kused.p, beta.p,
                               nact, flag, nseg == 1 ? gmon : nullptr, seg_ch.p, cnt.p};
                 const size_t gsm = 2 * (size_t)(j + 1) * sizeof(double2);      // coefficients, or column + rotated column
                 THM_LAUNCH(THM_K_UPDATE, st, k_update_givens<V><<<nch, KT, gsm, st>>>(d_chunks, basis.p, n, nk, w.p, nrm_part.p,
-                                                                                      active.p, ga));
+                                                                                      active.p, ga, kw(1)));
                 THM_LAUNCH(THM_K_KRYLOV, st, k_chunk_scale<V><<<nch, 256, 0, st>>>(d_chunks, w.p, beta.p, basis.p + (int64_t)(j + 1) * n, active.p));
                 ++total;
                 // monitor: one copy of the step's record into the ring
@@ -949,10 +981,20 @@ struct Work {
     DArr<int32_t> pseg_ch;
 };
 
+// The system's work counters (allocated and zeroed on first use).
+static unsigned long long* kwork(const thm_sys* s) {
+    if (!s->kwork.p) {
+        s->kwork.alloc(8);
+        s->kwork.zero(s->st);
+    }
+    return s->kwork.p;
+}
+
 static void ensure_work(thm_sys* s, bool fp32, int m_in, int m_out) {
     const thm_mesh* m = s->m;
     if (!s->w) s->w = new Work();
     Work* w = s->w;
+    unsigned long long* kw = kwork(s);
     if (w->m_in != m_in) { w->has64 = w->has32 = false; w->m_in = m_in; }
     std::vector<int64_t> segn(m->n_sub);
     for (int i = 0; i < m->n_sub; ++i) segn[i] = m->subs[i].n;
@@ -1002,6 +1044,11 @@ static void ensure_work(thm_sys* s, bool fp32, int m_in, int m_out) {
         w->uglob.alloc(m->n_dof); w->rglob.alloc(m->n_dof);
         w->npart.alloc(1024);
     }
+    // Gram-Schmidt pass bytes of every Krylov process go to the counters of
+    // its precision (the interface GMRES is FP64)
+    w->in64.work = kw + 1;
+    w->in32.work = kw + 5;
+    w->outer.work = kw + 1;
 }
 
 
@@ -1045,9 +1092,17 @@ static void apply_T(const thm_sys* s, const F* val, const F* bg, const F* bs, in
     const thm_mesh* m = s->m;
     const F *bvg, *bvs;
     bv_arrays(s, val, &bvg, &bvs);
-    THM_LAUNCH(THM_K_SPMV, s->st,
-               k_spmv<V, F><<<nblk(m->n_loc), 256, 0, s->st>>>(m->n_loc, m->d_slice_ptr.p, m->d_sell_col.p, val, bg, bs,
-                                                                use_bs, bvg, bvs, x, y, m->d_loc_sub.p, act));
+    unsigned long long* work = kwork(s) + (sizeof(F) == 4 ? 4 : 0);      // rows processed
+    if (m->col16)
+        THM_LAUNCH(THM_K_SPMV, s->st,
+                   (k_spmv<V, F, uint16_t><<<nblk(m->n_loc), 256, 0, s->st>>>(
+                       m->n_loc, m->d_slice_ptr.p, m->d_sell_col16.p, m->d_subs.p, val, bg, bs, use_bs, bvg, bvs, x, y,
+                       m->d_loc_sub.p, act, work)));
+    else
+        THM_LAUNCH(THM_K_SPMV, s->st,
+                   (k_spmv<V, F, int32_t><<<nblk(m->n_loc), 256, 0, s->st>>>(
+                       m->n_loc, m->d_slice_ptr.p, m->d_sell_col.p, m->d_subs.p, val, bg, bs, use_bs, bvg, bvs, x, y,
+                       m->d_loc_sub.p, act, work)));
 }
 
 // Twisted block-tridiagonal solve, one 2-CTA cluster per subdomain.  The
