@@ -906,28 +906,35 @@ __global__ void k_gather_slots(int64_t n, const int64_t* __restrict__ slot, cons
     }
 }
 
-// Order-2 gather tables of the condensation steps (see thm_sys::tab_*).
+// Order-2 gather tables of the condensation steps (see thm_sys::tab_*).  The
+// bubbles of a cell are 4 consecutive local rows, the cells of a subdomain
+// in bubble-row order; *bad is set if a row breaks that layout.
 __global__ void k_cond_tables(int64_t n_loc, int maxc, const uint8_t* __restrict__ is_bub,
                               const int32_t* __restrict__ row_cell, const int32_t* __restrict__ row_k,
-                              const int32_t* __restrict__ cell_loc, const double* __restrict__ cinv,
-                              const double* __restrict__ cg, int32_t* __restrict__ ai, double* __restrict__ av,
-                              float* __restrict__ av32, int32_t* __restrict__ ci, double* __restrict__ cv,
-                              float* __restrict__ cv32, int32_t* __restrict__ ei, double* __restrict__ ev,
-                              float* __restrict__ ev32) {
+                              const int32_t* __restrict__ cell_loc, const int32_t* __restrict__ loc_sub,
+                              const Sub* __restrict__ subs, const double* __restrict__ cinv,
+                              const double* __restrict__ cg, int32_t* __restrict__ ab, double* __restrict__ av,
+                              float* __restrict__ av32, double* __restrict__ cv, float* __restrict__ cv32,
+                              int32_t* __restrict__ e8, double* __restrict__ ev, float* __restrict__ ev32,
+                              int* __restrict__ bad) {
     int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (r >= n_loc) return;
-    for (int u = 0; u < 8; ++u) { ai[u * n_loc + r] = (int32_t)r; av[u * n_loc + r] = 0; av32[u * n_loc + r] = 0; }
-    for (int u = 0; u < 4; ++u) { ci[u * n_loc + r] = (int32_t)r; cv[u * n_loc + r] = 0; cv32[u * n_loc + r] = 0; }
-    for (int u = 0; u < 8; ++u) { ei[u * n_loc + r] = (int32_t)r; ev[u * n_loc + r] = 0; ev32[u * n_loc + r] = 0; }
+    for (int u = 0; u < 2; ++u) ab[u * n_loc + r] = -1;
+    for (int u = 0; u < 8; ++u) { av[u * n_loc + r] = 0; av32[u * n_loc + r] = 0; }
+    for (int u = 0; u < 4; ++u) { cv[u * n_loc + r] = 0; cv32[u * n_loc + r] = 0; }
+    for (int u = 0; u < 8; ++u) { ev[u * n_loc + r] = 0; ev32[u * n_loc + r] = 0; }
     if (!is_bub[r]) {
         int q = 0;
         for (int u = 0; u < maxc; ++u) {
             int32_t c = row_cell[r * maxc + u];
             if (c < 0) break;
-            int a = row_k[r * maxc + u];
+            if (u >= 2) { atomicExch(bad, 1); break; }
+            const int a = row_k[r * maxc + u];
+            const int32_t b0 = cell_loc[(int64_t)c * 12 + 8];
+            ab[u * n_loc + r] = b0;
             for (int k = 0; k < 4; ++k, ++q) {
+                if (cell_loc[(int64_t)c * 12 + 8 + k] != b0 + k) atomicExch(bad, 1);
                 double g = cg[(int64_t)c * 32 + a * 4 + k];
-                ai[q * n_loc + r] = cell_loc[(int64_t)c * 12 + 8 + k];
                 av[q * n_loc + r] = g;
                 av32[q * n_loc + r] = (float)g;
             }
@@ -935,17 +942,20 @@ __global__ void k_cond_tables(int64_t n_loc, int maxc, const uint8_t* __restrict
     } else {
         int32_t c = row_cell[r * maxc];
         int k = row_k[r * maxc] - 8;
+        const Sub S = subs[loc_sub[r]];
+        const int64_t q4 = r - k - (S.off + S.ne);
+        if (cell_loc[(int64_t)c * 12 + 8] != r - k || q4 < 0 || (q4 & 3) != 0) atomicExch(bad, 1);
         for (int j = 0; j < 4; ++j) {
             double d = cinv[(int64_t)c * 16 + k * 4 + j];
-            ci[j * n_loc + r] = cell_loc[(int64_t)c * 12 + 8 + j];
             cv[j * n_loc + r] = d;
             cv32[j * n_loc + r] = (float)d;
         }
+        const int64_t slot = S.cell0 + q4 / 4;
         for (int a = 0; a < 8; ++a) {
             int32_t e = cell_loc[(int64_t)c * 12 + a];
+            if (k == 0 && q4 >= 0) e8[slot * 8 + a] = e;
             if (e < 0) continue;
             double g = -cg[(int64_t)c * 32 + a * 4 + k];
-            ei[a * n_loc + r] = e;
             ev[a * n_loc + r] = g;
             ev32[a * n_loc + r] = (float)g;
         }
@@ -1081,15 +1091,21 @@ void assemble(thm_sys* s) {
     THM_CUDA(cudaGetLastError());
     if (condensed) {
         const size_t n8 = 8 * (size_t)m->n_loc, n4 = 4 * (size_t)m->n_loc;
-        s->tab_ai.alloc(n8); s->tab_av64.alloc(n8); s->tab_av32.alloc(n8);
-        s->tab_ci.alloc(n4); s->tab_cv64.alloc(n4); s->tab_cv32.alloc(n4);
-        s->tab_ei.alloc(n8); s->tab_ev64.alloc(n8); s->tab_ev32.alloc(n8);
+        s->tab_ab.alloc(2 * (size_t)m->n_loc); s->tab_av64.alloc(n8); s->tab_av32.alloc(n8);
+        s->tab_cv64.alloc(n4); s->tab_cv32.alloc(n4);
+        s->tab_e8.alloc(8 * (size_t)std::max<int64_t>(1, m->n_bcell)); s->tab_ev64.alloc(n8); s->tab_ev32.alloc(n8);
+        DArr<int> bad;
+        bad.alloc(1);
+        bad.zero(st);
         THM_LAUNCH(THM_K_SETUP, st, k_cond_tables<<<grid(m->n_loc), th, 0, st>>>(m->n_loc, m->maxc, m->d_loc_is_bub.p, m->d_row_cell.p,
-                                                     m->d_row_k.p, m->d_cell_loc.p, s->cinv64.p, s->cg64.p,
-                                                     s->tab_ai.p, s->tab_av64.p, s->tab_av32.p, s->tab_ci.p,
-                                                     s->tab_cv64.p, s->tab_cv32.p, s->tab_ei.p, s->tab_ev64.p,
-                                                     s->tab_ev32.p));
+                                                     m->d_row_k.p, m->d_cell_loc.p, m->d_loc_sub.p, m->d_subs.p,
+                                                     s->cinv64.p, s->cg64.p, s->tab_ab.p, s->tab_av64.p,
+                                                     s->tab_av32.p, s->tab_cv64.p, s->tab_cv32.p, s->tab_e8.p,
+                                                     s->tab_ev64.p, s->tab_ev32.p, bad.p));
         THM_CUDA(cudaGetLastError());
+        std::vector<int> hb;
+        bad.download(hb, st);
+        THM_REQUIRE(hb[0] == 0, "internal: order-2 bubble rows not in cell groups of 4");
     }
     s->f_loc.alloc(m->n_loc);
     s->f_res.alloc(m->n_loc);

@@ -415,9 +415,8 @@ template <class V, class F, class FW = F>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(BT_THREADS, 1)
 k_bt_solve(const Sub* __restrict__ subs, const Level* __restrict__ levels, const FW* __restrict__ fac,
            const int32_t* __restrict__ cptr, const int32_t* __restrict__ ccol, const F* __restrict__ cval,
-           int64_t n_loc, int condensed, const int32_t* __restrict__ ai, const F* __restrict__ av,
-           const int32_t* __restrict__ ci, const F* __restrict__ cv, const int32_t* __restrict__ ei,
-           const F* __restrict__ ev, int R, int ns, int slot_bytes, int cslot_bytes, int cglob, int max_lev, int nvec,
+           int64_t n_loc, int condensed, const int32_t* __restrict__ ab, const F* __restrict__ av,
+           const F* __restrict__ cv, const int32_t* __restrict__ e8, const F* __restrict__ ev, int R, int ns, int slot_bytes, int cslot_bytes, int cglob, int max_lev, int nvec,
            int max_m, unsigned long long wait_ns, int stall_w,
            int* __restrict__ err, const int* __restrict__ act, const int64_t* __restrict__ welem,
            unsigned long long* __restrict__ work, const V* __restrict__ x, V* __restrict__ y) {
@@ -542,9 +541,13 @@ k_bt_solve(const Sub* __restrict__ subs, const Level* __restrict__ levels, const
                 const int e = e0 + r * BT_NT;
                 const bool ok = e < vend;
                 xr[r] = ok ? x[e] : mk<V>(0, 0);
+                // the (<= 2) cells' bubbles: 4 consecutive rows from ab[u]
+                int32_t b0[2];
+#pragma unroll
+                for (int u = 0; u < 2; ++u) b0[u] = (ok && condensed) ? ab[u * n_loc + e] : -1;
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
-                    ix[r][u] = (ok && condensed) ? ai[u * n_loc + e] : -1;
+                    ix[r][u] = b0[u >> 2] >= 0 ? b0[u >> 2] + (u & 3) : -1;
                     gv[r][u] = (ok && condensed) ? (Rt)av[u * n_loc + e] : (Rt)0;
                 }
             }
@@ -686,16 +689,20 @@ k_bt_solve(const Sub* __restrict__ subs, const Level* __restrict__ levels, const
             for (int r = 0; r < BT_PROW; ++r) {
                 const int64_t b = b0r + r * (int64_t)blockDim.x;
                 const bool ok = b < hi;
+                // the row's cell: its 4 bubbles are the rows cb..cb+3, its 8
+                // edge rows are slot cell0 + (b - b0) / 4 of e8
+                const int64_t q4 = b - b0, cb = b - (q4 & 3);
+                const int32_t* ce = e8 + ((int64_t)S.cell0 + (q4 >> 2)) * 8;
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    cix[r][j] = ok ? ci[j * n_loc + b] : -1;
+                    cix[r][j] = ok ? (int32_t)(cb + j) : -1;
                     cc[r][j] = ok ? (Rt)cv[j * n_loc + b] : (Rt)0;
                 }
 #pragma unroll
                 for (int a = 0; a < 8; ++a) {
                     // the value is loaded whatever the index (it is masked
                     // below), so that both loads are in flight together
-                    const int64_t e = ok ? (int64_t)ei[a * n_loc + b] : -1;
+                    const int64_t e = ok ? (int64_t)ce[a] : -1;
                     eix[r][a] = (e >= S.off && e < S.off + S.ne) ? (int32_t)e : -1;
                     ec[r][a] = ok ? (Rt)ev[a * n_loc + b] : (Rt)0;
                 }

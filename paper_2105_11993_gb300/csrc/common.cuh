@@ -108,7 +108,7 @@ struct Sub {
     int32_t lev0;     // first level
     int32_t nlev;
     int32_t kmid;     // middle level of the twisted factorisation (0 <= kmid < nlev)
-    int32_t pad_;
+    int32_t cell0;    // order 2: slot of the first bubble cell (rows off+ne.. in groups of 4) in thm_sys::tab_e8
 };
 
 // Values one block solve streams for subdomain S (the byte model of the
@@ -157,6 +157,7 @@ struct thm_mesh {
 
     // local (per-subdomain, free DOFs) structure
     int64_t n_loc = 0;
+    int64_t n_bcell = 0;                            // order 2: cells (bubble groups) over all subdomains
     std::vector<thm::Sub> subs;
     std::vector<int64_t> loc_gdof;                  // [n_loc]
     std::vector<int32_t> loc_sub;                   // [n_loc]
@@ -310,8 +311,13 @@ struct thm_sys {
     thm::DArr<float> cpl32;
     // order-2 gather tables (structure of arrays, [8][n_loc]): for an edge row
     // the <= 8 (bubble, G entry) pairs of r_E - G r_I; for a bubble row the 4
-    // (bubble, D^{-1} entry) and 8 (edge, -G entry) pairs of D^{-1} r_I - G^T x_E
-    thm::DArr<int32_t> tab_ai, tab_ci, tab_ei;
+    // (bubble, D^{-1} entry) and 8 (edge, -G entry) pairs of D^{-1} r_I - G^T x_E.
+    // The bubbles of a cell are 4 consecutive local rows, so the indices are
+    // not stored per entry: tab_ab [2][n_loc] holds an edge row's (<= 2) cells'
+    // first bubble rows (-1: none; entry u*4+k of av belongs to bubble ab[u]+k),
+    // tab_e8 [bubble cells][8] a cell's 8 edge rows (-1: Dirichlet), the cell of
+    // bubble row b being slot subs.cell0 + (b - off - ne) / 4
+    thm::DArr<int32_t> tab_ab, tab_e8;
     thm::DArr<double> tab_av64, tab_cv64, tab_ev64;
     thm::DArr<float> tab_av32, tab_cv32, tab_ev32;
     // block-solve work actually done, per factor precision ([0..1] FP64, [2..3]

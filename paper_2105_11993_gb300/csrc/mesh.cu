@@ -412,6 +412,7 @@ void build_mesh(thm_mesh* m) {
     m->loc_gdof.clear();
     m->loc_sub.clear();
     m->levels.clear();
+    m->n_bcell = 0;
     std::vector<std::vector<int32_t>> row_cols_all;   // per local row: sorted local columns
     m->maxc = d == 2 ? 2 : 4;
     std::vector<int32_t> row_cell_v, row_k_v;
@@ -512,6 +513,9 @@ void build_mesh(thm_mesh* m) {
         m->subs[s].off = off;
         m->subs[s].n = n;
         m->subs[s].ne = n - nbub;
+        THM_REQUIRE(nbub % 4 == 0, "internal: order-2 bubbles not in groups of 4");
+        m->subs[s].cell0 = (int32_t)m->n_bcell;
+        m->n_bcell += nbub / 4;
         m->subs[s].lev0 = (int32_t)m->levels.size();
         m->subs[s].nlev = (int32_t)bsize.size();
         int32_t st = (int32_t)off;

@@ -1146,8 +1146,8 @@ static BtCfg bt_config(const thm_mesh* m, size_t target) {
 }
 
 template <class V, class F, class FW = F>
-static void bt_launch(const thm_sys* s, const BtCfg& c, const FW* fac, const F* cval, const int32_t* ai, const F* av,
-                      const int32_t* ci, const F* cv, const int32_t* ei, const F* ev, const V* x, V* y,
+static void bt_launch(const thm_sys* s, const BtCfg& c, const FW* fac, const F* cval, const int32_t* ab, const F* av,
+                      const F* cv, const int32_t* e8, const F* ev, const V* x, V* y,
                       const int* act = nullptr) {
     const thm_mesh* m = s->m;
     static size_t attr = 0;
@@ -1168,7 +1168,7 @@ static void bt_launch(const thm_sys* s, const BtCfg& c, const FW* fac, const F* 
     THM_LAUNCH(THM_K_PINV, s->st,
                (k_bt_solve<V, F, FW><<<dim3(2, m->n_sub), BT_THREADS, c.smem, s->st>>>(
                    m->d_subs.p, m->d_levels.p, fac, m->d_cpl_ptr.p, m->d_cpl_col.p, cval, m->n_loc,
-                   m->order == 2 ? 1 : 0, ai, av, ci, cv, ei, ev, c.rows, c.ns, (int)c.slot, (int)c.cslot, c.cglob,
+                   m->order == 2 ? 1 : 0, ab, av, cv, e8, ev, c.rows, c.ns, (int)c.slot, (int)c.cslot, c.cglob,
                    m->max_lev, c.nvec, m->max_m, wait_ns, stall_w, s->dev_err.p, act, m->d_bt_welem.p, work, x,
                    y)));
 }
@@ -1178,8 +1178,8 @@ static void bt_launch(const thm_sys* s, const BtCfg& c, const FW* fac, const F* 
 // is the same each time) and the fastest of two timed launches wins; later
 // systems on the same mesh reuse it.  THM_BT_TILE_BYTES fixes it instead.
 template <class V, class F, class FW = F>
-static void apply_Pinv(const thm_sys* s, const FW* fac, const F* cval, const int32_t* ai, const F* av,
-                       const int32_t* ci, const F* cv, const int32_t* ei, const F* ev, const V* x, V* y,
+static void apply_Pinv(const thm_sys* s, const FW* fac, const F* cval, const int32_t* ab, const F* av,
+                       const F* cv, const int32_t* e8, const F* ev, const V* x, V* y,
                        const int* act = nullptr) {
     const thm_mesh* m = s->m;
     THM_REQUIRE(m->max_m <= BT_MAX_M, "level block larger than the block-solve kernel supports (" +
@@ -1202,9 +1202,9 @@ static void apply_Pinv(const thm_sys* s, const FW* fac, const F* cval, const int
             for (size_t t : cand) {
                 const BtCfg c = bt_config<V, F, FW>(m, t);
                 if (c.rows == best_rows) continue;                // same tiles as a faster-or-equal candidate
-                bt_launch<V, F, FW>(s, c, fac, cval, ai, av, ci, cv, ei, ev, x, y);      // warm
+                bt_launch<V, F, FW>(s, c, fac, cval, ab, av, cv, e8, ev, x, y);          // warm
                 THM_CUDA(cudaEventRecord(e0, s->st));
-                for (int r = 0; r < 2; ++r) bt_launch<V, F, FW>(s, c, fac, cval, ai, av, ci, cv, ei, ev, x, y);
+                for (int r = 0; r < 2; ++r) bt_launch<V, F, FW>(s, c, fac, cval, ab, av, cv, e8, ev, x, y);
                 THM_CUDA(cudaEventRecord(e1, s->st));
                 THM_CUDA(cudaEventSynchronize(e1));
                 float ms = 0;
@@ -1215,7 +1215,7 @@ static void apply_Pinv(const thm_sys* s, const FW* fac, const F* cval, const int
             cudaEventDestroy(e1);
         }
     }
-    bt_launch<V, F, FW>(s, bt_config<V, F, FW>(m, tile), fac, cval, ai, av, ci, cv, ei, ev, x, y, act);
+    bt_launch<V, F, FW>(s, bt_config<V, F, FW>(m, tile), fac, cval, ab, av, cv, e8, ev, x, y, act);
 }
 
 // The full 2x2 block preconditioner (Section 3.2's alternative): T_i^{-1} from
@@ -1223,21 +1223,21 @@ static void apply_Pinv(const thm_sys* s, const FW* fac, const F* cval, const int
 template <class V>
 static void apply_Tinv_mode(const thm_sys* s, bool f32, const V* x, V* y, const int* act = nullptr) {
     if (f32)
-        apply_Pinv<V, float, float2>(s, s->facc32.p, s->cpl32.p, s->tab_ai.p, s->tab_av32.p, s->tab_ci.p,
-                                     s->tab_cv32.p, s->tab_ei.p, s->tab_ev32.p, x, y, act);
+        apply_Pinv<V, float, float2>(s, s->facc32.p, s->cpl32.p, s->tab_ab.p, s->tab_av32.p,
+                                     s->tab_cv32.p, s->tab_e8.p, s->tab_ev32.p, x, y, act);
     else
-        apply_Pinv<V, double, double2>(s, s->facc64.p, s->cpl64.p, s->tab_ai.p, s->tab_av64.p, s->tab_ci.p,
-                                       s->tab_cv64.p, s->tab_ei.p, s->tab_ev64.p, x, y, act);
+        apply_Pinv<V, double, double2>(s, s->facc64.p, s->cpl64.p, s->tab_ab.p, s->tab_av64.p,
+                                       s->tab_cv64.p, s->tab_e8.p, s->tab_ev64.p, x, y, act);
 }
 
 template <class V>
 static void apply_Pinv_mode(const thm_sys* s, bool f32, const V* x, V* y, const int* act = nullptr) {
     if (f32)
-        apply_Pinv<V, float>(s, s->fac32.p, s->cpl32.p, s->tab_ai.p, s->tab_av32.p, s->tab_ci.p, s->tab_cv32.p,
-                             s->tab_ei.p, s->tab_ev32.p, x, y, act);
+        apply_Pinv<V, float>(s, s->fac32.p, s->cpl32.p, s->tab_ab.p, s->tab_av32.p, s->tab_cv32.p,
+                             s->tab_e8.p, s->tab_ev32.p, x, y, act);
     else
-        apply_Pinv<V, double>(s, s->fac64.p, s->cpl64.p, s->tab_ai.p, s->tab_av64.p, s->tab_ci.p, s->tab_cv64.p,
-                              s->tab_ei.p, s->tab_ev64.p, x, y, act);
+        apply_Pinv<V, double>(s, s->fac64.p, s->cpl64.p, s->tab_ab.p, s->tab_av64.p, s->tab_cv64.p,
+                              s->tab_e8.p, s->tab_ev64.p, x, y, act);
 }
 
 
