@@ -60,8 +60,8 @@ constexpr int BT_GQ = 8;
 constexpr int BT_GMAX = 4;
 constexpr int BT_MAX_M = 4 * BT_GQ * BT_GMAX * BT_NW;     // 1536
 constexpr int BT_NC = 4;                    // slots of the coupling ring
-constexpr int BT_PROW = 2;                  // rows per pass of the order-2 prologue and epilogue
-                                            // (3 measured slower: the epilogue went from 25k to 41k cycles)
+constexpr int BT_PROW_A = 4;                // rows per pass of the order-2 prologue (a)
+constexpr int BT_PROW_C = 3;                // and of the epilogue (c)
 
 __host__ __device__ constexpr int bt_r4(int v) { return (v + 3) / 4 * 4; }
 __host__ __device__ constexpr size_t bt_r16(size_t v) { return (v + 15) / 16 * 16; }
@@ -530,14 +530,14 @@ k_bt_solve(const Sub* __restrict__ subs, const Level* __restrict__ levels, const
         const int vbase = rank == 0 ? lv[0].start : lv[k].start;
         const int vend = rank == 0 ? lv[k].start + lv[k].size : lv[L - 1].start + lv[L - 1].size;
         // (a) load r for this rank's levels; order 2: r_E <- r_E - G r_I.
-        // BT_PROW rows per pass: their table loads, then their gathers, are in
+        // BT_PROW_A rows per pass: their table loads, then their gathers, are in
         // flight together (each row's arithmetic is unchanged).
-        for (int e0 = vbase + tid; e0 < vend; e0 += BT_PROW * BT_NT) {
-            int32_t ix[BT_PROW][8];
-            Rt gv[BT_PROW][8];
-            V xr[BT_PROW];
+        for (int e0 = vbase + tid; e0 < vend; e0 += BT_PROW_A * BT_NT) {
+            int32_t ix[BT_PROW_A][8];
+            Rt gv[BT_PROW_A][8];
+            V xr[BT_PROW_A];
 #pragma unroll
-            for (int r = 0; r < BT_PROW; ++r) {
+            for (int r = 0; r < BT_PROW_A; ++r) {
                 const int e = e0 + r * BT_NT;
                 const bool ok = e < vend;
                 xr[r] = ok ? x[e] : mk<V>(0, 0);
@@ -552,7 +552,7 @@ k_bt_solve(const Sub* __restrict__ subs, const Level* __restrict__ levels, const
                 }
             }
 #pragma unroll
-            for (int r = 0; r < BT_PROW; ++r) {
+            for (int r = 0; r < BT_PROW_A; ++r) {
                 const int e = e0 + r * BT_NT;
                 Rt ar = xr[r].x, aim = xr[r].y;
                 V xb[8];
@@ -681,12 +681,12 @@ k_bt_solve(const Sub* __restrict__ subs, const Level* __restrict__ levels, const
         const int64_t b0 = S.off + S.ne, nbub = S.n - S.ne;
         const int64_t half = (nbub + 1) / 2;
         const int64_t lo = b0 + (rank == 0 ? 0 : half), hi = b0 + (rank == 0 ? half : nbub);
-        // BT_PROW rows per pass, as in (a)
-        for (int64_t b0r = lo + tid; b0r < hi; b0r += BT_PROW * (int64_t)blockDim.x) {
-            int32_t cix[BT_PROW][4], eix[BT_PROW][8];
-            Rt cc[BT_PROW][4], ec[BT_PROW][8];
+        // BT_PROW_C rows per pass, as in (a)
+        for (int64_t b0r = lo + tid; b0r < hi; b0r += BT_PROW_C * (int64_t)blockDim.x) {
+            int32_t cix[BT_PROW_C][4], eix[BT_PROW_C][8];
+            Rt cc[BT_PROW_C][4], ec[BT_PROW_C][8];
 #pragma unroll
-            for (int r = 0; r < BT_PROW; ++r) {
+            for (int r = 0; r < BT_PROW_C; ++r) {
                 const int64_t b = b0r + r * (int64_t)blockDim.x;
                 const bool ok = b < hi;
                 // the row's cell: its 4 bubbles are the rows cb..cb+3, its 8
@@ -708,7 +708,7 @@ k_bt_solve(const Sub* __restrict__ subs, const Level* __restrict__ levels, const
                 }
             }
 #pragma unroll
-            for (int r = 0; r < BT_PROW; ++r) {
+            for (int r = 0; r < BT_PROW_C; ++r) {
                 const int64_t b = b0r + r * (int64_t)blockDim.x;
                 V xb[4], xe[8];
 #pragma unroll
