@@ -95,23 +95,6 @@ __global__ void __launch_bounds__(256) k_spmv(int64_t n, const int64_t* __restri
     y[r] = mk<V>(ar - b * xr.y, ai + b * xr.x);
 }
 
-// ---------------------------------------------------------------------------
-// y = P_i^{-1} x (Eq. 7: the same real P_i^{-1} on the real and on the
-// imaginary part).  Grid (n_sub, 2): blockIdx.y picks the component, so the
-// two independent real solves of one subdomain run on two SMs.
-//   (a) order 2: r_E <- r_E - G r_I          (cell bubbles condensed)
-//   (b) S^{-1} on the edge DOFs by the block-tridiagonal chain
-//   (c) order 2: x_I = D^{-1} r_I - G^T x_E
-// ---------------------------------------------------------------------------
-template <class F, class R>
-__device__ __forceinline__ R warp_dot(const F* __restrict__ a, const R* __restrict__ x, int n) {
-    R acc = 0;
-    for (int j = threadIdx.x & 31; j < n; j += 32) acc += (R)a[j] * x[j];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    return acc;
-}
-
 // ---- TMA 1-D bulk copies completing on an mbarrier (sm_90+ PTX) ----------
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -134,20 +117,6 @@ __device__ __forceinline__ void tma_load_1d(void* dst, const void* src, unsigned
         : "memory");
 }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
-// Bounded wait for the given phase parity; false after the iteration limit
-// (each try_wait itself suspends for a bounded, hardware-defined time).
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
-    for (int it = 0; it < (1 << 22); ++it) {
-        unsigned done;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(done)
-            : "r"(smem_u32(bar)), "r"(parity)
-            : "memory");
-        if (done) return true;
-    }
-    return false;
-}
 
 // ---------------------------------------------------------------------------
 // Segmented reductions for the batched Arnoldi process.  A chunk lies inside
@@ -279,16 +248,6 @@ __device__ __forceinline__ void chunk_update_body(const Chunk& c, const V* __res
                                                   const double2* __restrict__ h, int ldh, V* __restrict__ w,
                                                   double* __restrict__ nrm_part, double2* sh, V* wout = nullptr);
 
-template <class V>
-__global__ void __launch_bounds__(KT) k_chunk_update(const Chunk* __restrict__ chunks, const V* __restrict__ basis,
-                                                     int64_t ld, int nk, const double2* __restrict__ h, int ldh,
-                                                     V* __restrict__ w, double* __restrict__ nrm_part,
-                                                     const int* __restrict__ act) {
-    extern __shared__ double2 sh[];            // [nk] coefficients of this segment
-    const Chunk c = chunks[blockIdx.x];
-    if (act && !act[c.seg]) return;            // converged segment: left as it is
-    chunk_update_body<V>(c, basis, ld, nk, h, ldh, w, nrm_part, sh);
-}
 
 template <class V>
 __device__ __forceinline__ void chunk_update_body(const Chunk& c, const V* __restrict__ basis, int64_t ld, int nk,
@@ -408,9 +367,6 @@ __global__ void __launch_bounds__(KT) k_chunk_norm2(const Chunk* __restrict__ ch
     }
 }
 
-// out[seg][k] (+)= sum over the segment's chunks of partial[chunk][k]
-__global__ void k_seg_reduce(int nseg, const int32_t* __restrict__ seg_ch, const double2* __restrict__ partial,
-                             int ldp, int nk, double2* __restrict__ out, int ldo, int accumulate);
 __global__ void k_seg_reduce_real(int nseg, const int32_t* __restrict__ seg_ch, const double* __restrict__ part,
                                   double* __restrict__ out);
 

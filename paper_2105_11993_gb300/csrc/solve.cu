@@ -779,8 +779,6 @@ struct Krylov {
         }
         if (dots_smem > dots_attr) {
             THM_CUDA(cudaFuncSetAttribute(k_chunk_dots<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dots_smem));
-            THM_CUDA(cudaFuncSetAttribute(k_chunk_update<V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)((m + 1) * sizeof(double2))));
             THM_CUDA(cudaFuncSetAttribute(k_update_givens<V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)givens_smem(m)));
             THM_CUDA(cudaFuncSetAttribute(k_update_dots<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dots_smem));
