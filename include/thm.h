@@ -429,7 +429,9 @@ int thm_work_bytes(const thm_sys* s, int mode, int cls, double* bytes);
 int thm_residual_noalloc(const thm_sys* s, const double* u, double* out);
 
 /* Bytes of the stored preconditioner factors (the dense inverse blocks W_l of
- * the twisted block factorisation) for precond THM_PRECOND_* in mode
+ * the twisted block factorisation and the backward-sweep blocks H_l^T =
+ * (W_l F_l)^T resp. (W_l E_l)^T of every level but the middle one, row strides
+ * padded to 4 entries) for precond THM_PRECOND_* in mode
  * THM_MODE_*: real values for Eq. 7, complex ones for the full 2x2 block
  * operator.  From the sizes alone (nothing is factorised by this call). */
 int thm_factor_bytes(const thm_sys* s, int precond, int mode, double* bytes);
